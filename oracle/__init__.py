@@ -1,0 +1,220 @@
+"""FP64 CPU oracle for the polarized lattice-Boltzmann radiative-transfer step.
+
+TEST INFRASTRUCTURE: only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package.  It shares no code with
+the CUDA library; the C source (``rtlb_oracle.c``) documents the readings of the
+paper it fixes.  This module only marshals numpy arrays into that library.
+
+State layout: ``S[z][x][d][s]`` float64, s = (I, Q, U, V), d = i_zen * n_az + i_az.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SURV_LINEAR, SURV_EXP = 0, 1
+ABS_BEER_LAMBERT, ABS_TAYLOR = 0, 1
+BC_VACUUM, BC_PERIODIC, BC_INFLOW = 0, 1, 2
+SIDE_TOP, SIDE_BOTTOM, SIDE_LEFT, SIDE_RIGHT = 0, 1, 2, 3
+PHASE_RAYLEIGH, PHASE_HG = 0, 1
+
+_lib = None
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+
+
+def lib():
+    """Load (building on first use) the oracle shared library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.orc_direction_grid.argtypes = [C.c_int, C.c_int, _dp, _dp]
+        L.orc_stream_offset.argtypes = [C.c_double, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.orc_stream_offset.restype = C.c_int
+        L.orc_rotation.argtypes = [C.c_double, _dp]
+        L.orc_rayleigh_matrix.argtypes = [C.c_double, _dp]
+        L.orc_hg_matrix.argtypes = [C.c_double, C.c_double, C.c_double, _dp]
+        L.orc_rpr_block.argtypes = [C.c_double] * 4 + [C.c_int, C.c_double, C.c_double, _dp,
+                                                       C.POINTER(C.c_double)]
+        L.orc_phase_table.argtypes = [C.c_int, _dp, _dp, C.c_int, C.c_double, C.c_double, _dp]
+        step_args = [C.c_int, C.c_int, C.c_int, _ip, _ip, _dp, _dp, C.c_void_p, C.c_void_p,
+                     _dp, C.c_int, C.c_int, _ip, _dp]
+        L.orc_step.argtypes = step_args + [_dp, _dp]
+        L.orc_run.argtypes = step_args + [_dp, C.c_int]
+        L.orc_run_to_steady.argtypes = step_args + [_dp, C.c_double, C.c_int, C.POINTER(C.c_double)]
+        L.orc_run_to_steady.restype = C.c_int
+        L.orc_residual.argtypes = [C.c_size_t, _dp, _dp]
+        L.orc_residual.restype = C.c_double
+        L.orc_radiance_out.argtypes = [C.c_int, C.c_int, C.c_int, _ip, _ip, C.c_int, _dp, _dp]
+        L.orc_dop.argtypes = [_dp]
+        L.orc_dop.restype = C.c_double
+        L.orc_num_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+# ------------------------------------------------------------------ geometry
+
+def direction_grid(n_zen: int, n_az: int):
+    """(mu, phi) of the uniform n_zen x n_az grid, float64 arrays of length n."""
+    n = n_zen * n_az
+    mu, phi = np.zeros(n), np.zeros(n)
+    lib().orc_direction_grid(n_zen, n_az, mu, phi)
+    return mu, phi
+
+
+def stream_offsets(mu, phi):
+    """Integer D2Q9 offsets (cx, cz) per direction; raises on a tie."""
+    n = len(mu)
+    cx, cz = np.zeros(n, np.int32), np.zeros(n, np.int32)
+    for d in range(n):
+        a, b = C.c_int(), C.c_int()
+        if lib().orc_stream_offset(float(mu[d]), float(phi[d]), C.byref(a), C.byref(b)):
+            raise ValueError(f"direction {d} lies exactly between two lattice offsets")
+        cx[d], cz[d] = a.value, b.value
+    return cx, cz
+
+
+def rotation(psi: float) -> np.ndarray:
+    R = np.zeros(16)
+    lib().orc_rotation(float(psi), R)
+    return R.reshape(4, 4)
+
+
+def rayleigh_matrix(cos_t: float) -> np.ndarray:
+    P = np.zeros(16)
+    lib().orc_rayleigh_matrix(float(cos_t), P)
+    return P.reshape(4, 4)
+
+
+def hg_matrix(cos_t: float, g: float, pol_amp: float) -> np.ndarray:
+    P = np.zeros(16)
+    lib().orc_hg_matrix(float(cos_t), float(g), float(pol_amp), P)
+    return P.reshape(4, 4)
+
+
+def rpr_block(mu_o, phi_o, mu_i, phi_i, kind=PHASE_RAYLEIGH, g=0.0, pol_amp=0.0):
+    """Un-normalized rotation-phase-rotation block M(o, i) and its scalar weight."""
+    M = np.zeros(16)
+    w = C.c_double()
+    lib().orc_rpr_block(float(mu_o), float(phi_o), float(mu_i), float(phi_i), int(kind),
+                        float(g), float(pol_amp), M, C.byref(w))
+    return M.reshape(4, 4), w.value
+
+
+def phase_table(mu, phi, kind=PHASE_RAYLEIGH, g=0.0, pol_amp=0.0) -> np.ndarray:
+    """Normalized 4n x 4n redistribution table Z (row = outgoing, col = incoming)."""
+    n = len(mu)
+    Z = np.zeros((4 * n) * (4 * n))
+    lib().orc_phase_table(n, np.ascontiguousarray(mu, np.float64),
+                          np.ascontiguousarray(phi, np.float64), int(kind), float(g),
+                          float(pol_amp), Z)
+    return Z.reshape(4 * n, 4 * n)
+
+
+def phase_table_spec(mu, phi, spec) -> np.ndarray:
+    """Table for a phase-class spec tuple: ("rayleigh",), ("hg", g, pol_amp) or
+    ("mix", m, g, pol_amp) = m * rayleigh + (1 - m) * hg (both normalized)."""
+    kind = spec[0]
+    if kind == "rayleigh":
+        return phase_table(mu, phi, PHASE_RAYLEIGH)
+    if kind == "hg":
+        return phase_table(mu, phi, PHASE_HG, spec[1], spec[2])
+    if kind == "mix":
+        m = spec[1]
+        return m * phase_table(mu, phi, PHASE_RAYLEIGH) + (1 - m) * phase_table(
+            mu, phi, PHASE_HG, spec[2], spec[3])
+    raise ValueError(f"unknown phase spec {spec!r}")
+
+
+# ------------------------------------------------------------------ solver
+
+class Problem:
+    """Medium, geometry and boundaries of one lattice, in oracle form (float64)."""
+
+    def __init__(self, nx, nz, mu, phi, tau, albedo, emission, cls, Z,
+                 surv_mode=SURV_LINEAR, abs_mode=ABS_BEER_LAMBERT,
+                 bc=(BC_VACUUM,) * 4, inflow=None, offsets=None):
+        self.nx, self.nz, self.n = int(nx), int(nz), len(mu)
+        self.mu = np.ascontiguousarray(mu, np.float64)
+        self.phi = np.ascontiguousarray(phi, np.float64)
+        cx, cz = offsets if offsets is not None else stream_offsets(self.mu, self.phi)
+        self.cx = np.ascontiguousarray(cx, np.int32)
+        self.cz = np.ascontiguousarray(cz, np.int32)
+        shp = (self.nz, self.nx)
+        self.tau = np.ascontiguousarray(np.broadcast_to(tau, shp), np.float64)
+        self.albedo = np.ascontiguousarray(np.broadcast_to(albedo, shp), np.float64)
+        self.emission = (None if emission is None else
+                         np.ascontiguousarray(np.broadcast_to(emission, shp), np.float64))
+        self.cls = (None if cls is None else
+                    np.ascontiguousarray(np.broadcast_to(cls, shp), np.int32))
+        Z = np.asarray(Z, np.float64)
+        if Z.ndim == 2:
+            Z = Z[None]
+        self.Z = np.ascontiguousarray(Z)
+        assert self.Z.shape[1:] == (4 * self.n, 4 * self.n)
+        self.surv_mode, self.abs_mode = int(surv_mode), int(abs_mode)
+        self.bc = np.ascontiguousarray(bc, np.int32)
+        if (self.bc[SIDE_TOP] == BC_PERIODIC) != (self.bc[SIDE_BOTTOM] == BC_PERIODIC) or \
+           (self.bc[SIDE_LEFT] == BC_PERIODIC) != (self.bc[SIDE_RIGHT] == BC_PERIODIC):
+            raise ValueError("periodic boundaries must be set on both sides of an axis")
+        self.inflow = np.zeros((4, self.n, 4)) if inflow is None else np.array(inflow, np.float64)
+        self.inflow = np.ascontiguousarray(self.inflow.reshape(4, self.n, 4))
+
+    def _args(self):
+        e = self.emission.ctypes.data if self.emission is not None else None
+        c = self.cls.ctypes.data if self.cls is not None else None
+        return (self.nx, self.nz, self.n, self.cx, self.cz, self.tau, self.albedo, e, c,
+                self.Z, self.surv_mode, self.abs_mode, self.bc, self.inflow)
+
+    def zero_state(self) -> np.ndarray:
+        return np.zeros((self.nz, self.nx, self.n, 4))
+
+    def step(self, S: np.ndarray) -> np.ndarray:
+        S = np.ascontiguousarray(S, np.float64)
+        out = np.empty_like(S)
+        lib().orc_step(*self._args(), S, out)
+        return out
+
+    def run(self, S: np.ndarray, nsteps: int) -> np.ndarray:
+        S = np.array(S, np.float64, order="C", copy=True)
+        lib().orc_run(*self._args(), S, int(nsteps))
+        return S
+
+    def run_to_steady(self, S, tol, max_steps):
+        S = np.array(S, np.float64, order="C", copy=True)
+        r = C.c_double()
+        t = lib().orc_run_to_steady(*self._args(), S, float(tol), int(max_steps), C.byref(r))
+        return S, t, r.value
+
+    def radiance_out(self, S, side=SIDE_TOP) -> np.ndarray:
+        S = np.ascontiguousarray(S, np.float64)
+        ln = self.nx if side in (SIDE_TOP, SIDE_BOTTOM) else self.nz
+        out = np.zeros((ln, self.n, 4))
+        lib().orc_radiance_out(self.nx, self.nz, self.n, self.cx, self.cz, int(side), S, out)
+        return out
+
+
+def residual(S_old, S_new) -> float:
+    a = np.ascontiguousarray(S_old, np.float64).ravel()
+    b = np.ascontiguousarray(S_new, np.float64).ravel()
+    return lib().orc_residual(a.size, a, b)
+
+
+def dop(stokes) -> np.ndarray:
+    """Degree of polarization of (..., 4) Stokes arrays (vectorised for tests)."""
+    s = np.asarray(stokes, np.float64)
+    if s.ndim == 1:
+        return lib().orc_dop(np.ascontiguousarray(s))
+    p = np.sqrt(s[..., 1] ** 2 + s[..., 2] ** 2 + s[..., 3] ** 2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(s[..., 0] != 0, p / s[..., 0], 0.0)

@@ -1,0 +1,384 @@
+/*
+ * rtlb_oracle.c -- FP64 CPU oracle for the classical polarized lattice-Boltzmann
+ * radiative-transfer time step of "A Quantum-Inspired Two-Dimensional Lattice
+ * Polarized Radiative Transfer Simulator" (Zeng, Lin, Omar).
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark may load this library.  The product path (the CUDA
+ * library) shares no code with it: its own table builder, streaming rule and step
+ * are written separately.  Everything here is plain, slow and in the order the
+ * paper states it; OpenMP only splits the outer loop over lattice rows.
+ *
+ * Layouts (all row-major, double):
+ *   state   S[z][x][d][s]      s = I,Q,U,V ; d = i_zen * n_az + i_az
+ *   medium  tau[z][x], albedo[z][x], emis[z][x] (per-step, per-direction, I only),
+ *           cls[z][x] (phase-table index)
+ *   table   Z[c][4n][4n]        Z[4*o + r][4*i + k] maps incoming (i, k) -> outgoing (o, r)
+ *
+ * Readings of the paper fixed here (each also listed in the design notes):
+ *   - directions: mu = -1 + (2 i_zen + 1)/n_zen (equal solid-angle bins, downward
+ *     first), phi = 2 pi i_az / n_az, equal quadrature weights 4 pi / n
+ *     (Sec. 2.1, "uniformly distributed zenith and azimuth", omega = 4 pi / n_d).
+ *   - streaming offset: the nearest of the 8 D2Q9 neighbour offsets (by angle) of
+ *     the (x, z) projection (sin(theta) cos(phi), mu); zero projection rests.
+ *   - polarization frame angles psi_in / psi_out: the geometric angle between the
+ *     local meridian plane and the scattering plane (Eq. 13 and 15; the literal
+ *     azimuth form of Eq. 15 does not reproduce the single-scatter degree of
+ *     polarization the paper reports in Sec. 3.2.2).
+ *   - normalization (Eq. 17): each 4x4 block is divided by the column sum of the
+ *     scalar phase function, so sum_o Z11(o, i) = 1.
+ *   - step order: emission, absorption, scattering, streaming (Sec. 2.1, Eq. 6-11,
+ *     then the propagation operator).
+ *
+ * parity of the D1Q2 peak values quoted in Sec. 3.1 (1.806 / 1.475): unpinned --
+ * they depend on the set-up of a cited paper that is not reproduced here.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_PI 3.14159265358979323846
+
+enum { ORC_SURV_LINEAR = 0, ORC_SURV_EXP = 1 };
+enum { ORC_ABS_BEER_LAMBERT = 0, ORC_ABS_TAYLOR = 1 };
+enum { ORC_BC_VACUUM = 0, ORC_BC_PERIODIC = 1, ORC_BC_INFLOW = 2 };
+enum { ORC_SIDE_TOP = 0, ORC_SIDE_BOTTOM = 1, ORC_SIDE_LEFT = 2, ORC_SIDE_RIGHT = 3 };
+enum { ORC_PHASE_RAYLEIGH = 0, ORC_PHASE_HG = 1 };
+
+/* ------------------------------------------------------------------ geometry */
+
+/* Uniform angular grid (Sec. 2.1; Eq. 4 text: directions equally distributed
+ * over zenith and azimuth).  Equal solid-angle zenith bins, cell midpoints. */
+void orc_direction_grid(int n_zen, int n_az, double *mu, double *phi)
+{
+    for (int iz = 0; iz < n_zen; ++iz)
+        for (int ia = 0; ia < n_az; ++ia) {
+            mu[iz * n_az + ia] = -1.0 + (2.0 * iz + 1.0) / n_zen;
+            phi[iz * n_az + ia] = 2.0 * ORC_PI * ia / n_az;
+        }
+}
+
+static void unit_vector(double mu, double phi, double v[3])
+{
+    double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+    v[0] = st * cos(phi);
+    v[1] = st * sin(phi);
+    v[2] = mu;
+}
+
+/* D2Q9 streaming offset of one direction (Sec. 2.1, Fig. 1b/2: propagation along
+ * (-1, 0, 1) on both lattice axes).  Returns 1 when the projection lies exactly
+ * between two neighbour offsets (no nearest one), else 0. */
+int orc_stream_offset(double mu, double phi, int *cx, int *cz)
+{
+    static const int ox[8] = {1, 1, 0, -1, -1, -1, 0, 1};
+    static const int oz[8] = {0, 1, 1, 1, 0, -1, -1, -1};
+    double px = sqrt(fmax(0.0, 1.0 - mu * mu)) * cos(phi);
+    double pz = mu;
+    if (hypot(px, pz) < 1e-12) { *cx = 0; *cz = 0; return 0; }
+    double t = atan2(pz, px) * (180.0 / ORC_PI) / 45.0;   /* angle in units of 45 deg */
+    double f = t - floor(t);
+    if (fabs(f - 0.5) < 1e-9) return 1;
+    long k = (long)floor(t + 0.5);
+    k = ((k % 8) + 8) % 8;
+    *cx = ox[k];
+    *cz = oz[k];
+    return 0;
+}
+
+/* ----------------------------------------------------- Mueller matrices (4x4) */
+
+/* Stokes frame rotation, Eq. 21/22. */
+void orc_rotation(double psi, double R[16])
+{
+    double c = cos(2.0 * psi), s = sin(2.0 * psi);
+    memset(R, 0, 16 * sizeof(double));
+    R[0] = 1.0;
+    R[5] = c;  R[6] = s;
+    R[9] = -s; R[10] = c;
+    R[15] = 1.0;
+}
+
+/* Normalized Rayleigh matrix P~(theta) of Eq. 16 (without the 3/(8 pi)). */
+void orc_rayleigh_matrix(double cos_t, double P[16])
+{
+    double a = 0.5 * (1.0 + cos_t * cos_t);
+    double b = -0.5 * (1.0 - cos_t * cos_t);
+    memset(P, 0, 16 * sizeof(double));
+    P[0] = a;  P[1] = b;
+    P[4] = b;  P[5] = a;
+    P[10] = cos_t;
+    P[15] = cos_t;
+}
+
+/* Henyey-Greenstein weighted Mueller matrix used for cloud cells: the HG
+ * scalar phase function times [[1,p,0,0],[p,1,0,0],[0,0,q,0],[0,0,0,q]] with
+ * p = pol_amp * sin^2(theta) and q = sqrt(1 - p^2).  (The paper names such
+ * matrices as the extension of its Rayleigh kernel to cloud droplets.) */
+void orc_hg_matrix(double cos_t, double g, double pol_amp, double P[16])
+{
+    double h = (1.0 - g * g) / pow(1.0 + g * g - 2.0 * g * cos_t, 1.5);
+    double p = pol_amp * (1.0 - cos_t * cos_t);
+    double q = sqrt(fmax(0.0, 1.0 - p * p));
+    memset(P, 0, 16 * sizeof(double));
+    P[0] = h;      P[1] = h * p;
+    P[4] = h * p;  P[5] = h;
+    P[10] = h * q;
+    P[15] = h * q;
+}
+
+static void matmul4(const double A[16], const double B[16], double C[16])
+{
+    double T[16];
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            double acc = 0.0;
+            for (int k = 0; k < 4; ++k) acc += A[4 * r + k] * B[4 * k + c];
+            T[4 * r + c] = acc;
+        }
+    memcpy(C, T, sizeof(T));
+}
+
+/* Angle from the meridian-plane axis of direction (mu, phi) to the in-plane
+ * axis n x Omega of the scattering plane with unit normal n, measured towards
+ * the azimuthal axis (Eq. 13/15, geometric reading). */
+static double frame_angle(const double nrm[3], double mu, double phi)
+{
+    double om[3], par[3], per[3], p[3];
+    unit_vector(mu, phi, om);
+    double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+    par[0] = mu * cos(phi); par[1] = mu * sin(phi); par[2] = -st;
+    per[0] = -sin(phi);     per[1] = cos(phi);      per[2] = 0.0;
+    p[0] = nrm[1] * om[2] - nrm[2] * om[1];
+    p[1] = nrm[2] * om[0] - nrm[0] * om[2];
+    p[2] = nrm[0] * om[1] - nrm[1] * om[0];
+    double x = p[0] * par[0] + p[1] * par[1] + p[2] * par[2];
+    double y = p[0] * per[0] + p[1] * per[1] + p[2] * per[2];
+    return atan2(y, x);
+}
+
+/* One rotation-phase-rotation block (Eq. 13): M = R(-psi_out) P~(theta) R(psi_in),
+ * theta from Eq. 14.  *w receives the scalar phase function P~11 used by the
+ * Eq. 17 weights.  Parallel and antiparallel pairs take psi = 0. */
+void orc_rpr_block(double mu_o, double phi_o, double mu_i, double phi_i,
+                   int kind, double g, double pol_amp, double M[16], double *w)
+{
+    double vo[3], vi[3], n[3], P[16], Ri[16], Ro[16];
+    unit_vector(mu_o, phi_o, vo);
+    unit_vector(mu_i, phi_i, vi);
+    double cos_t = vo[0] * vi[0] + vo[1] * vi[1] + vo[2] * vi[2];
+    if (cos_t > 1.0) cos_t = 1.0;
+    if (cos_t < -1.0) cos_t = -1.0;
+    if (kind == ORC_PHASE_RAYLEIGH) orc_rayleigh_matrix(cos_t, P);
+    else orc_hg_matrix(cos_t, g, pol_amp, P);
+    *w = P[0];
+    n[0] = vi[1] * vo[2] - vi[2] * vo[1];
+    n[1] = vi[2] * vo[0] - vi[0] * vo[2];
+    n[2] = vi[0] * vo[1] - vi[1] * vo[0];
+    double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    double psi_i = 0.0, psi_o = 0.0;
+    if (nn > 1e-12) {
+        n[0] /= nn; n[1] /= nn; n[2] /= nn;
+        psi_i = frame_angle(n, mu_i, phi_i);
+        psi_o = frame_angle(n, mu_o, phi_o);
+    }
+    orc_rotation(psi_i, Ri);
+    orc_rotation(-psi_o, Ro);
+    double T[16];
+    matmul4(P, Ri, T);
+    matmul4(Ro, T, M);
+}
+
+/* Full 4n x 4n redistribution table (Eq. 13-17, 25): Z(o, i) = M(o, i) / N(i),
+ * N(i) = sum_o P~11(theta(o, i)) (equal quadrature weights cancel). */
+void orc_phase_table(int n, const double *mu, const double *phi,
+                     int kind, double g, double pol_amp, double *Z)
+{
+    int K = 4 * n;
+    double *wcol = (double *)calloc((size_t)n, sizeof(double));
+    for (int o = 0; o < n; ++o)
+        for (int i = 0; i < n; ++i) {
+            double M[16], w;
+            orc_rpr_block(mu[o], phi[o], mu[i], phi[i], kind, g, pol_amp, M, &w);
+            wcol[i] += w;
+            for (int r = 0; r < 4; ++r)
+                for (int k = 0; k < 4; ++k)
+                    Z[(size_t)(4 * o + r) * K + 4 * i + k] = M[4 * r + k];
+        }
+    for (int row = 0; row < K; ++row)
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < 4; ++k)
+                Z[(size_t)row * K + 4 * i + k] /= wcol[i];
+    free(wcol);
+}
+
+/* ---------------------------------------------------------------- time step */
+
+/* Post-collision state P of one site: emission (Eq. 6/8), absorption
+ * (Sec. 2.1.4, Beer-Lambert or first-order Taylor), scattering (Eq. 11/12). */
+static void collide_site(int n, const double *Zc, double tau, double w0, double e,
+                         int surv_mode, int abs_mode, const double *S, double *P,
+                         double *Se)
+{
+    int K = 4 * n;
+    for (int j = 0; j < K; ++j) Se[j] = S[j];
+    for (int d = 0; d < n; ++d) Se[4 * d] += e;                     /* emission */
+    double kabs = (1.0 - w0) * tau, ksca = w0 * tau;
+    double A = (abs_mode == ORC_ABS_TAYLOR) ? 1.0 - kabs : exp(-kabs);
+    for (int j = 0; j < K; ++j) Se[j] *= A;                          /* absorption */
+    double s = (surv_mode == ORC_SURV_EXP) ? exp(-ksca) : 1.0 - ksca;
+    for (int row = 0; row < K; ++row) {                              /* scattering */
+        double red = 0.0;
+        for (int col = 0; col < K; ++col) red += Zc[(size_t)row * K + col] * Se[col];
+        P[row] = s * Se[row] + (1.0 - s) * red;
+    }
+}
+
+/* Value streamed into (x, z, d) from the upstream cell (x - cx, z - cz): interior,
+ * periodic wrap ("shifts taken modulo"), or the side's ghost value (vacuum = 0,
+ * inflow = the side's Stokes vector).  Ghost corners belong to the top/bottom
+ * side.  Returns a pointer into P or into the inflow table, or NULL for zero. */
+static const double *upstream(int nx, int nz, int n, int x, int z, int d, int cx, int cz,
+                              const int *bc, const double *inflow, const double *P)
+{
+    int xs = x - cx, zs = z - cz;
+    if (bc[ORC_SIDE_LEFT] == ORC_BC_PERIODIC) xs = ((xs % nx) + nx) % nx;
+    if (bc[ORC_SIDE_TOP] == ORC_BC_PERIODIC) zs = ((zs % nz) + nz) % nz;
+    int side = -1;
+    if (zs >= nz) side = ORC_SIDE_TOP;
+    else if (zs < 0) side = ORC_SIDE_BOTTOM;
+    else if (xs < 0) side = ORC_SIDE_LEFT;
+    else if (xs >= nx) side = ORC_SIDE_RIGHT;
+    if (side < 0) return P + (((size_t)zs * nx + xs) * n + d) * 4;
+    if (bc[side] == ORC_BC_INFLOW) return inflow + ((size_t)side * n + d) * 4;
+    return NULL;
+}
+
+/* One full step S_in -> S_out (emission, absorption, scattering, streaming).
+ * bc[4] = kinds of top, bottom, left, right; periodic must be set on both
+ * sides of an axis.  inflow[4][n][4] holds the ghost Stokes vectors. */
+void orc_step(int nx, int nz, int n, const int *cx, const int *cz,
+              const double *tau, const double *albedo, const double *emis, const int *cls,
+              const double *Z, int surv_mode, int abs_mode, const int *bc,
+              const double *inflow, const double *S_in, double *S_out)
+{
+    int K = 4 * n;
+    size_t nsite = (size_t)nx * nz;
+    double *P = (double *)malloc(nsite * K * sizeof(double));
+#pragma omp parallel
+    {
+        double *Se = (double *)malloc((size_t)K * sizeof(double));
+#pragma omp for schedule(static)
+        for (int z = 0; z < nz; ++z)
+            for (int x = 0; x < nx; ++x) {
+                size_t st = (size_t)z * nx + x;
+                const double *Zc = Z + (size_t)(cls ? cls[st] : 0) * K * K;
+                collide_site(n, Zc, tau[st], albedo[st], emis ? emis[st] : 0.0,
+                             surv_mode, abs_mode, S_in + st * K, P + st * K, Se);
+            }
+        free(Se);
+    }
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; ++z)
+        for (int x = 0; x < nx; ++x)
+            for (int d = 0; d < n; ++d) {
+                const double *src = upstream(nx, nz, n, x, z, d, cx[d], cz[d], bc, inflow, P);
+                double *dst = S_out + (((size_t)z * nx + x) * n + d) * 4;
+                for (int s = 0; s < 4; ++s) dst[s] = src ? src[s] : 0.0;
+            }
+    free(P);
+}
+
+/* Run nsteps steps in place on S (ping-pong through a scratch copy). */
+void orc_run(int nx, int nz, int n, const int *cx, const int *cz,
+             const double *tau, const double *albedo, const double *emis, const int *cls,
+             const double *Z, int surv_mode, int abs_mode, const int *bc,
+             const double *inflow, double *S, int nsteps)
+{
+    size_t len = (size_t)nx * nz * n * 4;
+    double *T = (double *)malloc(len * sizeof(double));
+    for (int t = 0; t < nsteps; ++t) {
+        orc_step(nx, nz, n, cx, cz, tau, albedo, emis, cls, Z, surv_mode, abs_mode, bc,
+                 inflow, S, T);
+        memcpy(S, T, len * sizeof(double));
+    }
+    free(T);
+}
+
+/* Steady-state residual: max |S_new - S_old| / max |S_new| over all entries. */
+double orc_residual(size_t len, const double *S_old, const double *S_new)
+{
+    double dmax = 0.0, vmax = 0.0;
+    for (size_t j = 0; j < len; ++j) {
+        double d = fabs(S_new[j] - S_old[j]), v = fabs(S_new[j]);
+        if (d > dmax) dmax = d;
+        if (v > vmax) vmax = v;
+    }
+    return vmax > 0.0 ? dmax / vmax : dmax;
+}
+
+/* Iterate to the steady state of Eq. 1 (time derivative zero): step until the
+ * residual falls below tol or max_steps is reached.  Returns steps taken. */
+int orc_run_to_steady(int nx, int nz, int n, const int *cx, const int *cz,
+                      const double *tau, const double *albedo, const double *emis,
+                      const int *cls, const double *Z, int surv_mode, int abs_mode,
+                      const int *bc, const double *inflow, double *S, double tol,
+                      int max_steps, double *residual)
+{
+    size_t len = (size_t)nx * nz * n * 4;
+    double *T = (double *)malloc(len * sizeof(double));
+    int t = 0;
+    double r = INFINITY;
+    while (t < max_steps) {
+        orc_step(nx, nz, n, cx, cz, tau, albedo, emis, cls, Z, surv_mode, abs_mode, bc,
+                 inflow, S, T);
+        r = orc_residual(len, S, T);
+        memcpy(S, T, len * sizeof(double));
+        ++t;
+        if (r < tol) break;
+    }
+    free(T);
+    *residual = r;
+    return t;
+}
+
+/* Outgoing radiance on one side: the state on the boundary row/column for the
+ * directions whose streaming offset leaves the domain through that side; zero
+ * for the other directions.  out[len][n][4], len = nx (top/bottom) or nz. */
+void orc_radiance_out(int nx, int nz, int n, const int *cx, const int *cz, int side,
+                      const double *S, double *out)
+{
+    int len = (side == ORC_SIDE_TOP || side == ORC_SIDE_BOTTOM) ? nx : nz;
+    for (int p = 0; p < len; ++p)
+        for (int d = 0; d < n; ++d) {
+            int x, z, leaves;
+            switch (side) {
+            case ORC_SIDE_TOP:    x = p; z = nz - 1; leaves = cz[d] == 1; break;
+            case ORC_SIDE_BOTTOM: x = p; z = 0;      leaves = cz[d] == -1; break;
+            case ORC_SIDE_LEFT:   x = 0; z = p;      leaves = cx[d] == -1; break;
+            default:              x = nx - 1; z = p; leaves = cx[d] == 1; break;
+            }
+            const double *src = S + (((size_t)z * nx + x) * n + d) * 4;
+            double *dst = out + ((size_t)p * n + d) * 4;
+            for (int s = 0; s < 4; ++s) dst[s] = leaves ? src[s] : 0.0;
+        }
+}
+
+/* Degree of polarization, sqrt(Q^2 + U^2 + V^2) / I (Sec. 3.2.1). */
+double orc_dop(const double *stokes)
+{
+    double I = stokes[0];
+    double p = sqrt(stokes[1] * stokes[1] + stokes[2] * stokes[2] + stokes[3] * stokes[3]);
+    return I != 0.0 ? p / I : 0.0;
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
