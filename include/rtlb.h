@@ -1,0 +1,181 @@
+/*
+ * rtlb.h -- C ABI of the B300 polarized lattice-Boltzmann radiative-transfer
+ * library (librtlb.so).
+ *
+ * The library advances the classical lattice form of the polarized radiative
+ * transfer equation (Eq. 1) on a 2D (x, z) lattice with n 3D directions, the
+ * discrete update of Eq. 2: every site holds a Stokes vector (I, Q, U, V) per
+ * direction, and one step applies emission (Eq. 6/8), absorption (Sec. 2.1.4),
+ * scattering through rotated phase matrices (Eq. 11-17, 21-25) and streaming to
+ * the D2Q9 neighbours (Sec. 2.1.6, boundary handling Sec. 2.1.7).
+ *
+ * Conventions shared by every call
+ *  - Status codes, never exceptions.  On any error the context is unchanged and
+ *    rtlb_last_error() describes the cause.
+ *  - Pointers marked "host or device" may point to either; the library checks
+ *    which with the CUDA runtime.  Pointers marked "device" must be device
+ *    memory of the context's GPU.  The library never keeps a caller pointer:
+ *    inputs are copied into library-owned buffers before the call returns (for
+ *    device inputs: before the stream work the call enqueues completes).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    stream-ordered unless marked "synchronizes".
+ *  - User state layout S[z][x][d][s], float32, s = I,Q,U,V; d = i_zen*n_az+i_az.
+ *  - Lattice: x = 0..nx-1 left to right, z = 0..nz-1 bottom to top.
+ */
+#ifndef RTLB_H
+#define RTLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rtlb_ctx rtlb_ctx; /* opaque, library-owned */
+
+typedef enum {
+    RTLB_OK = 0,
+    RTLB_E_ARG = 1,              /* null pointer, bad enum, bad count            */
+    RTLB_E_SHAPE = 2,            /* lattice / direction sizes out of range       */
+    RTLB_E_RANGE = 3,            /* medium value out of range (tau<0, albedo...) */
+    RTLB_E_AMBIGUOUS_STREAM = 4, /* a direction lies between two lattice offsets */
+    RTLB_E_STATE = 5,            /* call order (e.g. step before set_medium)     */
+    RTLB_E_OOM = 6,              /* device allocation failed                     */
+    RTLB_E_CUDA = 7,             /* CUDA runtime / launch error                  */
+    RTLB_E_NONFINITE = 8,        /* NaN or Inf in an input or in the state       */
+    RTLB_E_NOT_CONVERGED = 9,    /* run_to_steady hit max_steps                  */
+    RTLB_E_TIMEOUT = 10,         /* a bounded device wait gave up                */
+    RTLB_E_UNSUPPORTED = 11      /* precision form not available for this shape  */
+} rtlb_status;
+
+typedef enum { RTLB_SIDE_TOP = 0, RTLB_SIDE_BOTTOM = 1, RTLB_SIDE_LEFT = 2, RTLB_SIDE_RIGHT = 3 } rtlb_side;
+typedef enum { RTLB_BC_VACUUM = 0, RTLB_BC_PERIODIC = 1, RTLB_BC_INFLOW = 2 } rtlb_bc;
+
+/* Arithmetic of the scattering contraction (the state is always float32):
+ *  FP32     -- float32 FMA on the CUDA cores.
+ *  BF16     -- tcgen05 tensor-core MMA, bf16 operands, float32 accumulation.
+ *  BF16X3   -- tcgen05, operands split hi+lo in bf16, three MMAs per product. */
+typedef enum { RTLB_PREC_FP32 = 0, RTLB_PREC_BF16 = 1, RTLB_PREC_BF16X3 = 2 } rtlb_precision;
+
+/* Survival of unscattered light over one step: LINEAR = 1 - k_scat dt (Eq. 11
+ * as printed), EXP = exp(-k_scat dt).  Absorption: BEER_LAMBERT =
+ * exp(-k_abs dt), TAYLOR = 1 - k_abs dt (Sec. 2.1.4). */
+typedef enum { RTLB_SURV_LINEAR = 0, RTLB_SURV_EXP = 1 } rtlb_survival;
+typedef enum { RTLB_ABS_BEER_LAMBERT = 0, RTLB_ABS_TAYLOR = 1 } rtlb_absorption;
+
+typedef struct { int32_t nx, nz; } rtlb_grid;
+
+/* Angular grid (Sec. 2.1, Eq. 4 text): n = n_zen * n_az directions.  With mu
+ * and phi NULL the grid is uniform: mu = -1 + (2 i_zen + 1) / n_zen (equal
+ * solid-angle zenith bins, downward first), phi = 2 pi i_az / n_az.  Otherwise
+ * mu[n], phi[n] (host) list the directions explicitly (e.g. the azimuth and
+ * zenith sets of Tables 1-2). */
+typedef struct {
+    int32_t n_zen, n_az;
+    const double *mu;  /* host, optional, length n */
+    const double *phi; /* host, optional, length n */
+} rtlb_directions;
+
+typedef struct {
+    int32_t precision;  /* rtlb_precision  */
+    int32_t survival;   /* rtlb_survival   */
+    int32_t absorption; /* rtlb_absorption */
+} rtlb_options;
+
+/* Create a context on the current CUDA device.  Computes each direction's
+ * D2Q9 streaming offset: the neighbour offset nearest (by angle) to the (x, z)
+ * projection (sin(theta) cos(phi), mu); a zero projection rests.  Returns
+ * RTLB_E_AMBIGUOUS_STREAM when a projection lies within 1e-9 (in units of 45
+ * degrees) of the midpoint between two offsets.  1 <= nx, nz <= 65535;
+ * 1 <= n <= 256.  opts may be NULL (FP32, LINEAR, BEER_LAMBERT).  Allocates
+ * two state buffers of nx*nz*n*16 bytes (the state starts at zero). */
+rtlb_status rtlb_create(const rtlb_grid *grid, const rtlb_directions *dirs,
+                        const rtlb_options *opts, rtlb_ctx **out);
+
+/* Medium of Eq. 2 in per-step dimensionless form: tau = k_ext dt (optical depth
+ * of one cell and step), albedo = k_scat / k_ext, emission = dt J (added to I of
+ * every direction each step, Eq. 6/8; NULL = 0), all [nz][nx] float32, host or
+ * device.  phase_tables: host float64 [n_phase][4n][4n], row-major, entry
+ * [4o+r][4i+k] maps incoming direction i, Stokes k to outgoing o, Stokes r (the
+ * normalized redistribution of Eq. 13-17/25, e.g. from rtlb_phase_rayleigh).
+ * phase_index: [nz][nx] uint8 class per site, host or device, NULL = class 0.
+ * Checks (RTLB_E_RANGE / RTLB_E_NONFINITE): tau finite and >= 0, albedo in
+ * [0, 1], emission finite and >= 0, phase_index < n_phase, LINEAR survival
+ * needs albedo*tau <= 1, TAYLOR absorption needs (1-albedo)*tau <= 1.
+ * 1 <= n_phase <= 16.  Synchronizes on `stream` (validation result). */
+rtlb_status rtlb_set_medium(rtlb_ctx *ctx, const float *tau, const float *albedo,
+                            const float *emission, int32_t n_phase,
+                            const double *phase_tables, const uint8_t *phase_index,
+                            void *stream);
+
+/* Boundary kind of one side (Sec. 2.1.7): VACUUM = absorbing (zero-fill shift),
+ * PERIODIC = recycling (shift modulo; must be set on both sides of an axis
+ * before stepping), INFLOW = a fixed ghost Stokes vector per direction,
+ * inflow[n][4] float32 host (required for INFLOW, ignored otherwise).  Ghost
+ * corners belong to the top/bottom side.  Default: VACUUM everywhere. */
+rtlb_status rtlb_set_boundary(rtlb_ctx *ctx, int32_t side, int32_t kind, const float *inflow);
+
+/* Replace / read the state S[z][x][d][s] (float32, host or device). */
+rtlb_status rtlb_set_state(rtlb_ctx *ctx, const float *S, void *stream);
+rtlb_status rtlb_get_state(rtlb_ctx *ctx, float *S_out, void *stream);
+
+/* Advance nsteps >= 0 steps: per step and site, emission, absorption,
+ * scattering (the 4n x 4n contraction), then streaming of every direction to
+ * its neighbour.  The stored state is the paper's S^t (after streaming). */
+rtlb_status rtlb_step(rtlb_ctx *ctx, int32_t nsteps, void *stream);
+
+/* Step until the residual max|S^{t+1} - S^t| / max|S^{t+1}| (float64 on the
+ * device) is below tol, checking every check_every steps, or max_steps is
+ * reached (RTLB_E_NOT_CONVERGED; the state is kept).  Synchronizes. */
+rtlb_status rtlb_run_to_steady(rtlb_ctx *ctx, double tol, int32_t max_steps,
+                               int32_t check_every, int32_t *steps_taken,
+                               double *residual, void *stream);
+
+/* Residual between the current state and the one before the last step
+ * (float64, same definition as above).  Synchronizes. */
+rtlb_status rtlb_last_residual(rtlb_ctx *ctx, double *residual, void *stream);
+
+/* Radiance leaving through one side: out[len][n][4] float32 (host or device),
+ * len = nx for top/bottom and nz for left/right: the state on the boundary row
+ * or column for the directions whose offset points out of the domain through
+ * that side, zero for the others. */
+rtlb_status rtlb_radiance_out(rtlb_ctx *ctx, int32_t side, float *out, void *stream);
+
+/* Total I over the lattice and directions, accumulated in float64 on the
+ * device.  Synchronizes. */
+rtlb_status rtlb_total_intensity(rtlb_ctx *ctx, double *total, void *stream);
+
+/* Steps taken since the last rtlb_set_state (or creation). */
+int64_t rtlb_steps_done(const rtlb_ctx *ctx);
+
+const char *rtlb_last_error(const rtlb_ctx *ctx);
+void rtlb_destroy(rtlb_ctx *ctx);
+
+/* ---- host helpers (float64, no GPU needed) ---- */
+
+/* Per-direction D2Q9 offsets cx[n], cz[n] (host int32) of the grid. */
+rtlb_status rtlb_stream_offsets(const rtlb_directions *dirs, int32_t *cx, int32_t *cz);
+
+/* Normalized Rayleigh table (Eq. 13-17 with Eq. 16 and the rotation of Eq. 21):
+ * Z_out[4n][4n] host float64.  Block (o, i) = R(-psi_o) P~(theta) R(psi_i)
+ * divided by sum_o' P~11(theta(o', i)); psi is the angle between the local
+ * meridian plane and the scattering plane. */
+rtlb_status rtlb_phase_rayleigh(const rtlb_directions *dirs, double *Z_out);
+
+/* Henyey-Greenstein weighted Mueller table for cloud cells: HG(theta; g) times
+ * [[1,p,0,0],[p,1,0,0],[0,0,q,0],[0,0,0,q]], p = pol_amp sin^2(theta),
+ * q = sqrt(1 - p^2), rotated and normalized as above.  dZdg_out (optional,
+ * may be NULL) receives the derivative of the normalized table in g. */
+rtlb_status rtlb_phase_hg(const rtlb_directions *dirs, double g, double pol_amp,
+                          double *Z_out, double *dZdg_out);
+
+/* Mixture table m * Rayleigh + (1 - m) * HG(g, pol_amp), both normalized as
+ * above (so the mixture's weights also sum to one); 0 <= m <= 1. */
+rtlb_status rtlb_phase_mix(const rtlb_directions *dirs, double m, double g, double pol_amp,
+                           double *Z_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTLB_H */

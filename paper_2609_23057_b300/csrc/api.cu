@@ -1,0 +1,513 @@
+// C-ABI entry points of librtlb (declared in include/rtlb.h).
+//
+// A context owns: the direction set and streaming offsets, the boundary
+// description, the per-site step coefficients and phase tables of the current
+// medium, and two direction-major state buffers [d][site][4] that alternate
+// every step (the new state is written by push streaming from the old one).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "rtlb_internal.h"
+#include "tc.h"
+
+using namespace rtlb;
+
+namespace {
+
+rtlb_status fail(rtlb_ctx *ctx, rtlb_status st, const char *fmt, ...)
+{
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+rtlb_status cuda_fail(rtlb_ctx *ctx, cudaError_t e, const char *what)
+{
+    return fail(ctx, e == cudaErrorMemoryAllocation ? RTLB_E_OOM : RTLB_E_CUDA, "%s: %s (%s)", what,
+                cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define CK(ctx, call, what)                                        \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, (what)); \
+    } while (0)
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+rtlb_status build_dirs(const rtlb_directions *dirs, std::vector<double> &mu, std::vector<double> &phi,
+                       std::vector<int> &cx, std::vector<int> &cz, rtlb_ctx *ctx)
+{
+    if (!dirs) return fail(ctx, RTLB_E_ARG, "directions is NULL");
+    if (dirs->n_zen < 1 || dirs->n_az < 1 || (int64_t)dirs->n_zen * dirs->n_az > kMaxDirs)
+        return fail(ctx, RTLB_E_SHAPE, "need 1 <= n_zen*n_az <= %d (got %d x %d)", kMaxDirs, dirs->n_zen,
+                    dirs->n_az);
+    const int n = dirs->n_zen * dirs->n_az;
+    if ((dirs->mu == nullptr) != (dirs->phi == nullptr))
+        return fail(ctx, RTLB_E_ARG, "mu and phi must both be given or both be NULL");
+    if (dirs->mu) {
+        mu.assign(dirs->mu, dirs->mu + n);
+        phi.assign(dirs->phi, dirs->phi + n);
+        for (int d = 0; d < n; ++d)
+            if (!std::isfinite(mu[d]) || !std::isfinite(phi[d]) || mu[d] < -1.0 || mu[d] > 1.0)
+                return fail(ctx, RTLB_E_RANGE, "direction %d: mu must be in [-1, 1] and finite", d);
+    } else {
+        direction_grid(dirs->n_zen, dirs->n_az, mu, phi);
+    }
+    cx.assign(n, 0);
+    cz.assign(n, 0);
+    for (int d = 0; d < n; ++d)
+        if (stream_offset(mu[d], phi[d], &cx[d], &cz[d]))
+            return fail(ctx, RTLB_E_AMBIGUOUS_STREAM,
+                        "direction %d (mu=%.17g, phi=%.17g) lies between two lattice offsets", d, mu[d], phi[d]);
+    return RTLB_OK;
+}
+
+void free_ctx_buffers(rtlb_ctx *c)
+{
+    cudaFree(c->S[0]);
+    cudaFree(c->S[1]);
+    cudaFree(c->d_dir);
+    cudaFree(c->d_inflow);
+    cudaFree(c->d_coef);
+    cudaFree(c->d_ZT);
+    cudaFree(c->d_scratch);
+    cudaFree(c->d_out);
+    cudaFree(c->d_flags);
+    cudaFree(c->d_stage);
+    cudaFree(c->d_rad);
+    cudaFreeHost(c->h_out);
+    cudaFreeHost(c->h_flags);
+    tc_release(c);
+}
+
+rtlb_status require_boundary_pairs(rtlb_ctx *c)
+{
+    if ((c->bc[RTLB_SIDE_TOP] == RTLB_BC_PERIODIC) != (c->bc[RTLB_SIDE_BOTTOM] == RTLB_BC_PERIODIC) ||
+        (c->bc[RTLB_SIDE_LEFT] == RTLB_BC_PERIODIC) != (c->bc[RTLB_SIDE_RIGHT] == RTLB_BC_PERIODIC))
+        return fail(c, RTLB_E_STATE, "periodic boundaries must be set on both sides of an axis");
+    return RTLB_OK;
+}
+
+rtlb_status ensure_stage(rtlb_ctx *c)
+{
+    if (!c->d_stage) CK(c, cudaMalloc(&c->d_stage, c->state_floats() * sizeof(float)), "staging buffer");
+    return RTLB_OK;
+}
+
+StepParams make_params(rtlb_ctx *c)
+{
+    StepParams p;
+    p.S = c->S[c->cur];
+    p.S_new = c->S[c->cur ^ 1];
+    p.coef = c->d_coef;
+    p.ZT = c->d_ZT;
+    p.dir = c->d_dir;
+    p.inflow = c->d_inflow;
+    p.nx = c->nx;
+    p.nz = c->nz;
+    p.n = c->n;
+    p.n_phase = c->n_phase;
+    for (int k = 0; k < 4; ++k) p.bc[k] = c->bc[k];
+    return p;
+}
+
+}  // namespace
+
+extern "C" {
+
+rtlb_status rtlb_create(const rtlb_grid *grid, const rtlb_directions *dirs, const rtlb_options *opts,
+                        rtlb_ctx **out)
+{
+    if (!out) return RTLB_E_ARG;
+    *out = nullptr;
+    if (!grid || !dirs) return RTLB_E_ARG;
+    if (grid->nx < 1 || grid->nz < 1 || grid->nx > 65535 || grid->nz > 65535) return RTLB_E_SHAPE;
+    rtlb_options o = opts ? *opts : rtlb_options{RTLB_PREC_FP32, RTLB_SURV_LINEAR, RTLB_ABS_BEER_LAMBERT};
+    if (o.precision < RTLB_PREC_FP32 || o.precision > RTLB_PREC_BF16X3 || o.survival < 0 || o.survival > 1 ||
+        o.absorption < 0 || o.absorption > 1)
+        return RTLB_E_ARG;
+    std::vector<double> mu, phi;
+    std::vector<int> cx, cz;
+    rtlb_status st = build_dirs(dirs, mu, phi, cx, cz, nullptr);
+    if (st != RTLB_OK) return st;
+
+    rtlb_ctx *c = new (std::nothrow) rtlb_ctx();
+    if (!c) return RTLB_E_OOM;
+    cudaGetDevice(&c->dev);
+    c->nx = grid->nx;
+    c->nz = grid->nz;
+    c->n_zen = dirs->n_zen;
+    c->n_az = dirs->n_az;
+    c->n = dirs->n_zen * dirs->n_az;
+    c->mu = mu;
+    c->phi = phi;
+    c->cx = cx;
+    c->cz = cz;
+    c->opt = o;
+    c->inflow.assign((size_t)4 * c->n * 4, 0.0f);
+    const size_t bytes = c->state_floats() * sizeof(float);
+    const int nblk = residual_blocks(c->state_floats());
+    c->scratch_len = nblk;
+    std::vector<int> dirbuf(2 * c->n);
+    for (int d = 0; d < c->n; ++d) {
+        dirbuf[d] = cx[d];
+        dirbuf[c->n + d] = cz[d];
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&c->S[0], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->S[1], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_dir, dirbuf.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_inflow, c->inflow.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_scratch, (size_t)3 * nblk * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_out, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_flags, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_out, 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_flags, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->S[0], 0, bytes);
+    if (e == cudaSuccess) e = cudaMemset(c->S[1], 0, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_dir, dirbuf.data(), dirbuf.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_inflow, c->inflow.data(), c->inflow.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        const rtlb_status s = e == cudaErrorMemoryAllocation ? RTLB_E_OOM : RTLB_E_CUDA;
+        free_ctx_buffers(c);
+        delete c;
+        cudaGetLastError();
+        return s;
+    }
+    *out = c;
+    return RTLB_OK;
+}
+
+void rtlb_destroy(rtlb_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    free_ctx_buffers(ctx);
+    delete ctx;
+}
+
+const char *rtlb_last_error(const rtlb_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t rtlb_steps_done(const rtlb_ctx *ctx) { return ctx ? ctx->steps : -1; }
+
+rtlb_status rtlb_set_medium(rtlb_ctx *c, const float *tau, const float *albedo, const float *emission,
+                            int32_t n_phase, const double *phase_tables, const uint8_t *phase_index,
+                            void *stream)
+{
+    if (!c) return RTLB_E_ARG;
+    if (!tau || !albedo || !phase_tables) return fail(c, RTLB_E_ARG, "tau, albedo and phase_tables are required");
+    if (n_phase < 1 || n_phase > kMaxPhase) return fail(c, RTLB_E_ARG, "n_phase must be in [1, %d]", kMaxPhase);
+    const int N4 = 4 * c->n;
+    const size_t tsz = (size_t)N4 * N4;
+    for (size_t j = 0; j < (size_t)n_phase * tsz; ++j)
+        if (!std::isfinite(phase_tables[j])) return fail(c, RTLB_E_NONFINITE, "phase table entry %zu is not finite", j);
+    const int ns = (int)c->nsites();
+    cudaStream_t s = S(stream);
+
+    // device copies of host inputs
+    float *tmp[3] = {nullptr, nullptr, nullptr};
+    uint8_t *tmp_cls = nullptr;
+    float4 *coef = nullptr;
+    float *ZT = nullptr;
+    auto cleanup = [&]() {
+        for (float *t : tmp) cudaFree(t);
+        cudaFree(tmp_cls);
+        cudaFree(coef);
+        cudaFree(ZT);
+    };
+    const float *in[3] = {tau, albedo, emission};
+    const float *dev_in[3] = {nullptr, nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        if (!in[k]) continue;
+        if (is_device_ptr(in[k])) {
+            dev_in[k] = in[k];
+        } else {
+            e = cudaMalloc(&tmp[k], ns * sizeof(float));
+            if (e == cudaSuccess) e = cudaMemcpyAsync(tmp[k], in[k], ns * sizeof(float), cudaMemcpyHostToDevice, s);
+            dev_in[k] = tmp[k];
+        }
+    }
+    const uint8_t *dev_cls = nullptr;
+    if (e == cudaSuccess && phase_index) {
+        if (is_device_ptr(phase_index)) {
+            dev_cls = phase_index;
+        } else {
+            e = cudaMalloc(&tmp_cls, ns);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(tmp_cls, phase_index, ns, cudaMemcpyHostToDevice, s);
+            dev_cls = tmp_cls;
+        }
+    }
+    std::vector<float> zt((size_t)n_phase * tsz);
+    for (int p = 0; p < n_phase; ++p)
+        for (int row = 0; row < N4; ++row)
+            for (int col = 0; col < N4; ++col)
+                zt[(size_t)p * tsz + (size_t)col * N4 + row] = (float)phase_tables[(size_t)p * tsz + (size_t)row * N4 + col];
+    if (e == cudaSuccess) e = cudaMalloc(&coef, (size_t)ns * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&ZT, zt.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ZT, zt.data(), zt.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_flags, 0, sizeof(int), s);
+    if (e == cudaSuccess)
+        e = launch_prep_medium(dev_in[0], dev_in[1], dev_in[2], dev_cls, coef, ns, n_phase, c->opt.survival,
+                               c->opt.absorption, c->d_flags, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_flags, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(c, e, "set_medium");
+    }
+    const int flags = c->h_flags[0];
+    if (flags) {
+        cleanup();
+        if (flags & 1) return fail(c, RTLB_E_NONFINITE, "medium contains NaN or Inf");
+        if (flags & 4) return fail(c, RTLB_E_RANGE, "phase_index >= n_phase");
+        return fail(c, RTLB_E_RANGE,
+                    "medium out of range: need tau >= 0, 0 <= albedo <= 1, emission >= 0, "
+                    "albedo*tau <= 1 (linear survival), (1-albedo)*tau <= 1 (Taylor absorption)");
+    }
+    rtlb_status tst = tc_prepare_tables(c, phase_tables, n_phase, s);
+    if (tst != RTLB_OK) {
+        cleanup();
+        return tst;
+    }
+    for (float *t : tmp) cudaFree(t);
+    cudaFree(tmp_cls);
+    cudaFree(c->d_coef);
+    cudaFree(c->d_ZT);
+    c->d_coef = coef;
+    c->d_ZT = ZT;
+    c->n_phase = n_phase;
+    c->medium_set = true;
+    return RTLB_OK;
+}
+
+rtlb_status rtlb_set_boundary(rtlb_ctx *c, int32_t side, int32_t kind, const float *inflow)
+{
+    if (!c) return RTLB_E_ARG;
+    if (side < 0 || side > 3) return fail(c, RTLB_E_ARG, "side must be 0..3");
+    if (kind < RTLB_BC_VACUUM || kind > RTLB_BC_INFLOW) return fail(c, RTLB_E_ARG, "bad boundary kind %d", kind);
+    if (kind == RTLB_BC_INFLOW && !inflow) return fail(c, RTLB_E_ARG, "INFLOW needs an inflow table");
+    std::vector<float> nv = c->inflow;
+    float *dst = &nv[(size_t)side * c->n * 4];
+    for (int j = 0; j < c->n * 4; ++j) {
+        const float v = (kind == RTLB_BC_INFLOW) ? inflow[j] : 0.0f;
+        if (!std::isfinite(v)) return fail(c, RTLB_E_NONFINITE, "inflow entry %d is not finite", j);
+        dst[j] = v;
+    }
+    CK(c, cudaDeviceSynchronize(), "set_boundary sync");
+    CK(c, cudaMemcpy(c->d_inflow, nv.data(), nv.size() * sizeof(float), cudaMemcpyHostToDevice), "inflow upload");
+    c->inflow.swap(nv);
+    c->bc[side] = kind;
+    return RTLB_OK;
+}
+
+rtlb_status rtlb_set_state(rtlb_ctx *c, const float *Sin, void *stream)
+{
+    if (!c || !Sin) return fail(c, RTLB_E_ARG, "null argument");
+    cudaStream_t s = S(stream);
+    const size_t bytes = c->state_floats() * sizeof(float);
+    const float *src = Sin;
+    if (!is_device_ptr(Sin)) {
+        rtlb_status st = ensure_stage(c);
+        if (st != RTLB_OK) return st;
+        CK(c, cudaMemcpyAsync(c->d_stage, Sin, bytes, cudaMemcpyHostToDevice, s), "state upload");
+        src = c->d_stage;
+    }
+    CK(c, launch_user_to_dm(src, c->S[c->cur], (int)c->nsites(), c->n, s), "state layout");
+    c->steps = 0;
+    c->has_prev = false;
+    return RTLB_OK;
+}
+
+rtlb_status rtlb_get_state(rtlb_ctx *c, float *Sout, void *stream)
+{
+    if (!c || !Sout) return fail(c, RTLB_E_ARG, "null argument");
+    cudaStream_t s = S(stream);
+    const size_t bytes = c->state_floats() * sizeof(float);
+    if (is_device_ptr(Sout)) {
+        CK(c, launch_dm_to_user(c->S[c->cur], Sout, (int)c->nsites(), c->n, s), "state layout");
+        return RTLB_OK;
+    }
+    rtlb_status st = ensure_stage(c);
+    if (st != RTLB_OK) return st;
+    CK(c, launch_dm_to_user(c->S[c->cur], c->d_stage, (int)c->nsites(), c->n, s), "state layout");
+    CK(c, cudaMemcpyAsync(Sout, c->d_stage, bytes, cudaMemcpyDeviceToHost, s), "state download");
+    CK(c, cudaStreamSynchronize(s), "state download sync");
+    return RTLB_OK;
+}
+
+rtlb_status rtlb_step(rtlb_ctx *c, int32_t nsteps, void *stream)
+{
+    if (!c) return RTLB_E_ARG;
+    if (nsteps < 0) return fail(c, RTLB_E_ARG, "nsteps must be >= 0");
+    if (!c->medium_set) return fail(c, RTLB_E_STATE, "rtlb_set_medium must come before rtlb_step");
+    rtlb_status st = require_boundary_pairs(c);
+    if (st != RTLB_OK) return st;
+    cudaStream_t s = S(stream);
+    for (int t = 0; t < nsteps; ++t) {
+        StepParams p = make_params(c);
+        cudaError_t e;
+        if (c->opt.precision == RTLB_PREC_FP32) {
+            e = launch_step_fp32(p, s);
+        } else {
+            st = tc_step(c, p, s);
+            if (st != RTLB_OK) return st;
+            e = cudaSuccess;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+        c->cur ^= 1;
+        c->has_prev = true;
+        ++c->steps;
+    }
+    return RTLB_OK;
+}
+
+static rtlb_status residual_now(rtlb_ctx *c, double *res, cudaStream_t s)
+{
+    CK(c, launch_residual(c->S[c->cur ^ 1], c->S[c->cur], c->state_floats(), c->d_scratch, c->scratch_len, c->d_out, s),
+       "residual");
+    CK(c, cudaMemcpyAsync(c->h_out, c->d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, s), "residual copy");
+    CK(c, cudaStreamSynchronize(s), "residual sync");
+    if (c->h_out[2] != 0.0) return fail(c, RTLB_E_NONFINITE, "state contains %.0f non-finite entries", c->h_out[2]);
+    *res = c->h_out[1] > 0.0 ? c->h_out[0] / c->h_out[1] : c->h_out[0];
+    return RTLB_OK;
+}
+
+rtlb_status rtlb_last_residual(rtlb_ctx *c, double *residual, void *stream)
+{
+    if (!c || !residual) return fail(c, RTLB_E_ARG, "null argument");
+    if (!c->has_prev) return fail(c, RTLB_E_STATE, "no step since the state was set");
+    return residual_now(c, residual, S(stream));
+}
+
+rtlb_status rtlb_run_to_steady(rtlb_ctx *c, double tol, int32_t max_steps, int32_t check_every,
+                               int32_t *steps_taken, double *residual, void *stream)
+{
+    if (!c || !steps_taken || !residual) return fail(c, RTLB_E_ARG, "null argument");
+    if (!(tol > 0.0) || max_steps < 1 || check_every < 1) return fail(c, RTLB_E_ARG, "need tol > 0, max_steps >= 1, check_every >= 1");
+    cudaStream_t s = S(stream);
+    int taken = 0;
+    double r = INFINITY;
+    while (taken < max_steps) {
+        const int k = (max_steps - taken) < check_every ? (max_steps - taken) : check_every;
+        rtlb_status st = rtlb_step(c, k, stream);
+        if (st != RTLB_OK) return st;
+        taken += k;
+        st = residual_now(c, &r, s);
+        if (st != RTLB_OK) {
+            *steps_taken = taken;
+            return st;
+        }
+        if (r < tol) break;
+    }
+    *steps_taken = taken;
+    *residual = r;
+    if (!(r < tol)) return fail(c, RTLB_E_NOT_CONVERGED, "residual %.3e after %d steps (tol %.3e)", r, taken, tol);
+    return RTLB_OK;
+}
+
+rtlb_status rtlb_radiance_out(rtlb_ctx *c, int32_t side, float *out, void *stream)
+{
+    if (!c || !out) return fail(c, RTLB_E_ARG, "null argument");
+    if (side < 0 || side > 3) return fail(c, RTLB_E_ARG, "side must be 0..3");
+    cudaStream_t s = S(stream);
+    const int len = (side == RTLB_SIDE_TOP || side == RTLB_SIDE_BOTTOM) ? c->nx : c->nz;
+    const size_t bytes = (size_t)len * c->n * 4 * sizeof(float);
+    if (is_device_ptr(out)) {
+        CK(c, launch_radiance_out(c->S[c->cur], out, c->nx, c->nz, c->n, c->d_dir, side, s), "radiance_out");
+        return RTLB_OK;
+    }
+    const size_t need = (size_t)(c->nx > c->nz ? c->nx : c->nz) * c->n * 4;
+    if (!c->d_rad) CK(c, cudaMalloc(&c->d_rad, need * sizeof(float)), "radiance staging");
+    CK(c, launch_radiance_out(c->S[c->cur], c->d_rad, c->nx, c->nz, c->n, c->d_dir, side, s), "radiance_out");
+    CK(c, cudaMemcpyAsync(out, c->d_rad, bytes, cudaMemcpyDeviceToHost, s), "radiance download");
+    CK(c, cudaStreamSynchronize(s), "radiance sync");
+    return RTLB_OK;
+}
+
+rtlb_status rtlb_total_intensity(rtlb_ctx *c, double *total, void *stream)
+{
+    if (!c || !total) return fail(c, RTLB_E_ARG, "null argument");
+    cudaStream_t s = S(stream);
+    CK(c, launch_total_I(c->S[c->cur], c->state_floats() / 4, c->d_scratch, c->scratch_len, c->d_out, s), "total I");
+    CK(c, cudaMemcpyAsync(c->h_out, c->d_out, sizeof(double), cudaMemcpyDeviceToHost, s), "total copy");
+    CK(c, cudaStreamSynchronize(s), "total sync");
+    *total = c->h_out[0];
+    return RTLB_OK;
+}
+
+rtlb_status rtlb_stream_offsets(const rtlb_directions *dirs, int32_t *cx, int32_t *cz)
+{
+    if (!cx || !cz) return RTLB_E_ARG;
+    std::vector<double> mu, phi;
+    std::vector<int> x, z;
+    rtlb_status st = build_dirs(dirs, mu, phi, x, z, nullptr);
+    if (st != RTLB_OK) return st;
+    for (size_t d = 0; d < x.size(); ++d) {
+        cx[d] = x[d];
+        cz[d] = z[d];
+    }
+    return RTLB_OK;
+}
+
+rtlb_status rtlb_phase_rayleigh(const rtlb_directions *dirs, double *Z_out)
+{
+    if (!Z_out) return RTLB_E_ARG;
+    std::vector<double> mu, phi;
+    std::vector<int> x, z;
+    rtlb_status st = build_dirs(dirs, mu, phi, x, z, nullptr);
+    if (st != RTLB_OK && st != RTLB_E_AMBIGUOUS_STREAM) return st;
+    phase_rayleigh(mu, phi, Z_out);
+    return RTLB_OK;
+}
+
+rtlb_status rtlb_phase_hg(const rtlb_directions *dirs, double g, double pol_amp, double *Z_out, double *dZdg_out)
+{
+    if (!Z_out) return RTLB_E_ARG;
+    if (!(g > -1.0 && g < 1.0) || !(std::fabs(pol_amp) <= 1.0)) return RTLB_E_RANGE;
+    std::vector<double> mu, phi;
+    std::vector<int> x, z;
+    rtlb_status st = build_dirs(dirs, mu, phi, x, z, nullptr);
+    if (st != RTLB_OK && st != RTLB_E_AMBIGUOUS_STREAM) return st;
+    phase_hg(mu, phi, g, pol_amp, Z_out, dZdg_out);
+    return RTLB_OK;
+}
+
+rtlb_status rtlb_phase_mix(const rtlb_directions *dirs, double m, double g, double pol_amp, double *Z_out)
+{
+    if (!Z_out) return RTLB_E_ARG;
+    if (!(m >= 0.0 && m <= 1.0) || !(g > -1.0 && g < 1.0) || !(std::fabs(pol_amp) <= 1.0)) return RTLB_E_RANGE;
+    std::vector<double> mu, phi;
+    std::vector<int> x, z;
+    rtlb_status st = build_dirs(dirs, mu, phi, x, z, nullptr);
+    if (st != RTLB_OK && st != RTLB_E_AMBIGUOUS_STREAM) return st;
+    const size_t len = 16 * mu.size() * mu.size();
+    std::vector<double> zr(len), zh(len);
+    phase_rayleigh(mu, phi, zr.data());
+    phase_hg(mu, phi, g, pol_amp, zh.data(), nullptr);
+    for (size_t j = 0; j < len; ++j) Z_out[j] = m * zr[j] + (1.0 - m) * zh[j];
+    return RTLB_OK;
+}
+
+}  // extern "C"

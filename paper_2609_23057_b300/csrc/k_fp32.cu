@@ -1,0 +1,265 @@
+// Fused collide+stream step, float32 on the CUDA cores.
+//
+// One step (Eq. 2 with the operator order of Sec. 2.1: emission, absorption,
+// scattering, streaming) for a tile of consecutive lattice sites:
+//   S~ = S + e (I of every direction)                         (Eq. 6/8)
+//   P  = alpha S~ + beta Z_c S~                                (absorption, Eq. 11)
+//   S_new(x + c_d, d) = P(x, d)                                (streaming)
+// The 4n x 4n contraction Z_c S~ is a small GEMM per tile (M = sites,
+// N = K = 4n), register-tiled 8 sites x 8 outputs per thread.  Streaming is a
+// push: every thread stores its post-collision Stokes vectors at the neighbour
+// site, and also writes the ghost value (zero or inflow) into its own entries
+// whose upstream cell lies outside a non-periodic side -- those entries have
+// no other writer.  The state is direction-major [d][site][4], so a warp's
+// loads of one direction are contiguous 16-byte vectors.
+#include "rtlb_internal.h"
+
+namespace rtlb {
+
+namespace {
+
+template <int N4>
+struct Cfg {
+    static constexpr int TS = 8;                         // sites per thread
+    static constexpr int CG = N4 / 8;                    // column groups (8 outputs each)
+    static constexpr int SG = 256 / CG;                  // site groups
+    static constexpr int SITES = SG * TS;                // sites per CTA
+    static constexpr int KC = 16;                        // k rows per B chunk
+    static constexpr size_t SMEM = (size_t)N4 * SITES * 4 + (size_t)KC * N4 * 4 + (size_t)SITES * 12;
+};
+
+__device__ __forceinline__ void site_xz(int site, int nx, int &x, int &z)
+{
+    z = site / nx;
+    x = site - z * nx;
+}
+
+// Where the post-collision vector of (x, z) in direction (cx, cz) lands;
+// false when it leaves through a non-periodic side.
+__device__ __forceinline__ bool push_target(const StepParams &p, int x, int z, int cx, int cz,
+                                            int &xt, int &zt)
+{
+    xt = x + cx;
+    zt = z + cz;
+    if (p.bc[RTLB_SIDE_LEFT] == RTLB_BC_PERIODIC) xt = xt < 0 ? xt + p.nx : (xt >= p.nx ? xt - p.nx : xt);
+    if (p.bc[RTLB_SIDE_TOP] == RTLB_BC_PERIODIC) zt = zt < 0 ? zt + p.nz : (zt >= p.nz ? zt - p.nz : zt);
+    return xt >= 0 && xt < p.nx && zt >= 0 && zt < p.nz;
+}
+
+// Ghost side feeding (x, z) in direction (cx, cz), or -1 when the upstream
+// cell is inside the lattice (after periodic wrap).  Corners belong to the
+// top / bottom side.
+__device__ __forceinline__ int ghost_side(const StepParams &p, int x, int z, int cx, int cz)
+{
+    int xs = x - cx, zs = z - cz;
+    if (p.bc[RTLB_SIDE_LEFT] == RTLB_BC_PERIODIC) xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
+    if (p.bc[RTLB_SIDE_TOP] == RTLB_BC_PERIODIC) zs = zs < 0 ? zs + p.nz : (zs >= p.nz ? zs - p.nz : zs);
+    if (zs >= p.nz) return RTLB_SIDE_TOP;
+    if (zs < 0) return RTLB_SIDE_BOTTOM;
+    if (xs < 0) return RTLB_SIDE_LEFT;
+    if (xs >= p.nx) return RTLB_SIDE_RIGHT;
+    return -1;
+}
+
+__device__ __forceinline__ float4 ghost_value(const StepParams &p, int side, int d)
+{
+    if (p.bc[side] == RTLB_BC_INFLOW)
+        return reinterpret_cast<const float4 *>(p.inflow)[side * p.n + d];
+    return make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ void store_out(const StepParams &p, int site, int d, float4 v)
+{
+    const size_t nsites = (size_t)p.nx * p.nz;
+    int x, z, xt, zt;
+    site_xz(site, p.nx, x, z);
+    const int cx = p.dir[d], cz = p.dir[p.n + d];
+    float4 *out = reinterpret_cast<float4 *>(p.S_new) + (size_t)d * nsites;
+    if (push_target(p, x, z, cx, cz, xt, zt)) out[(size_t)zt * p.nx + xt] = v;
+    const int side = ghost_side(p, x, z, cx, cz);
+    if (side >= 0) out[site] = ghost_value(p, side, d);
+}
+
+template <int N4>
+__global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
+{
+    using C = Cfg<N4>;
+    constexpr int TS = C::TS, SG = C::SG, SITES = C::SITES, KC = C::KC;
+    extern __shared__ __align__(16) float smem[];
+    float *As = smem;                        // [N4][SITES]   S~ (k-major)
+    float *Bs = As + N4 * SITES;             // [KC][N4]      Z^T chunk
+    float *s_alpha = Bs + KC * N4;           // [SITES]
+    float *s_beta = s_alpha + SITES;         // [SITES]
+    int *s_cls = reinterpret_cast<int *>(s_beta + SITES);
+    __shared__ unsigned s_mask;
+
+    const int n = p.n;
+    const int nsites = p.nx * p.nz;
+    const int site0 = blockIdx.x * SITES;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_mask = 0u;
+    __syncthreads();
+
+    // coefficients and classes of the tile
+    unsigned my_mask = 0u;
+    for (int s = tid; s < SITES; s += 256) {
+        const int site = site0 + s;
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (site < nsites) c = p.coef[site];
+        s_alpha[s] = c.x;
+        s_beta[s] = c.y;
+        const int cl = (int)c.w;
+        s_cls[s] = cl;
+        if (site < nsites) my_mask |= 1u << cl;
+    }
+    if (my_mask) atomicOr(&s_mask, my_mask);
+
+    // S~ tile, transposed to k-major; emission added to I (Eq. 6/8)
+    const float4 *S4 = reinterpret_cast<const float4 *>(p.S);
+    for (int idx = tid; idx < n * SITES; idx += 256) {
+        const int d = idx / SITES, s = idx - d * SITES;
+        const int site = site0 + s;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (site < nsites) {
+            v = S4[(size_t)d * nsites + site];
+            v.x += p.coef[site].z;
+        }
+        As[(4 * d + 0) * SITES + s] = v.x;
+        As[(4 * d + 1) * SITES + s] = v.y;
+        As[(4 * d + 2) * SITES + s] = v.z;
+        As[(4 * d + 3) * SITES + s] = v.w;
+    }
+    __syncthreads();
+
+    const int sg = tid % SG, cg = tid / SG;
+    const int sl = sg * TS;       // first local site of this thread
+    const int c0 = cg * 8;        // first output column of this thread
+    const unsigned mask = s_mask;
+    const bool mixed = (mask & (mask - 1u)) != 0u;
+
+    float acc[TS][8];
+#pragma unroll
+    for (int i = 0; i < TS; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+    for (int cl = 0; cl < p.n_phase; ++cl) {
+        if (!(mask & (1u << cl))) continue;
+        const float *Zc = p.ZT + (size_t)cl * N4 * N4;
+        float m[TS];
+#pragma unroll
+        for (int i = 0; i < TS; ++i) m[i] = (!mixed || s_cls[sl + i] == cl) ? 1.f : 0.f;
+        for (int k0 = 0; k0 < N4; k0 += KC) {
+            __syncthreads();
+            for (int idx = tid; idx < KC * N4 / 4; idx += 256)
+                reinterpret_cast<float4 *>(Bs)[idx] =
+                    reinterpret_cast<const float4 *>(Zc + (size_t)k0 * N4)[idx];
+            __syncthreads();
+#pragma unroll 4
+            for (int k = 0; k < KC; ++k) {
+                const float4 a0 = *reinterpret_cast<const float4 *>(&As[(k0 + k) * SITES + sl]);
+                const float4 a1 = *reinterpret_cast<const float4 *>(&As[(k0 + k) * SITES + sl + 4]);
+                const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[k * N4 + c0]);
+                const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[k * N4 + c0 + 4]);
+                float a[TS] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                if (mixed) {
+#pragma unroll
+                    for (int i = 0; i < TS; ++i) a[i] *= m[i];
+                }
+#pragma unroll
+                for (int i = 0; i < TS; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+            }
+        }
+    }
+
+    // epilogue: P = alpha S~ + beta Y, pushed to the neighbour
+#pragma unroll
+    for (int i = 0; i < TS; ++i) {
+        const int s = sl + i, site = site0 + s;
+        if (site >= nsites) continue;
+        const float al = s_alpha[s], be = s_beta[s];
+#pragma unroll
+        for (int jd = 0; jd < 2; ++jd) {
+            const int d = (c0 >> 2) + jd;
+            const int col = 4 * d;
+            float4 v;
+            v.x = fmaf(al, As[(col + 0) * SITES + s], be * acc[i][4 * jd + 0]);
+            v.y = fmaf(al, As[(col + 1) * SITES + s], be * acc[i][4 * jd + 1]);
+            v.z = fmaf(al, As[(col + 2) * SITES + s], be * acc[i][4 * jd + 2]);
+            v.w = fmaf(al, As[(col + 3) * SITES + s], be * acc[i][4 * jd + 3]);
+            store_out(p, site, d, v);
+        }
+    }
+}
+
+// Any n: one thread per (site, outgoing direction); Z^T read through the
+// read-only cache (the whole warp shares one direction and usually one class).
+__global__ void __launch_bounds__(128) k_step_fp32_generic(StepParams p)
+{
+    const int nsites = p.nx * p.nz;
+    const int site = blockIdx.x * blockDim.x + threadIdx.x;
+    const int o = blockIdx.y;
+    if (site >= nsites) return;
+    const int N4 = 4 * p.n;
+    const float4 cf = p.coef[site];
+    const float *Zc = p.ZT + (size_t)(int)cf.w * N4 * N4;
+    const float4 *S4 = reinterpret_cast<const float4 *>(p.S);
+    float y[4] = {0.f, 0.f, 0.f, 0.f};
+    float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int d = 0; d < p.n; ++d) {
+        float4 v = S4[(size_t)d * nsites + site];
+        v.x += cf.z;
+        if (d == o) own = v;
+        const float sv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) y[r] = fmaf(__ldg(&Zc[(size_t)(4 * d + k) * N4 + 4 * o + r]), sv[k], y[r]);
+    }
+    float4 v;
+    v.x = fmaf(cf.x, own.x, cf.y * y[0]);
+    v.y = fmaf(cf.x, own.y, cf.y * y[1]);
+    v.z = fmaf(cf.x, own.z, cf.y * y[2]);
+    v.w = fmaf(cf.x, own.w, cf.y * y[3]);
+    store_out(p, site, o, v);
+}
+
+template <int N4>
+cudaError_t launch_tiled(const StepParams &p, cudaStream_t s)
+{
+    using C = Cfg<N4>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_step_fp32_tiled<N4>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int nsites = p.nx * p.nz;
+    const int grid = (nsites + C::SITES - 1) / C::SITES;
+    k_step_fp32_tiled<N4><<<grid, 256, C::SMEM, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_step_fp32(const StepParams &p, cudaStream_t s)
+{
+    switch (4 * p.n) {
+    case 32: return launch_tiled<32>(p, s);
+    case 64: return launch_tiled<64>(p, s);
+    case 128: return launch_tiled<128>(p, s);
+    case 256: return launch_tiled<256>(p, s);
+    default: {
+        const int nsites = p.nx * p.nz;
+        dim3 grid((nsites + 127) / 128, p.n);
+        k_step_fp32_generic<<<grid, 128, 0, s>>>(p);
+        return cudaGetLastError();
+    }
+    }
+}
+
+}  // namespace rtlb

@@ -1,0 +1,88 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rtlb.h"
+
+namespace rtlb {
+
+// ---- host geometry / tables (phase.cpp) ----
+void direction_grid(int n_zen, int n_az, std::vector<double> &mu, std::vector<double> &phi);
+int stream_offset(double mu, double phi, int *cx, int *cz);  // 1 = tie
+void phase_rayleigh(const std::vector<double> &mu, const std::vector<double> &phi, double *Z);
+void phase_hg(const std::vector<double> &mu, const std::vector<double> &phi, double g,
+              double pol_amp, double *Z, double *dZdg);
+
+constexpr int kMaxPhase = 16;
+constexpr int kMaxDirs = 256;
+
+// Everything one step kernel needs, passed by value.
+struct StepParams {
+    const float *S;      // direction-major state [n][nsites][4], nsites = nx*nz
+    float *S_new;        // same layout, the other buffer
+    const float4 *coef;  // [nsites] {alpha, beta, emission, class (as float)}
+    const float *ZT;     // [n_phase][4n (k)][4n (col)] float32, Z transposed
+    const int *dir;      // [2n] cx then cz
+    const float *inflow; // [4 sides][n][4]
+    int nx, nz, n, n_phase;
+    int bc[4];           // top, bottom, left, right
+};
+
+// ---- kernels (launchers return the launch error) ----
+cudaError_t launch_user_to_dm(const float *user, float *dm, int nsites, int n, cudaStream_t s);
+cudaError_t launch_dm_to_user(const float *dm, float *user, int nsites, int n, cudaStream_t s);
+cudaError_t launch_prep_medium(const float *tau, const float *albedo, const float *emis,
+                               const uint8_t *cls, float4 *coef, int nsites, int n_phase,
+                               int surv_mode, int abs_mode, int *flags, cudaStream_t s);
+cudaError_t launch_step_fp32(const StepParams &p, cudaStream_t s);
+cudaError_t launch_residual(const float *a, const float *b, size_t count, double *partials,
+                            int nblocks, double *out2, cudaStream_t s);
+int residual_blocks(size_t count);
+cudaError_t launch_total_I(const float *dm, size_t nvec, double *partials, int nblocks,
+                           double *out, cudaStream_t s);
+cudaError_t launch_radiance_out(const float *dm, float *out, int nx, int nz, int n,
+                                const int *dir, int side, cudaStream_t s);
+cudaError_t launch_fill(float *p, size_t count, float v, cudaStream_t s);
+
+}  // namespace rtlb
+
+struct rtlb_ctx {
+    int dev = 0;
+    int nx = 0, nz = 0, n = 0, n_zen = 0, n_az = 0;
+    std::vector<double> mu, phi;
+    std::vector<int> cx, cz;
+    rtlb_options opt{};
+    int bc[4] = {0, 0, 0, 0};
+    std::vector<float> inflow;  // [4][n][4]
+
+    // device buffers
+    float *S[2] = {nullptr, nullptr};  // direction-major [n][nsites][4]
+    int cur = 0;
+    int *d_dir = nullptr;
+    float *d_inflow = nullptr;
+    float4 *d_coef = nullptr;
+    float *d_ZT = nullptr;
+    int n_phase = 0;
+    bool medium_set = false;
+    double *d_scratch = nullptr;  // reduction partials
+    int scratch_len = 0;
+    double *d_out = nullptr;      // small device results
+    int *d_flags = nullptr;
+    double *h_out = nullptr;      // pinned host results
+    int *h_flags = nullptr;
+    float *d_stage = nullptr;     // user-layout staging for host transfers
+    float *d_rad = nullptr;       // radiance_out staging for host transfers
+    void *tc = nullptr;           // tensor-core path state (tc.cu)
+
+    int64_t steps = 0;
+    bool has_prev = false;
+    std::string err;
+
+    size_t nsites() const { return (size_t)nx * nz; }
+    size_t state_floats() const { return nsites() * n * 4; }
+};

@@ -1,0 +1,218 @@
+"""Python face of librtlb: a thin wrapper that hands torch / numpy buffers to
+the C ABI.  torch is used for device memory and streams only; every step of
+the solver runs in the library's CUDA kernels."""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _lib
+from ._lib import Directions, Grid, Options, check, lib
+
+PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2}
+SURVIVAL = {"linear": 0, "exp": 1}
+ABSORPTION = {"beer_lambert": 0, "taylor": 1}
+SIDES = {"top": 0, "bottom": 1, "left": 2, "right": 3}
+BCS = {"vacuum": 0, "periodic": 1, "inflow": 2}
+
+
+def _dirs(n_zen: int, n_az: int, mu=None, phi=None):
+    d = Directions(n_zen, n_az, None, None)
+    keep = None
+    if mu is not None:
+        mu = np.ascontiguousarray(mu, np.float64)
+        phi = np.ascontiguousarray(phi, np.float64)
+        d.mu = mu.ctypes.data_as(C.POINTER(C.c_double))
+        d.phi = phi.ctypes.data_as(C.POINTER(C.c_double))
+        keep = (mu, phi)
+    return d, keep
+
+
+def stream_offsets(n_zen: int, n_az: int, mu=None, phi=None):
+    """(cx, cz) int32 arrays of the library's D2Q9 streaming offsets."""
+    n = n_zen * n_az
+    d, keep = _dirs(n_zen, n_az, mu, phi)
+    cx, cz = np.zeros(n, np.int32), np.zeros(n, np.int32)
+    check(lib().rtlb_stream_offsets(C.byref(d), cx.ctypes.data, cz.ctypes.data))
+    return cx, cz
+
+
+def phase_rayleigh(n_zen: int, n_az: int, mu=None, phi=None) -> np.ndarray:
+    n = n_zen * n_az
+    d, keep = _dirs(n_zen, n_az, mu, phi)
+    Z = np.zeros((4 * n, 4 * n))
+    check(lib().rtlb_phase_rayleigh(C.byref(d), Z.ctypes.data))
+    return Z
+
+
+def phase_hg(n_zen: int, n_az: int, g: float, pol_amp: float, mu=None, phi=None, with_dg=False):
+    n = n_zen * n_az
+    d, keep = _dirs(n_zen, n_az, mu, phi)
+    Z = np.zeros((4 * n, 4 * n))
+    dZ = np.zeros((4 * n, 4 * n)) if with_dg else None
+    check(lib().rtlb_phase_hg(C.byref(d), float(g), float(pol_amp), Z.ctypes.data,
+                              dZ.ctypes.data if with_dg else None))
+    return (Z, dZ) if with_dg else Z
+
+
+def phase_mix(n_zen: int, n_az: int, m: float, g: float, pol_amp: float, mu=None, phi=None):
+    n = n_zen * n_az
+    d, keep = _dirs(n_zen, n_az, mu, phi)
+    Z = np.zeros((4 * n, 4 * n))
+    check(lib().rtlb_phase_mix(C.byref(d), float(m), float(g), float(pol_amp), Z.ctypes.data))
+    return Z
+
+
+def phase_table_spec(n_zen: int, n_az: int, spec, mu=None, phi=None) -> np.ndarray:
+    """Library table for a phase-class spec: ("rayleigh",), ("hg", g, pol_amp),
+    ("mix", m, g, pol_amp)."""
+    if spec[0] == "rayleigh":
+        return phase_rayleigh(n_zen, n_az, mu, phi)
+    if spec[0] == "hg":
+        return phase_hg(n_zen, n_az, spec[1], spec[2], mu, phi)
+    if spec[0] == "mix":
+        return phase_mix(n_zen, n_az, spec[1], spec[2], spec[3], mu, phi)
+    raise ValueError(f"unknown phase spec {spec!r}")
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor (device or host) or numpy array; the
+    caller keeps the object alive for the duration of the call."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensor must be contiguous"
+        return a.data_ptr()
+    assert a.flags["C_CONTIGUOUS"], "array must be C-contiguous"
+    return a.ctypes.data
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Solver:
+    """One lattice, one medium, one state, on the current CUDA device."""
+
+    def __init__(self, nx: int, nz: int, n_zen: int, n_az: int, precision: str = "fp32",
+                 survival: str = "linear", absorption: str = "beer_lambert", mu=None, phi=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("librtlb needs a CUDA device")
+        self.nx, self.nz, self.n_zen, self.n_az = nx, nz, n_zen, n_az
+        self.n = n_zen * n_az
+        self.precision = precision
+        d, self._keep = _dirs(n_zen, n_az, mu, phi)
+        opts = Options(PRECISIONS[precision], SURVIVAL[survival], ABSORPTION[absorption])
+        ctx = C.c_void_p()
+        check(lib().rtlb_create(C.byref(Grid(nx, nz)), C.byref(d), C.byref(opts), C.byref(ctx)))
+        self._ctx = ctx
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_ctx", None):
+            lib().rtlb_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        check(st, self._ctx)
+
+    # -- configuration
+    def set_medium(self, tau, albedo, phase_tables, emission=None, phase_index=None, stream=None):
+        """tau, albedo, emission: [nz][nx] float32 (torch cuda/cpu or numpy);
+        phase_tables: float64 numpy [n_phase][4n][4n]; phase_index [nz][nx] uint8."""
+        tabs = np.ascontiguousarray(phase_tables, np.float64)
+        if tabs.ndim == 2:
+            tabs = tabs[None]
+        args = [tau, albedo, emission, phase_index]
+        conv = []
+        for a, dt in zip(args, [np.float32, np.float32, np.float32, np.uint8]):
+            if a is None or hasattr(a, "data_ptr"):
+                conv.append(a if a is None or a.is_contiguous() else a.contiguous())
+            else:
+                conv.append(np.ascontiguousarray(a, dt))
+        self._check(lib().rtlb_set_medium(self._ctx, _ptr(conv[0]), _ptr(conv[1]), _ptr(conv[2]),
+                                          tabs.shape[0], tabs.ctypes.data, _ptr(conv[3]),
+                                          _stream(stream)))
+
+    def set_boundary(self, side, kind, inflow=None):
+        side = SIDES[side] if isinstance(side, str) else int(side)
+        kind = BCS[kind] if isinstance(kind, str) else int(kind)
+        buf = None if inflow is None else np.ascontiguousarray(inflow, np.float32).reshape(self.n, 4)
+        self._check(lib().rtlb_set_boundary(self._ctx, side, kind, _ptr(buf)))
+
+    # -- state
+    def set_state(self, S, stream=None):
+        """S: [nz][nx][n][4] float32, a torch tensor (device or pinned host) or numpy."""
+        if not hasattr(S, "data_ptr"):
+            S = np.ascontiguousarray(S, np.float32)
+        self._check(lib().rtlb_set_state(self._ctx, _ptr(S), _stream(stream)))
+
+    def get_state(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.nz, self.nx, self.n, 4), dtype=torch.float32, device="cuda")
+        self._check(lib().rtlb_get_state(self._ctx, _ptr(out), _stream(stream)))
+        return out
+
+    # -- stepping
+    def step(self, nsteps: int = 1, stream=None):
+        self._check(lib().rtlb_step(self._ctx, int(nsteps), _stream(stream)))
+
+    def run_to_steady(self, tol: float, max_steps: int, check_every: int = 10, stream=None):
+        steps = C.c_int32()
+        res = C.c_double()
+        st = lib().rtlb_run_to_steady(self._ctx, float(tol), int(max_steps), int(check_every),
+                                      C.byref(steps), C.byref(res), _stream(stream))
+        if st not in (0, 9):
+            self._check(st)
+        return steps.value, res.value, st == 0
+
+    def last_residual(self, stream=None) -> float:
+        r = C.c_double()
+        self._check(lib().rtlb_last_residual(self._ctx, C.byref(r), _stream(stream)))
+        return r.value
+
+    def total_intensity(self, stream=None) -> float:
+        r = C.c_double()
+        self._check(lib().rtlb_total_intensity(self._ctx, C.byref(r), _stream(stream)))
+        return r.value
+
+    def radiance_out(self, side="top", out=None, stream=None):
+        import torch
+        side = SIDES[side] if isinstance(side, str) else int(side)
+        ln = self.nx if side in (0, 1) else self.nz
+        if out is None:
+            out = torch.empty((ln, self.n, 4), dtype=torch.float32, device="cuda")
+        self._check(lib().rtlb_radiance_out(self._ctx, side, _ptr(out), _stream(stream)))
+        return out
+
+    @property
+    def steps_done(self) -> int:
+        return int(lib().rtlb_steps_done(self._ctx))
+
+
+def solver_for(w, precision: str = "fp32") -> Solver:
+    """Solver set up for a workloads.Workload (medium, tables, boundaries)."""
+    surv = "exp" if w.surv_mode == 1 else "linear"
+    absm = "taylor" if w.abs_mode == 1 else "beer_lambert"
+    s = Solver(w.nx, w.nz, w.n_zen, w.n_az, precision=precision, survival=surv, absorption=absm)
+    tabs = np.stack([phase_table_spec(w.n_zen, w.n_az, sp) for sp in w.phase_specs])
+    s.set_medium(w.tau.astype(np.float32), w.albedo.astype(np.float32), tabs,
+                 emission=None if w.emission is None else w.emission.astype(np.float32),
+                 phase_index=w.phase_index)
+    for side in range(4):
+        inflow = None if w.inflow is None else w.inflow[side]
+        s.set_boundary(side, w.bc[side], inflow if w.bc[side] == 2 else None)
+    return s

@@ -86,15 +86,24 @@ def top_beam(n: int, direction: int = 0, stokes=(1.0, 0.0, 0.0, 0.0)) -> np.ndar
     return inflow
 
 
-def random_state(nz: int, nx: int, n: int, seed: int, scale: float = 1.0) -> np.ndarray:
-    """A physically realizable random Stokes field S[z][x][d][4]: I >= |(Q,U,V)|."""
+def random_state(nz: int, nx: int, n: int, seed: int, scale: float = 1.0,
+                 dtype=np.float64) -> np.ndarray:
+    """A physically realizable random Stokes field S[z][x][d][4]: I >= |(Q,U,V)|.
+    Values are float32-representable; ``dtype=np.float32`` skips the float64
+    temporaries for large lattices (same values)."""
     rng = np.random.default_rng(seed)
-    I = rng.uniform(0.1, 1.0, (nz, nx, n)) * scale
-    v = rng.standard_normal((nz, nx, n, 3))
-    v /= np.linalg.norm(v, axis=-1, keepdims=True)
-    p = rng.uniform(0.0, 1.0, (nz, nx, n))
-    S = np.concatenate([I[..., None], (I * p)[..., None] * v], axis=-1)
-    return _f32(S)
+    out = np.empty((nz, nx, n, 4), np.float32)
+    rows = max(1, (1 << 22) // max(1, nx * n))
+    for z0 in range(0, nz, rows):
+        z1 = min(nz, z0 + rows)
+        shp = (z1 - z0, nx, n)
+        I = rng.uniform(0.1, 1.0, shp).astype(np.float32) * np.float32(scale)
+        v = rng.standard_normal(shp + (3,), dtype=np.float32)
+        v /= np.linalg.norm(v, axis=-1, keepdims=True)
+        p = rng.uniform(0.0, 1.0, shp).astype(np.float32)
+        out[z0:z1, ..., 0] = I
+        out[z0:z1, ..., 1:] = (I * p * np.float32(0.999))[..., None] * v
+    return out if dtype == np.float32 else out.astype(dtype)
 
 
 def _gaussian_smooth(field: np.ndarray, sigma: float) -> np.ndarray:

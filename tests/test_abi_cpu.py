@@ -1,0 +1,91 @@
+"""CPU-only checks of the C-ABI library: it loads, exports every symbol that
+include/rtlb.h declares, and its host-side (float64) helpers -- streaming
+offsets and phase tables, written independently of the oracle -- agree with
+the oracle.  No GPU call is made here."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2609_23057_b300 import _lib
+from paper_2609_23057_b300 import solver as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(rtlb_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    L = _lib.lib()
+    declared = _declared_symbols()
+    assert declared, "no declarations found"
+    missing = [n for n in sorted(declared) if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(_lib.EXPORTS) <= declared
+
+
+@pytest.mark.parametrize("nzen,naz", [(2, 4), (4, 8), (8, 8), (3, 6), (1, 4), (5, 7)])
+def test_offsets_match_oracle(orc, nzen, naz):
+    mu, phi = orc.direction_grid(nzen, naz)
+    cx, cz = S.stream_offsets(nzen, naz)
+    ox, oz = orc.stream_offsets(mu, phi)
+    assert np.array_equal(cx, ox) and np.array_equal(cz, oz)
+
+
+def test_tie_is_rejected():
+    mu = np.array([np.sin(np.radians(22.5))])
+    with pytest.raises(_lib.RtlbError) as ei:
+        S.stream_offsets(1, 1, mu, np.array([0.0]))
+    assert ei.value.status == 4
+
+
+@pytest.mark.parametrize("nzen,naz", [(2, 4), (4, 8), (8, 8), (3, 6)])
+@pytest.mark.parametrize("spec", [("rayleigh",), ("hg", 0.85, -0.1), ("mix", 0.4, 0.6, -0.1)])
+def test_tables_match_oracle(orc, nzen, naz, spec):
+    mu, phi = orc.direction_grid(nzen, naz)
+    Zl = S.phase_table_spec(nzen, naz, spec)
+    Zo = orc.phase_table_spec(mu, phi, spec)
+    assert np.abs(Zl - Zo).max() <= 1e-14 * max(1.0, np.abs(Zo).max())
+
+
+def test_explicit_direction_lists(orc):
+    """Tables 1-2 use explicit azimuth / zenith sets (e.g. {0,120,240} deg)."""
+    mu = np.array([-0.5, -0.5, -0.5, 0.5, 0.5, 0.5])
+    phi = np.radians([0.0, 120.0, 240.0, 0.0, 120.0, 240.0])
+    Zl = S.phase_rayleigh(2, 3, mu, phi)
+    Zo = orc.phase_table(mu, phi)
+    assert np.abs(Zl - Zo).max() < 1e-15
+    cx, cz = S.stream_offsets(2, 3, mu, phi)
+    ox, oz = orc.stream_offsets(mu, phi)
+    assert np.array_equal(cx, ox) and np.array_equal(cz, oz)
+
+
+def test_hg_derivative_matches_central_difference():
+    """dZ/dg of the normalized HG table (used by the adjoint) against a
+    central difference of the table itself."""
+    Z, dZ = S.phase_hg(4, 8, 0.7, -0.1, with_dg=True)
+    h = 1e-5
+    fd = (S.phase_hg(4, 8, 0.7 + h, -0.1) - S.phase_hg(4, 8, 0.7 - h, -0.1)) / (2 * h)
+    assert np.abs(dZ - fd).max() < 1e-6 * max(1.0, np.abs(fd).max())
+
+
+def test_host_helper_argument_errors():
+    L = _lib.lib()
+    d = _lib.Directions(0, 4, None, None)
+    Z = np.zeros(16)
+    assert L.rtlb_phase_rayleigh(C.byref(d), Z.ctypes.data) == 2           # RTLB_E_SHAPE
+    d = _lib.Directions(2, 4, None, None)
+    assert L.rtlb_phase_hg(C.byref(d), 1.5, -0.1, Z.ctypes.data, None) == 3  # RTLB_E_RANGE
+    assert L.rtlb_phase_rayleigh(C.byref(d), None) == 1                     # RTLB_E_ARG
+    big = _lib.Directions(32, 16, None, None)
+    assert L.rtlb_stream_offsets(C.byref(big), Z.ctypes.data, Z.ctypes.data) == 2
