@@ -152,6 +152,31 @@ int64_t rtlb_steps_done(const rtlb_ctx *ctx);
 const char *rtlb_last_error(const rtlb_ctx *ctx);
 void rtlb_destroy(rtlb_ctx *ctx);
 
+/* ---- residual without allocation (the paper has no counterpart) ----
+ *
+ * Same float64 residual as rtlb_last_residual, for callers that must not
+ * allocate device memory: code running inside an allocator hook or a host
+ * callback (where cudaMalloc is not allowed), processes whose device memory
+ * pool is owned and capped by another framework, and latency-bound loops that
+ * must never enter the driver's allocator.  Instead of a scratch buffer this
+ * call uses a fixed 1.5 MiB array compiled into the library, which every GPU
+ * that loads the library holds until the process exits.
+ *
+ * S_old, S_new: device float32 arrays of `count` entries (any layout, compared
+ * elementwise), 16-byte aligned, count a multiple of 4.  out: device, 3
+ * doubles, 8-byte aligned: {max|S_new - S_old|, max|S_new|, number of
+ * non-finite entries of S_new}; the residual is out[0] / out[1].
+ * count > RTLB_NOALLOC_MAX_COUNT returns RTLB_E_SHAPE; bad pointers, alignment
+ * or count % 4 != 0 return RTLB_E_ARG.  Never calls cudaMalloc / cudaFree.
+ * The first call on a device (with that device current) looks up the array's
+ * device address once; make that first call before any stream capture.  All
+ * calls share the one array and each overwrites the slots it reads, so two
+ * calls that overlap on the GPU (different streams, no ordering) race.
+ * Stream-ordered on `stream`. */
+#define RTLB_NOALLOC_MAX_COUNT ((size_t)1 << 30)
+rtlb_status rtlb_residual_noalloc(const float *S_old, const float *S_new, size_t count,
+                                  double *out, void *stream);
+
 /* ---- host helpers (float64, no GPU needed) ---- */
 
 /* Per-direction D2Q9 offsets cx[n], cz[n] (host int32) of the grid. */
