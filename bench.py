@@ -160,6 +160,75 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _time_steps(torch, s, stream, steps):
+    """Per-launch CUDA-event times (ms) of `steps` single steps on `stream`."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for k in range(steps):
+        s.step(1)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    return [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)], ev[0].elapsed_time(ev[-1])
+
+
+def _measured_traffic(kernel, sites):
+    """DRAM bytes per launch from the committed ncu capture of `kernel`,
+    scaled to `sites`, or None when the kernel source changed since."""
+    import hashlib
+    try:
+        with open(os.path.join(HERE, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[kernel]
+    except (OSError, KeyError, ValueError):
+        return None
+    src = b"".join(open(os.path.join(HERE, "paper_2609_23057_b300", "csrc", fn), "rb").read()
+                   for fn in ("tc.cu", "step_common.cuh"))
+    if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"]:
+        return None
+    return (rec["dram_bytes_read"] + rec["dram_bytes_write"]) * sites / rec["captured_sites"]
+
+
+def _roofline(precision, n, sdu_per_launch, avg_launch_s, peaks, src):
+    if precision == "fp32":
+        flops = 32.0 * n * sdu_per_launch
+        smax = float(peaks.get("sm_max_mhz", 2032.0))
+        peak = 148 * 128 * 2 * smax * 1e6 / 1e12
+        ach = flops / avg_launch_s / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {smax:.0f} MHz"}
+    gbs = (32.0 + 16.0 / n) * sdu_per_launch / avg_launch_s / 1e9
+    peak = float(peaks["hbm_gbs"])
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "traffic": None, "peak_source": f"hbm_gbs of {src} MEASURED_PEAKS"}
+
+
+def accuracy(precisions, steps):
+    """Top-of-domain radiance error of each precision form against the FP64
+    oracle on the 256x256 crop [896,1152)^2 of the same medium, run for
+    `steps` steps from zero as its own problem."""
+    import torch
+    import oracle
+    from paper_2609_23057_b300.solver import solver_for
+    sys.path.insert(0, os.path.join(HERE, "tests"))
+    from _util import abs_err_dop, oracle_problem, rel_err_I
+    w = W.precision_crop(steps=steps)
+    P = oracle_problem(oracle, w)
+    ref = P.run(P.zero_state(), steps)
+    top_ref = P.radiance_out(ref, oracle.SIDE_TOP)
+    out = {"workload": "256x256 crop [896,1152)^2, n=64", "steps": steps,
+           "reference": "FP64 oracle", "metric": "top radiance: max |dI| / max(|I|, 1e-3 max|I|); |dDOP|"}
+    for prec in precisions:
+        s = solver_for(w, prec)
+        s.step(steps)
+        got = s.get_state().cpu().numpy().astype(np.float64)
+        s.close()
+        top = P.radiance_out(got, oracle.SIDE_TOP)
+        out[prec] = {"rel_err_I_top": rel_err_I(top, top_ref, floor_frac=1e-3),
+                     "abs_err_dop_top": abs_err_dop(top, top_ref, floor_frac=1e-3),
+                     "rel_err_I_state": rel_err_I(got, ref, floor_frac=1e-3)}
+        torch.cuda.synchronize()
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2609_23057_b300 import solver as SV
@@ -170,11 +239,14 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = W.precision(seed=1, steps=args.steps)
-    s = SV.solver_for(w, args.precision)
-    stream = torch.cuda.current_stream(dev)
+    if args.nx == 2048 and args.nz == 2048:
+        w = W.precision(seed=1, steps=args.steps)
+    else:
+        w = W.cloud(f"lattice{args.nx}x{args.nz}_n64", args.nx, args.nz, 8, 8, seed=1, steps=args.steps)
     n, sites = w.n, w.sites
     sdu_per_step = sites * n
+    stream = torch.cuda.current_stream(dev)
+    peaks, src = _peaks()
 
     def barrier():
         if ws > 1:
@@ -182,22 +254,29 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    # warm-up (also brings the state away from zero)
+    # comparison form first (float32 on the CUDA cores), then the headline form
+    compare = {}
+    if args.precision != "fp32" and not args.no_compare:
+        s32 = SV.solver_for(w, "fp32")
+        s32.step(3)
+        barrier()
+        per, tot = _time_steps(torch, s32, stream, max(3, args.steps // 5))
+        s32.close()
+        compare["fp32"] = {"value": ws * sdu_per_step * len(per) / (tot * 1e-3), "unit": UNIT,
+                           "ms_per_step": tot / len(per),
+                           "roofline": _roofline("fp32", n, sdu_per_step, statistics.mean(per) * 1e-3, peaks, src)}
+        del s32
+        torch.cuda.empty_cache()
+
+    s = SV.solver_for(w, args.precision)
     s.step(args.warmup)
     barrier()
-
     sampler = ClockSampler(local)
     sampler.start()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     barrier()
-    ev[0].record(stream)
-    for k in range(args.steps):
-        s.step(1)
-        ev[k + 1].record(stream)
+    per_launch, total_ms = _time_steps(torch, s, stream, args.steps)
     barrier()
     clocks = sampler.stop()
-    per_launch = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
     t_max = total_ms
     if ws > 1:
         import torch.distributed as dist
@@ -209,7 +288,7 @@ def run_ours(args):
     # end to end through the public API with host buffers: each step uploads
     # the state from pinned host memory, advances one step and reads the top
     # radiance back to the host.
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = 3
     host_state = torch.empty((w.nz, w.nx, n, 4), dtype=torch.float32, pin_memory=True)
     s.get_state(out=host_state)
     host_top = torch.empty((w.nx, n, 4), dtype=torch.float32, pin_memory=True)
@@ -223,44 +302,42 @@ def run_ours(args):
     e2e_dt = time.perf_counter() - t0
     e2e = {"value": ws * sdu_per_step * e2e_steps / e2e_dt, "unit": UNIT,
            "h2d_bytes_per_step": host_state.numel() * 4, "d2h_bytes_per_step": host_top.numel() * 4}
+    s.close()
+    del s, host_state
+    torch.cuda.empty_cache()
 
-    peaks, src = _peaks()
-    bytes_per_sdu = 32.0 + 16.0 / n
-    avg_launch_s = statistics.mean(per_launch) * 1e-3
-    if args.precision == "fp32":
-        flops = 32.0 * n * sdu_per_step
-        smax = float(peaks.get("sm_max_mhz", 2032.0))
-        peak = 148 * 128 * 2 * smax * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": flops / avg_launch_s / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "frac": flops / avg_launch_s / 1e12 / peak, "traffic": None,
-                "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {smax:.0f} MHz"}
-    else:
-        gbs = bytes_per_sdu * sdu_per_step / avg_launch_s / 1e9
-        peak = float(peaks["hbm_gbs"])
-        roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                "traffic": None, "peak_source": f"{src} hbm_gbs"}
-
+    roof = _roofline(args.precision, n, sdu_per_step, statistics.mean(per_launch) * 1e-3, peaks, src)
+    if args.precision != "fp32":
+        roof["traffic"] = _measured_traffic("k_step_tc", sites)
+        roof["traffic_note"] = "DRAM bytes per launch from profiles/traffic.json, scaled by sites"
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "bf16": "bf16 operands, f32 accumulate + f32 state",
-                      "bf16x3": "bf16 hi+lo operands, f32 accumulate + f32 state"}[args.precision],
+            "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.precision],
             "data": "synthetic",
             "config": {"workload": w.name, "nx": w.nx, "nz": w.nz, "n_dirs": n,
-                       "precision": args.precision, "sites": sites, "phase_classes": 2,
+                       "precision": args.precision,
+                       "arithmetic": {"fp32": "float32 FMA",
+                                      "bf16": "bf16 operands, float32 accumulate, float32 state",
+                                      "bf16x3": "bf16 hi+lo operands (3 MMAs), float32 accumulate"}[args.precision],
+                       "sites": sites, "phase_classes": 2,
                        "l2": "inputs larger than L2 (4.3 GB state per buffer)",
                        "parallelism": f"replicas{ws}" if ws > 1 else "single"},
             "roofline": roof,
             "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": clocks,
+            "compare": compare,
+            "adjoint_over_forward": None,
         }
+        if ws == 1 and args.accuracy_steps > 0:
+            precs = [args.precision] + (["fp32"] if args.precision != "fp32" else [])
+            line["accuracy"] = accuracy(precs, args.accuracy_steps)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.steps)
         print(json.dumps(line), flush=True)
-    s.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -272,8 +349,13 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x3"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x3"], default="bf16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the FP32 comparison form")
+    ap.add_argument("--nx", type=int, default=2048, help="lattice width (profiling of smaller cases)")
+    ap.add_argument("--nz", type=int, default=2048, help="lattice height (profiling of smaller cases)")
+    ap.add_argument("--accuracy-steps", type=int, default=200,
+                    help="steps of the 256x256 crop compared with the oracle (0 = skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

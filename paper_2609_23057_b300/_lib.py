@@ -9,7 +9,9 @@ import ctypes as C
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "librtlb.so")
+# RTLB_LIBRARY may point at another build of the same library (e.g. a variant
+# compiled with different tuning macros); the default is the in-tree build.
+LIB_PATH = os.environ.get("RTLB_LIBRARY") or os.path.join(_HERE, "librtlb.so")
 
 RTLB_OK = 0
 STATUS_NAMES = {

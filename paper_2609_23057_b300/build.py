@@ -31,8 +31,8 @@ def _headers_mtime():
     return max(os.path.getmtime(h) for h in hs)
 
 
-def _compile(src, force, extra):
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src, force, extra, build_dir=None):
+    obj = os.path.join(build_dir or BUILD, os.path.basename(src) + ".o")
     if (not force and os.path.exists(obj)
             and os.path.getmtime(obj) >= max(os.path.getmtime(src), _headers_mtime())):
         return obj
@@ -45,22 +45,25 @@ def _compile(src, force, extra):
     return obj
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    """Compile every CUDA / C++ source for sm_103a and link librtlb.so."""
-    os.makedirs(BUILD, exist_ok=True)
-    extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+def build(force: bool = False, verbose_ptxas: bool = False, defines=(), out=None) -> str:
+    """Compile every CUDA / C++ source for sm_103a and link librtlb.so (or
+    `out`, with extra -D `defines` in a build folder of its own)."""
+    lib_path = out or LIB
+    build_dir = BUILD if not defines else os.path.join(BUILD, "_".join(d.replace("=", "") for d in defines))
+    os.makedirs(build_dir, exist_ok=True)
+    extra = (["-Xptxas", "-v"] if verbose_ptxas else []) + [f"-D{d}" for d in defines]
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, force, extra), srcs))
-    if (force or not os.path.exists(LIB)
-            or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs)):
-        tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, force, extra, build_dir), srcs))
+    if (force or not os.path.exists(lib_path)
+            or os.path.getmtime(lib_path) < max(os.path.getmtime(o) for o in objs)):
+        tmp = lib_path + f".tmp{os.getpid()}"
         cmd = [NVCC, *ARCH, "-shared", "-cudart", "shared", "-Xlinker", "-rpath,/usr/local/cuda/lib64", "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

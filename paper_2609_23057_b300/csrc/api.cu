@@ -89,6 +89,7 @@ void free_ctx_buffers(rtlb_ctx *c)
     cudaFree(c->d_dir);
     cudaFree(c->d_inflow);
     cudaFree(c->d_coef);
+    cudaFree(c->d_cls);
     cudaFree(c->d_ZT);
     cudaFree(c->d_scratch);
     cudaFree(c->d_out);
@@ -120,6 +121,7 @@ StepParams make_params(rtlb_ctx *c)
     p.S = c->S[c->cur];
     p.S_new = c->S[c->cur ^ 1];
     p.coef = c->d_coef;
+    p.cls = c->d_cls;
     p.ZT = c->d_ZT;
     p.dir = c->d_dir;
     p.inflow = c->d_inflow;
@@ -150,6 +152,8 @@ rtlb_status rtlb_create(const rtlb_grid *grid, const rtlb_directions *dirs, cons
     std::vector<int> cx, cz;
     rtlb_status st = build_dirs(dirs, mu, phi, cx, cz, nullptr);
     if (st != RTLB_OK) return st;
+    if (o.precision != RTLB_PREC_FP32 && !tc_shape_ok(dirs->n_zen * dirs->n_az, o.precision == RTLB_PREC_BF16X3))
+        return RTLB_E_UNSUPPORTED;
 
     rtlb_ctx *c = new (std::nothrow) rtlb_ctx();
     if (!c) return RTLB_E_OOM;
@@ -229,11 +233,13 @@ rtlb_status rtlb_set_medium(rtlb_ctx *c, const float *tau, const float *albedo, 
     float *tmp[3] = {nullptr, nullptr, nullptr};
     uint8_t *tmp_cls = nullptr;
     float4 *coef = nullptr;
+    uint8_t *cls_dev = nullptr;
     float *ZT = nullptr;
     auto cleanup = [&]() {
         for (float *t : tmp) cudaFree(t);
         cudaFree(tmp_cls);
         cudaFree(coef);
+        cudaFree(cls_dev);
         cudaFree(ZT);
     };
     const float *in[3] = {tau, albedo, emission};
@@ -265,12 +271,13 @@ rtlb_status rtlb_set_medium(rtlb_ctx *c, const float *tau, const float *albedo, 
             for (int col = 0; col < N4; ++col)
                 zt[(size_t)p * tsz + (size_t)col * N4 + row] = (float)phase_tables[(size_t)p * tsz + (size_t)row * N4 + col];
     if (e == cudaSuccess) e = cudaMalloc(&coef, (size_t)ns * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&cls_dev, (size_t)ns);
     if (e == cudaSuccess) e = cudaMalloc(&ZT, zt.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpyAsync(ZT, zt.data(), zt.size() * sizeof(float), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_flags, 0, sizeof(int), s);
     if (e == cudaSuccess)
-        e = launch_prep_medium(dev_in[0], dev_in[1], dev_in[2], dev_cls, coef, ns, n_phase, c->opt.survival,
-                               c->opt.absorption, c->d_flags, s);
+        e = launch_prep_medium(dev_in[0], dev_in[1], dev_in[2], dev_cls, coef, cls_dev, ns, n_phase,
+                               c->opt.survival, c->opt.absorption, c->d_flags, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_flags, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
@@ -286,7 +293,7 @@ rtlb_status rtlb_set_medium(rtlb_ctx *c, const float *tau, const float *albedo, 
                     "medium out of range: need tau >= 0, 0 <= albedo <= 1, emission >= 0, "
                     "albedo*tau <= 1 (linear survival), (1-albedo)*tau <= 1 (Taylor absorption)");
     }
-    rtlb_status tst = tc_prepare_tables(c, phase_tables, n_phase, s);
+    rtlb_status tst = tc_prepare(c, phase_tables, n_phase, dev_cls, s);
     if (tst != RTLB_OK) {
         cleanup();
         return tst;
@@ -294,8 +301,10 @@ rtlb_status rtlb_set_medium(rtlb_ctx *c, const float *tau, const float *albedo, 
     for (float *t : tmp) cudaFree(t);
     cudaFree(tmp_cls);
     cudaFree(c->d_coef);
+    cudaFree(c->d_cls);
     cudaFree(c->d_ZT);
     c->d_coef = coef;
+    c->d_cls = cls_dev;
     c->d_ZT = ZT;
     c->n_phase = n_phase;
     c->medium_set = true;
@@ -354,7 +363,7 @@ rtlb_status rtlb_get_state(rtlb_ctx *c, float *Sout, void *stream)
     CK(c, launch_dm_to_user(c->S[c->cur], c->d_stage, (int)c->nsites(), c->n, s), "state layout");
     CK(c, cudaMemcpyAsync(Sout, c->d_stage, bytes, cudaMemcpyDeviceToHost, s), "state download");
     CK(c, cudaStreamSynchronize(s), "state download sync");
-    return RTLB_OK;
+    return tc_check_error(c, s);
 }
 
 rtlb_status rtlb_step(rtlb_ctx *c, int32_t nsteps, void *stream)
@@ -385,6 +394,10 @@ rtlb_status rtlb_step(rtlb_ctx *c, int32_t nsteps, void *stream)
 
 static rtlb_status residual_now(rtlb_ctx *c, double *res, cudaStream_t s)
 {
+    {
+        const rtlb_status te = tc_check_error(c, s);
+        if (te != RTLB_OK) return te;
+    }
     CK(c, launch_residual(c->S[c->cur ^ 1], c->S[c->cur], c->state_floats(), c->d_scratch, c->scratch_len, c->d_out, s),
        "residual");
     CK(c, cudaMemcpyAsync(c->h_out, c->d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, s), "residual copy");
@@ -453,6 +466,10 @@ rtlb_status rtlb_total_intensity(rtlb_ctx *c, double *total, void *stream)
     CK(c, launch_total_I(c->S[c->cur], c->state_floats() / 4, c->d_scratch, c->scratch_len, c->d_out, s), "total I");
     CK(c, cudaMemcpyAsync(c->h_out, c->d_out, sizeof(double), cudaMemcpyDeviceToHost, s), "total copy");
     CK(c, cudaStreamSynchronize(s), "total sync");
+    {
+        const rtlb_status te = tc_check_error(c, s);
+        if (te != RTLB_OK) return te;
+    }
     *total = c->h_out[0];
     return RTLB_OK;
 }

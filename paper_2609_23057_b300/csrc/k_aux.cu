@@ -46,32 +46,38 @@ __global__ void k_dm_to_user(const float4 *__restrict__ dm, float4 *__restrict__
 // Per-site step coefficients (emission e, absorption A, survival s):
 //   P = alpha * (S + e) + beta * Z (S + e),  alpha = A s,  beta = A (1 - s)
 // with A = exp(-(1-w) tau) or 1 - (1-w) tau and s = 1 - w tau or exp(-w tau).
+// Evaluated once per medium in float64 and stored as float32; alpha, which
+// multiplies the whole state every step, is kept as a hi + lo pair so that a
+// uniform layer does not turn its rounding into a per-step bias.
 __global__ void k_prep_medium(const float *__restrict__ tau, const float *__restrict__ albedo,
-                              const float *__restrict__ emis, const uint8_t *__restrict__ cls,
-                              float4 *__restrict__ coef, int nsites, int n_phase, int surv_mode,
-                              int abs_mode, int *__restrict__ flags)
+                              const float *__restrict__ emis, const uint8_t *__restrict__ cls_in,
+                              float4 *__restrict__ coef, uint8_t *__restrict__ cls_out, int nsites,
+                              int n_phase, int surv_mode, int abs_mode, int *__restrict__ flags)
 {
     int bad = 0;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nsites; j += gridDim.x * blockDim.x) {
         const float t = tau[j], w = albedo[j];
         const float e = emis ? emis[j] : 0.0f;
-        const int c = cls ? (int)cls[j] : 0;
+        const int c = cls_in ? (int)cls_in[j] : 0;
         if (!isfinite(t) || !isfinite(w) || !isfinite(e)) bad |= 1;
         if (!(t >= 0.0f) || !(w >= 0.0f) || !(w <= 1.0f) || !(e >= 0.0f)) bad |= 2;
         if (c >= n_phase) bad |= 4;
-        const float kabs = (1.0f - w) * t, ksca = w * t;
-        if (surv_mode == RTLB_SURV_LINEAR && ksca > 1.0f) bad |= 2;
-        if (abs_mode == RTLB_ABS_TAYLOR && kabs > 1.0f) bad |= 2;
-        const float A = (abs_mode == RTLB_ABS_TAYLOR) ? 1.0f - kabs : expf(-kabs);
-        float s, one_minus_s;
+        const double kabs = (1.0 - (double)w) * (double)t, ksca = (double)w * (double)t;
+        if (surv_mode == RTLB_SURV_LINEAR && ksca > 1.0) bad |= 2;
+        if (abs_mode == RTLB_ABS_TAYLOR && kabs > 1.0) bad |= 2;
+        const double A = (abs_mode == RTLB_ABS_TAYLOR) ? 1.0 - kabs : exp(-kabs);
+        double s, one_minus_s;
         if (surv_mode == RTLB_SURV_LINEAR) {
-            s = 1.0f - ksca;
+            s = 1.0 - ksca;
             one_minus_s = ksca;
         } else {
-            s = expf(-ksca);
-            one_minus_s = -expm1f(-ksca);
+            s = exp(-ksca);
+            one_minus_s = -expm1(-ksca);
         }
-        coef[j] = make_float4(A * s, A * one_minus_s, e, (float)c);
+        const double alpha = A * s;
+        const float a_hi = (float)alpha;
+        coef[j] = make_float4(a_hi, (float)(alpha - (double)a_hi), (float)(A * one_minus_s), e);
+        cls_out[j] = (uint8_t)(c < n_phase ? c : 0);
     }
     if (bad) atomicOr(flags, bad);
 }
@@ -250,10 +256,10 @@ cudaError_t launch_dm_to_user(const float *dm, float *user, int nsites, int n, c
 }
 
 cudaError_t launch_prep_medium(const float *tau, const float *albedo, const float *emis,
-                               const uint8_t *cls, float4 *coef, int nsites, int n_phase,
-                               int surv_mode, int abs_mode, int *flags, cudaStream_t s)
+                               const uint8_t *cls_in, float4 *coef, uint8_t *cls_out, int nsites,
+                               int n_phase, int surv_mode, int abs_mode, int *flags, cudaStream_t s)
 {
-    k_prep_medium<<<grid_for(nsites), kThreads, 0, s>>>(tau, albedo, emis, cls, coef, nsites,
+    k_prep_medium<<<grid_for(nsites), kThreads, 0, s>>>(tau, albedo, emis, cls_in, coef, cls_out, nsites,
                                                         n_phase, surv_mode, abs_mode, flags);
     return cudaGetLastError();
 }

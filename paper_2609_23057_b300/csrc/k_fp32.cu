@@ -13,6 +13,7 @@
 // no other writer.  The state is direction-major [d][site][4], so a warp's
 // loads of one direction are contiguous 16-byte vectors.
 #include "rtlb_internal.h"
+#include "step_common.cuh"
 
 namespace rtlb {
 
@@ -25,59 +26,12 @@ struct Cfg {
     static constexpr int SG = 256 / CG;                  // site groups
     static constexpr int SITES = SG * TS;                // sites per CTA
     static constexpr int KC = 16;                        // k rows per B chunk
-    static constexpr size_t SMEM = (size_t)N4 * SITES * 4 + (size_t)KC * N4 * 4 + (size_t)SITES * 12;
+    static constexpr size_t SMEM = (size_t)N4 * SITES * 4 + (size_t)KC * N4 * 4 + (size_t)SITES * 16;
 };
-
-__device__ __forceinline__ void site_xz(int site, int nx, int &x, int &z)
-{
-    z = site / nx;
-    x = site - z * nx;
-}
-
-// Where the post-collision vector of (x, z) in direction (cx, cz) lands;
-// false when it leaves through a non-periodic side.
-__device__ __forceinline__ bool push_target(const StepParams &p, int x, int z, int cx, int cz,
-                                            int &xt, int &zt)
-{
-    xt = x + cx;
-    zt = z + cz;
-    if (p.bc[RTLB_SIDE_LEFT] == RTLB_BC_PERIODIC) xt = xt < 0 ? xt + p.nx : (xt >= p.nx ? xt - p.nx : xt);
-    if (p.bc[RTLB_SIDE_TOP] == RTLB_BC_PERIODIC) zt = zt < 0 ? zt + p.nz : (zt >= p.nz ? zt - p.nz : zt);
-    return xt >= 0 && xt < p.nx && zt >= 0 && zt < p.nz;
-}
-
-// Ghost side feeding (x, z) in direction (cx, cz), or -1 when the upstream
-// cell is inside the lattice (after periodic wrap).  Corners belong to the
-// top / bottom side.
-__device__ __forceinline__ int ghost_side(const StepParams &p, int x, int z, int cx, int cz)
-{
-    int xs = x - cx, zs = z - cz;
-    if (p.bc[RTLB_SIDE_LEFT] == RTLB_BC_PERIODIC) xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
-    if (p.bc[RTLB_SIDE_TOP] == RTLB_BC_PERIODIC) zs = zs < 0 ? zs + p.nz : (zs >= p.nz ? zs - p.nz : zs);
-    if (zs >= p.nz) return RTLB_SIDE_TOP;
-    if (zs < 0) return RTLB_SIDE_BOTTOM;
-    if (xs < 0) return RTLB_SIDE_LEFT;
-    if (xs >= p.nx) return RTLB_SIDE_RIGHT;
-    return -1;
-}
-
-__device__ __forceinline__ float4 ghost_value(const StepParams &p, int side, int d)
-{
-    if (p.bc[side] == RTLB_BC_INFLOW)
-        return reinterpret_cast<const float4 *>(p.inflow)[side * p.n + d];
-    return make_float4(0.f, 0.f, 0.f, 0.f);
-}
 
 __device__ __forceinline__ void store_out(const StepParams &p, int site, int d, float4 v)
 {
-    const size_t nsites = (size_t)p.nx * p.nz;
-    int x, z, xt, zt;
-    site_xz(site, p.nx, x, z);
-    const int cx = p.dir[d], cz = p.dir[p.n + d];
-    float4 *out = reinterpret_cast<float4 *>(p.S_new) + (size_t)d * nsites;
-    if (push_target(p, x, z, cx, cz, xt, zt)) out[(size_t)zt * p.nx + xt] = v;
-    const int side = ghost_side(p, x, z, cx, cz);
-    if (side >= 0) out[site] = ghost_value(p, side, d);
+    push_store(p.dir, p.inflow, pack_bc(p.bc), p.S_new, p.nx, p.nz, p.n, site, d, v);
 }
 
 template <int N4>
@@ -88,14 +42,25 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
     extern __shared__ __align__(16) float smem[];
     float *As = smem;                        // [N4][SITES]   S~ (k-major)
     float *Bs = As + N4 * SITES;             // [KC][N4]      Z^T chunk
-    float *s_alpha = Bs + KC * N4;           // [SITES]
-    float *s_beta = s_alpha + SITES;         // [SITES]
+    float *s_alpha = Bs + KC * N4;           // [SITES]  alpha hi
+    float *s_alo = s_alpha + SITES;          // [SITES]  alpha lo
+    float *s_beta = s_alo + SITES;           // [SITES]
     int *s_cls = reinterpret_cast<int *>(s_beta + SITES);
     __shared__ unsigned s_mask;
 
     const int n = p.n;
-    const int nsites = p.nx * p.nz;
-    const int site0 = blockIdx.x * SITES;
+    int site0, nsites;
+    if (p.tile_list) {
+        // one CTA per slice of a listed tile of p.tile_span sites
+        const int per = p.tile_span > SITES ? p.tile_span / SITES : 1;
+        const int tile = p.tile_list[blockIdx.x / per];
+        site0 = tile * p.tile_span + (blockIdx.x % per) * SITES;
+        nsites = min(p.nx * p.nz, tile * p.tile_span + p.tile_span);
+    } else {
+        site0 = blockIdx.x * SITES;
+        nsites = p.nx * p.nz;
+    }
+    const int nsites_all = p.nx * p.nz;
     const int tid = threadIdx.x;
     if (tid == 0) s_mask = 0u;
     __syncthreads();
@@ -105,10 +70,14 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
     for (int s = tid; s < SITES; s += 256) {
         const int site = site0 + s;
         float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (site < nsites) c = p.coef[site];
+        int cl = 0;
+        if (site < nsites) {
+            c = p.coef[site];
+            cl = p.cls[site];
+        }
         s_alpha[s] = c.x;
-        s_beta[s] = c.y;
-        const int cl = (int)c.w;
+        s_alo[s] = c.y;
+        s_beta[s] = c.z;
         s_cls[s] = cl;
         if (site < nsites) my_mask |= 1u << cl;
     }
@@ -121,8 +90,8 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
         const int site = site0 + s;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (site < nsites) {
-            v = S4[(size_t)d * nsites + site];
-            v.x += p.coef[site].z;
+            v = S4[(size_t)d * nsites_all + site];
+            v.x += p.coef[site].w;
         }
         As[(4 * d + 0) * SITES + s] = v.x;
         As[(4 * d + 1) * SITES + s] = v.y;
@@ -180,17 +149,18 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
     for (int i = 0; i < TS; ++i) {
         const int s = sl + i, site = site0 + s;
         if (site >= nsites) continue;
-        const float al = s_alpha[s], be = s_beta[s];
+        const float al = s_alpha[s], alo = s_alo[s], be = s_beta[s];
 #pragma unroll
         for (int jd = 0; jd < 2; ++jd) {
             const int d = (c0 >> 2) + jd;
             const int col = 4 * d;
-            float4 v;
-            v.x = fmaf(al, As[(col + 0) * SITES + s], be * acc[i][4 * jd + 0]);
-            v.y = fmaf(al, As[(col + 1) * SITES + s], be * acc[i][4 * jd + 1]);
-            v.z = fmaf(al, As[(col + 2) * SITES + s], be * acc[i][4 * jd + 2]);
-            v.w = fmaf(al, As[(col + 3) * SITES + s], be * acc[i][4 * jd + 3]);
-            store_out(p, site, d, v);
+            float o[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float sv = As[(col + k) * SITES + s];
+                o[k] = fmaf(al, sv, fmaf(alo, sv, be * acc[i][4 * jd + k]));
+            }
+            store_out(p, site, d, make_float4(o[0], o[1], o[2], o[3]));
         }
     }
 }
@@ -205,13 +175,13 @@ __global__ void __launch_bounds__(128) k_step_fp32_generic(StepParams p)
     if (site >= nsites) return;
     const int N4 = 4 * p.n;
     const float4 cf = p.coef[site];
-    const float *Zc = p.ZT + (size_t)(int)cf.w * N4 * N4;
+    const float *Zc = p.ZT + (size_t)p.cls[site] * N4 * N4;
     const float4 *S4 = reinterpret_cast<const float4 *>(p.S);
     float y[4] = {0.f, 0.f, 0.f, 0.f};
     float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int d = 0; d < p.n; ++d) {
         float4 v = S4[(size_t)d * nsites + site];
-        v.x += cf.z;
+        v.x += cf.w;
         if (d == o) own = v;
         const float sv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -220,10 +190,10 @@ __global__ void __launch_bounds__(128) k_step_fp32_generic(StepParams p)
             for (int r = 0; r < 4; ++r) y[r] = fmaf(__ldg(&Zc[(size_t)(4 * d + k) * N4 + 4 * o + r]), sv[k], y[r]);
     }
     float4 v;
-    v.x = fmaf(cf.x, own.x, cf.y * y[0]);
-    v.y = fmaf(cf.x, own.y, cf.y * y[1]);
-    v.z = fmaf(cf.x, own.z, cf.y * y[2]);
-    v.w = fmaf(cf.x, own.w, cf.y * y[3]);
+    v.x = fmaf(cf.x, own.x, fmaf(cf.y, own.x, cf.z * y[0]));
+    v.y = fmaf(cf.x, own.y, fmaf(cf.y, own.y, cf.z * y[1]));
+    v.z = fmaf(cf.x, own.z, fmaf(cf.y, own.z, cf.z * y[2]));
+    v.w = fmaf(cf.x, own.w, fmaf(cf.y, own.w, cf.z * y[3]));
     store_out(p, site, o, v);
 }
 
@@ -238,8 +208,14 @@ cudaError_t launch_tiled(const StepParams &p, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int nsites = p.nx * p.nz;
-    const int grid = (nsites + C::SITES - 1) / C::SITES;
+    int grid;
+    if (p.tile_list) {
+        const int per = p.tile_span > C::SITES ? p.tile_span / C::SITES : 1;
+        grid = p.n_tiles * per;
+    } else {
+        grid = (p.nx * p.nz + C::SITES - 1) / C::SITES;
+    }
+    if (grid == 0) return cudaSuccess;
     k_step_fp32_tiled<N4><<<grid, 256, C::SMEM, s>>>(p);
     return cudaGetLastError();
 }

@@ -25,20 +25,24 @@ constexpr int kMaxDirs = 256;
 struct StepParams {
     const float *S;      // direction-major state [n][nsites][4], nsites = nx*nz
     float *S_new;        // same layout, the other buffer
-    const float4 *coef;  // [nsites] {alpha, beta, emission, class (as float)}
+    const float4 *coef;  // [nsites] {alpha_hi, alpha_lo, beta, emission}
+    const uint8_t *cls;  // [nsites] phase class
     const float *ZT;     // [n_phase][4n (k)][4n (col)] float32, Z transposed
     const int *dir;      // [2n] cx then cz
     const float *inflow; // [4 sides][n][4]
     int nx, nz, n, n_phase;
     int bc[4];           // top, bottom, left, right
+    // optional: restrict the step to listed tiles of tile_span sites
+    const int *tile_list = nullptr;
+    int n_tiles = 0, tile_span = 0;
 };
 
 // ---- kernels (launchers return the launch error) ----
 cudaError_t launch_user_to_dm(const float *user, float *dm, int nsites, int n, cudaStream_t s);
 cudaError_t launch_dm_to_user(const float *dm, float *user, int nsites, int n, cudaStream_t s);
 cudaError_t launch_prep_medium(const float *tau, const float *albedo, const float *emis,
-                               const uint8_t *cls, float4 *coef, int nsites, int n_phase,
-                               int surv_mode, int abs_mode, int *flags, cudaStream_t s);
+                               const uint8_t *cls_in, float4 *coef, uint8_t *cls_out, int nsites,
+                               int n_phase, int surv_mode, int abs_mode, int *flags, cudaStream_t s);
 cudaError_t launch_step_fp32(const StepParams &p, cudaStream_t s);
 cudaError_t launch_residual(const float *a, const float *b, size_t count, double *partials,
                             int nblocks, double *out2, cudaStream_t s);
@@ -66,6 +70,7 @@ struct rtlb_ctx {
     int *d_dir = nullptr;
     float *d_inflow = nullptr;
     float4 *d_coef = nullptr;
+    uint8_t *d_cls = nullptr;
     float *d_ZT = nullptr;
     int n_phase = 0;
     bool medium_set = false;

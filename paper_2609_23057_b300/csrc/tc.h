@@ -3,10 +3,19 @@
 #include "rtlb_internal.h"
 
 namespace rtlb {
-// Converts the float64 phase tables into the MMA operand tables (bf16, and the
-// low parts for the split form) when the context's precision needs them.
-rtlb_status tc_prepare_tables(rtlb_ctx *c, const double *tables, int n_phase, cudaStream_t s);
-// One step with the tensor-core kernel.
+// True when the tensor-core kernel handles n directions (n in {8,16,32,64};
+// the split form must also fit its operands in shared memory).
+bool tc_shape_ok(int n, bool split);
+// Builds the bf16 operand tables (and low parts for the split form) and the
+// per-tile class lists from the float64 tables and the device class array
+// (may be NULL = class 0).  No-op for the FP32 precision.
+rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uint8_t *dev_cls, cudaStream_t s);
+// One step: the tensor-core kernel over single-class tiles, the CUDA-core
+// kernel over tiles that mix phase classes.
 rtlb_status tc_step(rtlb_ctx *c, const StepParams &p, cudaStream_t s);
+// Reads (synchronizing `s`) and clears the device error flag of the
+// tensor-core kernel; RTLB_E_TIMEOUT when a bounded wait gave up.
+rtlb_status tc_check_error(rtlb_ctx *c, cudaStream_t s);
+int tc_mixed_tiles(const rtlb_ctx *c);
 void tc_release(rtlb_ctx *c);
 }  // namespace rtlb
