@@ -256,16 +256,17 @@ def run_ours(args):
 
     # comparison form first (float32 on the CUDA cores), then the headline form
     compare = {}
-    if args.precision != "fp32" and not args.no_compare:
-        s32 = SV.solver_for(w, "fp32")
-        s32.step(3)
+    others = [] if args.no_compare else [p for p in ("fp32", "bf16") if p != args.precision]
+    for prec in others:
+        sc = SV.solver_for(w, prec)
+        sc.step(3)
         barrier()
-        per, tot = _time_steps(torch, s32, stream, max(3, args.steps // 5))
-        s32.close()
-        compare["fp32"] = {"value": ws * sdu_per_step * len(per) / (tot * 1e-3), "unit": UNIT,
-                           "ms_per_step": tot / len(per),
-                           "roofline": _roofline("fp32", n, sdu_per_step, statistics.mean(per) * 1e-3, peaks, src)}
-        del s32
+        per, tot = _time_steps(torch, sc, stream, max(3, args.steps // (5 if prec == "fp32" else 1)))
+        sc.close()
+        compare[prec] = {"value": ws * sdu_per_step * len(per) / (tot * 1e-3), "unit": UNIT,
+                         "ms_per_step": tot / len(per),
+                         "roofline": _roofline(prec, n, sdu_per_step, statistics.mean(per) * 1e-3, peaks, src)}
+        del sc
         torch.cuda.empty_cache()
 
     s = SV.solver_for(w, args.precision)
@@ -308,19 +309,22 @@ def run_ours(args):
 
     roof = _roofline(args.precision, n, sdu_per_step, statistics.mean(per_launch) * 1e-3, peaks, src)
     if args.precision != "fp32":
-        roof["traffic"] = _measured_traffic("k_step_tc", sites)
+        kern = "k_step_tc_pair" if (args.precision == "bf16x2" and n == 64) else "k_step_tc"
+        roof["kernel"] = kern
+        roof["traffic"] = _measured_traffic(kern, sites)
         roof["traffic_note"] = "DRAM bytes per launch from profiles/traffic.json, scaled by sites"
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.precision],
+            "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x2": "bf16x2", "bf16x3": "bf16x3"}[args.precision],
             "data": "synthetic",
             "config": {"workload": w.name, "nx": w.nx, "nz": w.nz, "n_dirs": n,
                        "precision": args.precision,
                        "arithmetic": {"fp32": "float32 FMA",
                                       "bf16": "bf16 operands, float32 accumulate, float32 state",
+                                      "bf16x2": "bf16 state operand, bf16 hi+lo table (2 MMAs), float32 accumulate",
                                       "bf16x3": "bf16 hi+lo operands (3 MMAs), float32 accumulate"}[args.precision],
                        "sites": sites, "phase_classes": 2,
                        "l2": "inputs larger than L2 (4.3 GB state per buffer)",
@@ -333,7 +337,7 @@ def run_ours(args):
             "adjoint_over_forward": None,
         }
         if ws == 1 and args.accuracy_steps > 0:
-            precs = [args.precision] + (["fp32"] if args.precision != "fp32" else [])
+            precs = [args.precision] + [p for p in ("bf16", "fp32") if p != args.precision]
             line["accuracy"] = accuracy(precs, args.accuracy_steps)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.steps)
@@ -349,7 +353,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x3"], default="bf16")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x2", "bf16x3"], default="bf16x2",
+                    help="headline form; bf16x2 is the tensor-core form that meets 1e-3 on the crop")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the FP32 comparison form")
     ap.add_argument("--nx", type=int, default=2048, help="lattice width (profiling of smaller cases)")

@@ -52,11 +52,17 @@ typedef enum {
 typedef enum { RTLB_SIDE_TOP = 0, RTLB_SIDE_BOTTOM = 1, RTLB_SIDE_LEFT = 2, RTLB_SIDE_RIGHT = 3 } rtlb_side;
 typedef enum { RTLB_BC_VACUUM = 0, RTLB_BC_PERIODIC = 1, RTLB_BC_INFLOW = 2 } rtlb_bc;
 
-/* Arithmetic of the scattering contraction (the state is always float32):
+/* Arithmetic of the scattering contraction (the state is always float32; the
+ * unscattered and forward-scattered light are applied in float32 in every form):
  *  FP32     -- float32 FMA on the CUDA cores.
  *  BF16     -- tcgen05 tensor-core MMA, bf16 operands, float32 accumulation.
- *  BF16X3   -- tcgen05, operands split hi+lo in bf16, three MMAs per product. */
-typedef enum { RTLB_PREC_FP32 = 0, RTLB_PREC_BF16 = 1, RTLB_PREC_BF16X3 = 2 } rtlb_precision;
+ *  BF16X3   -- tcgen05, both operands split hi+lo in bf16, three MMAs
+ *              (n <= 32: the operands must fit one CTA's shared memory).
+ *  BF16X2   -- tcgen05, bf16 state operand and the phase table as bf16 hi+lo,
+ *              two MMAs (n = 64 runs on CTA pairs, each holding half the table).
+ * Tensor-core forms need n in {8, 16, 32, 64}; rtlb_create returns
+ * RTLB_E_UNSUPPORTED otherwise. */
+typedef enum { RTLB_PREC_FP32 = 0, RTLB_PREC_BF16 = 1, RTLB_PREC_BF16X3 = 2, RTLB_PREC_BF16X2 = 3 } rtlb_precision;
 
 /* Survival of unscattered light over one step: LINEAR = 1 - k_scat dt (Eq. 11
  * as printed), EXP = exp(-k_scat dt).  Absorption: BEER_LAMBERT =

@@ -145,14 +145,14 @@ rtlb_status rtlb_create(const rtlb_grid *grid, const rtlb_directions *dirs, cons
     if (!grid || !dirs) return RTLB_E_ARG;
     if (grid->nx < 1 || grid->nz < 1 || grid->nx > 65535 || grid->nz > 65535) return RTLB_E_SHAPE;
     rtlb_options o = opts ? *opts : rtlb_options{RTLB_PREC_FP32, RTLB_SURV_LINEAR, RTLB_ABS_BEER_LAMBERT};
-    if (o.precision < RTLB_PREC_FP32 || o.precision > RTLB_PREC_BF16X3 || o.survival < 0 || o.survival > 1 ||
+    if (o.precision < RTLB_PREC_FP32 || o.precision > RTLB_PREC_BF16X2 || o.survival < 0 || o.survival > 1 ||
         o.absorption < 0 || o.absorption > 1)
         return RTLB_E_ARG;
     std::vector<double> mu, phi;
     std::vector<int> cx, cz;
     rtlb_status st = build_dirs(dirs, mu, phi, cx, cz, nullptr);
     if (st != RTLB_OK) return st;
-    if (o.precision != RTLB_PREC_FP32 && !tc_shape_ok(dirs->n_zen * dirs->n_az, o.precision == RTLB_PREC_BF16X3))
+    if (o.precision != RTLB_PREC_FP32 && !tc_shape_ok(dirs->n_zen * dirs->n_az, o.precision))
         return RTLB_E_UNSUPPORTED;
 
     rtlb_ctx *c = new (std::nothrow) rtlb_ctx();

@@ -40,10 +40,13 @@
 
 #include "step_common.cuh"
 #include "tc.h"
+#include "tc_ptx.cuh"
 
 namespace rtlb {
 
 namespace {
+
+using namespace tcptx;
 
 constexpr int kTileM = 128;
 constexpr int kWarps = 14;
@@ -56,30 +59,17 @@ constexpr int kDirsPerStage = 8;                    // directions per state chun
 constexpr int kStageBytes = kDirsPerStage * kTileM * 16;
 constexpr int kHalfSites = 64;                      // sites per TMA box row (256 floats)
 constexpr int kSmemLimit = 232448;                  // max dynamic smem per block
-constexpr unsigned long long kTimeoutNs = 2000000000ull;
 
-// Memory-system policy of the streamed state (each byte is read once and
-// written once per step): how many tiles ahead the producer prefetches into
-// L2, whether the epilogue's stores are marked evict-first, and whether the
-// TMA loads of the state are marked evict-first.
-#ifndef RTLB_TC_PREFETCH_TILES
-#define RTLB_TC_PREFETCH_TILES 0
-#endif
-#ifndef RTLB_TC_STREAM_STORES
-#define RTLB_TC_STREAM_STORES 1
-#endif
-#ifndef RTLB_TC_LOAD_EVICT_FIRST
-#define RTLB_TC_LOAD_EVICT_FIRST 1
-#endif
 
 enum ErrCode { kErrTimeoutProducer = 1, kErrTimeoutConverter = 2, kErrTimeoutMma = 4, kErrTimeoutEpilogue = 8 };
 
 struct TcState {
     int N4 = 0, KP = 0, C = 0, n_phase = 0;
-    bool split = false;
+    int mode = 1;                    // 1 bf16, 2 bf16 + table lo, 3 hi+lo both
+    bool pair = false;               // CTA-pair kernel (table rows split over two CTAs)
     __nv_bfloat16 *d_Zhi = nullptr;  // [n_phase][N4][KP]
     __nv_bfloat16 *d_Zlo = nullptr;
-    int *d_pure = nullptr;           // tile | class << 24, sorted by class
+    int *d_pure = nullptr;           // tile | class << 24, sorted by class (pairs: 2 per entry)
     int n_pure = 0;
     int *d_mixed = nullptr;          // tile indices
     int n_mixed = 0;
@@ -94,181 +84,6 @@ struct TcState {
     size_t smem = 0;
 };
 
-// ------------------------------------------------------------ PTX wrappers
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Bounded wait on one mbarrier phase.  Returns false (after raising the CTA's
-// abort flag and recording `code`) when the wait times out or another role
-// has already aborted.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err, int code)
-{
-    if (mbar_try(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (unsigned it = 1;; ++it) {
-        if (mbar_try(bar, parity)) return true;
-        if ((it & 63u) == 0u) {
-            if (*abort_flag) return false;
-            if (global_ns() - t0 > kTimeoutNs) {
-                *abort_flag = 1;
-                atomicOr(err, code);
-                return false;
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1, int c2)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1)
-{
-#if RTLB_TC_LOAD_EVICT_FIRST
-    uint64_t policy;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "l"(policy)
-        : "memory");
-#else
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
-        : "memory");
-#endif
-}
-
-__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int c0, int c1)
-{
-    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(map)),
-                 "r"(c0), "r"(c1)
-                 : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols)
-{
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols) : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
-{
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-// D[tmem] (+)= A[smem] . B[smem]^T, bf16 inputs, f32 accumulate, M = 128.
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc, uint32_t accumulate)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float v[8])
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
-                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
-}
-
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (SBO), descriptor version 1.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;                 // LBO (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;       // SBO
-    d |= (uint64_t)1 << 46;                 // version
-    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
-    return d;
-}
-
-// Instruction descriptor: D f32, A/B bf16, both K-major, M = 128, N = n4.
-__host__ __device__ constexpr uint32_t idesc_bf16(int n4)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n4 >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
-{
-    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<const uint32_t *>(&h);
-}
-
 struct TcParams {
     const float4 *coef;  // {alpha_hi, alpha_lo, beta, emission}
     const int *dir;
@@ -282,13 +97,16 @@ struct TcParams {
     int *err;
 };
 
-template <bool SPLIT>
+// MODE 1: bf16 operands; 2: bf16 state operand, table as bf16 hi + lo (two
+// MMAs); 3: both operands hi + lo (three MMAs).
+template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     k_step_tc(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmZhi,
               const __grid_constant__ CUtensorMap tmZlo, TcParams p, int N4, int stages)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    constexpr bool ZLO = MODE >= 2, ALO = MODE == 3;
     const int C = (N4 + 63) / 64;                  // K chunks of 64
     const int n = p.n;
     const int nsites = p.nx * p.nz;
@@ -298,9 +116,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     uint8_t *sZ = smem;
     uint8_t *sZlo = sZ + C * z_chunk;
-    uint8_t *sA = sZlo + (SPLIT ? C * z_chunk : 0);
+    uint8_t *sA = sZlo + (ZLO ? C * z_chunk : 0);
     uint8_t *sAlo = sA + C * a_chunk;
-    uint8_t *sStage = sAlo + (SPLIT ? C * a_chunk : 0);
+    uint8_t *sStage = sAlo + (ALO ? C * a_chunk : 0);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sStage + (size_t)stages * kStageBytes);
     uint64_t *st_full = bars;
     uint64_t *st_empty = st_full + stages;
@@ -363,10 +181,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ok = mbar_wait(smem_u32(&acc_full[(i - 1) & 1]), ((i - 1) >> 1) & 1, abort_flag, p.err, kErrTimeoutProducer);
                     if (!ok) break;
                     const uint32_t zb = smem_u32(z_full);
-                    mbar_expect_tx(zb, (SPLIT ? 2u : 1u) * C * z_chunk);
+                    mbar_expect_tx(zb, (ZLO ? 2u : 1u) * C * z_chunk);
                     for (int c = 0; c < C; ++c) {
                         tma_load_3d(smem_u32(sZ + c * z_chunk), &tmZhi, zb, 64 * c, 0, cls);
-                        if (SPLIT) tma_load_3d(smem_u32(sZlo + c * z_chunk), &tmZlo, zb, 64 * c, 0, cls);
+                        if (ZLO) tma_load_3d(smem_u32(sZlo + c * z_chunk), &tmZlo, zb, 64 * c, 0, cls);
                     }
                     prev_cls = cls;
                 }
@@ -401,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == kMmaWarp) {
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(N4);
+            const uint32_t idesc = idesc_bf16(kTileM, N4);
             int prev_cls = -1;
             uint32_t zl = 0;
             bool ok = true;
@@ -424,10 +242,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int kk = 0; kk < ksteps; ++kk) {
                         const uint32_t ao = c * a_chunk + kk * 32, zo = c * z_chunk + kk * 32;
                         mma_bf16(d_tmem, sw128_desc(smem_u32(sA + ao)), sw128_desc(smem_u32(sZ + zo)), idesc, 1u);
-                        if (SPLIT) {
-                            mma_bf16(d_tmem, sw128_desc(smem_u32(sAlo + ao)), sw128_desc(smem_u32(sZ + zo)), idesc, 1u);
-                            mma_bf16(d_tmem, sw128_desc(smem_u32(sA + ao)), sw128_desc(smem_u32(sZlo + zo)), idesc, 1u);
-                        }
+                        if (ZLO) mma_bf16(d_tmem, sw128_desc(smem_u32(sA + ao)), sw128_desc(smem_u32(sZlo + zo)), idesc, 1u);
+                        if (ALO) mma_bf16(d_tmem, sw128_desc(smem_u32(sAlo + ao)), sw128_desc(smem_u32(sZ + zo)), idesc, 1u);
                     }
                     mma_commit(smem_u32(&a_empty[c]));
                 }
@@ -502,7 +318,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t gran = (uint32_t)((d & 15) >> 1);          // 16-byte granule in the row
                     const uint32_t off = c * a_chunk + r * 128u + ((gran ^ (uint32_t)(r & 7)) << 4);
                     *reinterpret_cast<uint4 *>(sA + off) = hi;
-                    if (SPLIT) {
+                    if (ALO) {
                         const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&hi);
                         uint4 lo;
                         uint32_t *lw = reinterpret_cast<uint32_t *>(&lo);
@@ -578,6 +394,295 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == kMmaWarp) tmem_dealloc(tmem, tcols);
 }
 
+// Split-table form (MODE 2) on a CTA pair (cluster of 2, cta_group::2) for
+// tables too large for one CTA's shared memory with their low parts (n = 64:
+// 2 x 128 KB).  CTA r of the pair processes its own 128-site tile (A rows,
+// TMEM init, epilogue exactly as above) and holds rows [r N/2, (r+1) N/2) of
+// the table's hi and lo parts.  The even CTA issues M = 256 MMAs that read A
+// from both CTAs and B halves from each; their commits are multicast to both
+// CTAs' barriers.  The odd CTA's converter reports a ready tile to the even
+// CTA with a remote mbarrier arrive, and its producer forwards the completion
+// of its half of the table the same way.
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    k_step_tc_pair(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmZhi,
+                   const __grid_constant__ CUtensorMap tmZlo, TcParams p, int N4, int stages)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int C = (N4 + 63) / 64;
+    const int NH = N4 / 2;                          // table rows held by this CTA
+    const int n = p.n;
+    const int nsites = p.nx * p.nz;
+    const int groups = n / kDirsPerStage;
+    const uint32_t z_chunk = (uint32_t)NH * 128u;
+    const uint32_t a_chunk = (uint32_t)kTileM * 128u;
+
+    uint8_t *sZ = smem;
+    uint8_t *sZlo = sZ + C * z_chunk;
+    uint8_t *sA = sZlo + C * z_chunk;
+    uint8_t *sStage = sA + C * a_chunk;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sStage + (size_t)stages * kStageBytes);
+    uint64_t *st_full = bars;
+    uint64_t *st_empty = st_full + stages;
+    uint64_t *a_empty = st_empty + stages;     // [C]   multicast commit from the even CTA
+    uint64_t *t_ready = a_empty + C;           // [2]   used in the even CTA: 8 converter warps
+    uint64_t *acc_full = t_ready + 2;          // [2]   multicast commit
+    uint64_t *acc_empty = acc_full + 2;        // [2]   local epilogue warps
+    uint64_t *z_full = acc_empty + 2;          // [1]   even CTA: own TMA + odd CTA's forward
+    uint64_t *drain = z_full + 1;              // [1]   multicast commit
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    int8_t *s_cx = reinterpret_cast<int8_t *>(tmem_slot + 2);
+    int8_t *s_cz = s_cx + kMaxDirs;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t tcols = 512;                 // two N4 = 256 accumulators
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(smem_u32(&st_full[s]), 1);
+            mbar_init(smem_u32(&st_empty[s]), 4);
+        }
+        for (int c = 0; c < C; ++c) mbar_init(smem_u32(&a_empty[c]), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&t_ready[b]), 8);
+            mbar_init(smem_u32(&acc_full[b]), 1);
+            mbar_init(smem_u32(&acc_empty[b]), kEpiWarps);
+        }
+        mbar_init(smem_u32(z_full), leader ? 2 : 1);
+        mbar_init(smem_u32(drain), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int d = threadIdx.x; d < n; d += blockDim.x) {
+        s_cx[d] = (int8_t)p.dir[d];
+        s_cz[d] = (int8_t)p.dir[n + d];
+    }
+    if (warp == kMmaWarp) tmem_alloc_pair(smem_u32(tmem_slot), tcols);
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();                             // barriers of both CTAs initialized
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int ncl = (int)cluster_nclusters_x(), cid = (int)cluster_id_x();
+    const int t_begin = (int)((long long)p.n_tiles * cid / ncl);
+    const int t_end = (int)((long long)p.n_tiles * (cid + 1) / ncl);
+    const int T = t_end - t_begin;
+    // pair entries: tile_a | class << 24 at 2k, tile_b at 2k + 1
+    auto my_tile = [&](int i) { return p.tiles[2 * (t_begin + i) + (int)rank] & 0xFFFFFF; };
+    auto pair_cls = [&](int i) { return p.tiles[2 * (t_begin + i)] >> 24; };
+
+    if (warp == kProdWarp) {
+        if (lane == 0) {
+            int prev_cls = -1;
+            uint32_t g = 0, zl = 0;
+            bool ok = true;
+            for (int i = 0; i < T && ok; ++i) {
+                const int tile = my_tile(i), cls = pair_cls(i);
+                if (cls != prev_cls) {
+                    if (i > 0)
+                        ok = mbar_wait(smem_u32(&acc_full[(i - 1) & 1]), ((i - 1) >> 1) & 1, abort_flag, p.err, kErrTimeoutProducer);
+                    if (!ok) break;
+                    const uint32_t zb = smem_u32(z_full);
+                    mbar_expect_tx(zb, 2u * C * z_chunk);
+                    for (int c = 0; c < C; ++c) {
+                        tma_load_3d(smem_u32(sZ + c * z_chunk), &tmZhi, zb, 64 * c, NH * (int)rank, cls);
+                        tma_load_3d(smem_u32(sZlo + c * z_chunk), &tmZlo, zb, 64 * c, NH * (int)rank, cls);
+                    }
+                    if (!leader) {
+                        // forward the completion of this half to the even CTA
+                        ok = mbar_wait(zb, zl & 1, abort_flag, p.err, kErrTimeoutProducer);
+                        if (!ok) break;
+                        mbar_arrive_cluster(mapa(zb, 0));
+                    }
+                    ++zl;
+                    prev_cls = cls;
+                }
+                for (int j = 0; j < groups && ok; ++j, ++g) {
+                    const int s = g % stages;
+                    ok = mbar_wait(smem_u32(&st_empty[s]), ((g / stages) & 1) ^ 1, abort_flag, p.err, kErrTimeoutProducer);
+                    if (!ok) break;
+                    const uint32_t fb = smem_u32(&st_full[s]);
+                    mbar_expect_tx(fb, kStageBytes);
+                    for (int h = 0; h < kTileM / kHalfSites; ++h)
+                        tma_load_2d(smem_u32(sStage + (size_t)s * kStageBytes + h * (kStageBytes / 2)), &tmS, fb,
+                                    4 * (tile * kTileM + h * kHalfSites), j * kDirsPerStage);
+                }
+            }
+            for (uint32_t k = 0; k < (uint32_t)stages && k < g; ++k) {
+                const uint32_t gg = g - 1 - k;
+                const int s = gg % stages;
+                unsigned long long t0 = global_ns();
+                while (!mbar_try(smem_u32(&st_full[s]), (gg / stages) & 1) && global_ns() - t0 < kTimeoutNs) {
+                }
+            }
+        }
+    } else if (warp == kMmaWarp) {
+        if (lane == 0 && leader) {
+            const uint32_t idesc = idesc_bf16(2 * kTileM, N4);
+            int prev_cls = -1;
+            uint32_t zl = 0;
+            bool ok = true, issued = false;
+            for (int i = 0; i < T && ok; ++i) {
+                const int cls = pair_cls(i);
+                const int b = i & 1;
+                if (cls != prev_cls) {
+                    ok = mbar_wait_cluster(smem_u32(z_full), zl & 1, abort_flag, p.err, kErrTimeoutMma);
+                    ++zl;
+                    prev_cls = cls;
+                    if (!ok) break;
+                }
+                ok = mbar_wait_cluster(smem_u32(&t_ready[b]), (i >> 1) & 1, abort_flag, p.err, kErrTimeoutMma);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(b * N4);
+                for (int c = 0; c < C; ++c) {
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t ao = c * a_chunk + kk * 32, zo = c * z_chunk + kk * 32;
+                        const uint64_t ad = sw128_desc(smem_u32(sA + ao));
+                        mma_bf16_pair(d_tmem, ad, sw128_desc(smem_u32(sZ + zo)), idesc, 1u);
+                        mma_bf16_pair(d_tmem, ad, sw128_desc(smem_u32(sZlo + zo)), idesc, 1u);
+                    }
+                    mma_commit_pair(smem_u32(&a_empty[c]), 0x3);
+                }
+                mma_commit_pair(smem_u32(&acc_full[b]), 0x3);
+                issued = true;
+            }
+            if (issued) mma_commit_pair(smem_u32(drain), 0x3);
+        }
+        __syncwarp();
+    } else if (warp >= kConvWarp0) {
+        const int q = warp & 3;
+        const int r = q * 32 + lane;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        const int half = r / kHalfSites, hr = r % kHalfSites;
+        const uint32_t t_ready_leader0 = mapa(smem_u32(&t_ready[0]), 0);
+        const uint32_t t_ready_leader1 = mapa(smem_u32(&t_ready[1]), 0);
+        uint32_t g = 0;
+        bool ok = true;
+        for (int i = 0; i < T && ok; ++i) {
+            const int tile = my_tile(i);
+            const float *fwd = p.fwd + (size_t)pair_cls(i) * n;
+            const int b = i & 1;
+            const int site = tile * kTileM + r;
+            float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (site < nsites) cf = p.coef[site];
+            ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_empty[b]), ((i >> 1) & 1) ^ 1, abort_flag, p.err,
+                                                   kErrTimeoutConverter));
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t acc = tmem + lane_base + (uint32_t)(b * N4);
+            for (int j = 0; j < groups && ok; ++j, ++g) {
+                const int s = g % stages;
+                ok = __all_sync(0xffffffffu,
+                                mbar_wait(smem_u32(&st_full[s]), (g / stages) & 1, abort_flag, p.err, kErrTimeoutConverter));
+                if (!ok) break;
+                const float4 *stg = reinterpret_cast<const float4 *>(sStage + (size_t)s * kStageBytes) +
+                                    half * (kDirsPerStage * kHalfSites) + hr;
+#pragma unroll
+                for (int dl = 0; dl < kDirsPerStage; dl += 2) {
+                    const int d = j * kDirsPerStage + dl;
+                    const int c = d >> 4;
+                    if ((d & 15) == 0) {
+                        ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&a_empty[c]), (i & 1) ^ 1, abort_flag, p.err,
+                                                               kErrTimeoutConverter));
+                        if (!ok) break;
+                    }
+                    float4 v0 = stg[dl * kHalfSites], v1 = stg[(dl + 1) * kHalfSites];
+                    v0.x += cf.w;
+                    v1.x += cf.w;
+                    const float sv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                    const float g0 = fmaf(cf.z, __ldg(&fwd[d]), cf.y), g1 = fmaf(cf.z, __ldg(&fwd[d + 1]), cf.y);
+                    float init[8], bs[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        init[k] = fmaf(cf.x, sv[k], (k < 4 ? g0 : g1) * sv[k]);
+                        bs[k] = cf.z * sv[k];
+                    }
+                    tmem_st8(acc + 4 * d, init);
+                    uint4 hi;
+                    hi.x = pack_bf16(bs[0], bs[1]);
+                    hi.y = pack_bf16(bs[2], bs[3]);
+                    hi.z = pack_bf16(bs[4], bs[5]);
+                    hi.w = pack_bf16(bs[6], bs[7]);
+                    const uint32_t gran = (uint32_t)((d & 15) >> 1);
+                    const uint32_t off = c * a_chunk + r * 128u + ((gran ^ (uint32_t)(r & 7)) << 4);
+                    *reinterpret_cast<uint4 *>(sA + off) = hi;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&st_empty[s]));
+            }
+            if (!ok) break;
+            tmem_wait_st();
+            fence_proxy_async();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(b ? t_ready_leader1 : t_ready_leader0);
+        }
+    } else {
+        const int q = warp & 3;
+        const int dhalf = warp >> 2;
+        const int r = q * 32 + lane;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        const int dn = n / 2, dbeg = dhalf * dn;
+        float4 *out = reinterpret_cast<float4 *>(p.S_new);
+        bool ok = true;
+        for (int i = 0; i < T && ok; ++i) {
+            const int tile = my_tile(i);
+            const int b = i & 1;
+            const int site = tile * kTileM + r;
+            const int z = site / p.nx, x = site - z * p.nx;
+            const bool interior = site < nsites && x > 0 && x < p.nx - 1 && z > 0 && z < p.nz - 1;
+            ok = __all_sync(0xffffffffu,
+                            mbar_wait(smem_u32(&acc_full[b]), (i >> 1) & 1, abort_flag, p.err, kErrTimeoutEpilogue));
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t acc = tmem + lane_base + (uint32_t)(b * N4);
+            for (int d0 = dbeg; d0 < dbeg + dn; d0 += 4) {
+                float v[16];
+                tmem_ld16(acc + 4 * d0, v);
+                if (interior) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int d = d0 + k;
+                        const long long t = (long long)d * nsites + site + s_cx[d] + (long long)s_cz[d] * p.nx;
+                        const float4 val = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+#if RTLB_TC_STREAM_STORES
+                        __stcs(&out[t], val);
+#else
+                        out[t] = val;
+#endif
+                    }
+                } else if (site < nsites) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        push_store(p.dir, p.inflow, p.bcbits, p.S_new, p.nx, p.nz, n, site, d0 + k,
+                                   make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
+        }
+    }
+
+    // every MMA issued into this CTA's TMEM has completed (bounded wait), then
+    // both CTAs leave together and free the pair's TMEM
+    if (warp == kMmaWarp && lane == 0 && T > 0) {
+        unsigned long long t0 = global_ns();
+        while (!mbar_try_cluster(smem_u32(drain), 0) && global_ns() - t0 < kTimeoutNs && !*abort_flag) {
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    tc_fence_after();
+    if (warp == kMmaWarp) tmem_dealloc_pair(tmem, tcols);
+}
+
 // ------------------------------------------------------------------ host side
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -607,13 +712,13 @@ bool encode_state_map(CUtensorMap *m, const float *S, size_t nsites, int n)
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool encode_z_map(CUtensorMap *m, const __nv_bfloat16 *Z, int N4, int KP, int n_phase)
+bool encode_z_map(CUtensorMap *m, const __nv_bfloat16 *Z, int N4, int KP, int n_phase, int box_rows)
 {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {(cuuint64_t)KP, (cuuint64_t)N4, (cuuint64_t)n_phase};
     cuuint64_t strides[2] = {(cuuint64_t)KP * 2, (cuuint64_t)N4 * KP * 2};
-    cuuint32_t box[3] = {64, (cuuint32_t)N4, 1};
+    cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(Z), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -635,43 +740,64 @@ void free_tables(TcState *t)
     t->n_pure = t->n_mixed = 0;
 }
 
-size_t smem_bytes(int N4, bool split, int stages)
+size_t smem_bytes(int N4, int mode, int stages)
 {
     const int C = (N4 + 63) / 64;
-    size_t b = (size_t)C * N4 * 128 * (split ? 2 : 1) + (size_t)C * kTileM * 128 * (split ? 2 : 1) +
+    size_t b = (size_t)C * N4 * 128 * (mode >= 2 ? 2 : 1) + (size_t)C * kTileM * 128 * (mode == 3 ? 2 : 1) +
                (size_t)stages * kStageBytes + (size_t)(2 * stages + C + 8) * 8 + 16 + 2 * kMaxDirs;
     return b + 1024;  // alignment slack
+}
+
+size_t smem_bytes_pair(int N4, int stages)
+{
+    const int C = (N4 + 63) / 64;
+    size_t b = (size_t)C * (N4 / 2) * 128 * 2 + (size_t)C * kTileM * 128 + (size_t)stages * kStageBytes +
+               (size_t)(2 * stages + C + 8) * 8 + 16 + 2 * kMaxDirs;
+    return b + 1024;
+}
+
+int mode_of(int precision)
+{
+    return precision == RTLB_PREC_BF16X3 ? 3 : (precision == RTLB_PREC_BF16X2 ? 2 : 1);
+}
+
+// Largest stage count that fits (0 = does not fit).
+int fit_stages(int N4, int mode, bool pair)
+{
+    for (int st = 8; st >= 2; --st)
+        if ((pair ? smem_bytes_pair(N4, st) : smem_bytes(N4, mode, st)) <= (size_t)kSmemLimit) return st;
+    return 0;
 }
 
 }  // namespace
 
 bool tc_supported(int n) { return n == 8 || n == 16 || n == 32 || n == 64; }
 
-bool tc_shape_ok(int n, bool split)
+bool tc_shape_ok(int n, int precision)
 {
     if (!tc_supported(n)) return false;
-    for (int st = 8; st >= 2; --st)
-        if (smem_bytes(4 * n, split, st) <= (size_t)kSmemLimit) return true;
-    return false;
+    const int mode = mode_of(precision);
+    return fit_stages(4 * n, mode, false) > 0 || (mode == 2 && fit_stages(4 * n, mode, true) > 0);
 }
 
 rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uint8_t *dev_cls, cudaStream_t s)
 {
     if (c->opt.precision == RTLB_PREC_FP32) return RTLB_OK;
-    const bool split = c->opt.precision == RTLB_PREC_BF16X3;
+    const int mode = mode_of(c->opt.precision);
+    const bool split = mode >= 2;
     if (!tc_supported(c->n)) {
         c->err = "tensor-core forms need n in {8, 16, 32, 64}";
         return RTLB_E_UNSUPPORTED;
     }
     const int N4 = 4 * c->n, KP = ((N4 + 63) / 64) * 64, C = KP / 64;
-    int stages = 0;
-    for (int st = 8; st >= 2; --st)
-        if (smem_bytes(N4, split, st) <= (size_t)kSmemLimit) {
-            stages = st;
-            break;
-        }
+    bool pair = false;
+    int stages = fit_stages(N4, mode, false);
+    if (stages == 0 && mode == 2) {
+        pair = true;
+        stages = fit_stages(N4, mode, true);
+    }
     if (stages == 0) {
-        c->err = "the split bf16 form does not fit in shared memory for n = 64";
+        c->err = "this precision form does not fit in shared memory for this n";
         return RTLB_E_UNSUPPORTED;
     }
     if (!encode_fn()) {
@@ -755,6 +881,23 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
         else mixed.push_back(tile);
     }
     std::stable_sort(pure.begin(), pure.end(), [](int x, int y) { return (x >> 24) < (y >> 24); });
+    if (pair) {
+        // consecutive single-class tiles of the same class form a pair; a
+        // tile left alone in its class runs on the CUDA-core kernel
+        std::vector<int> pairs;
+        size_t k = 0;
+        while (k < pure.size()) {
+            if (k + 1 < pure.size() && (pure[k] >> 24) == (pure[k + 1] >> 24)) {
+                pairs.push_back(pure[k]);
+                pairs.push_back(pure[k + 1]);
+                k += 2;
+            } else {
+                mixed.push_back(pure[k] & 0xFFFFFF);
+                k += 1;
+            }
+        }
+        pure.swap(pairs);
+    }
 
     free_tables(t);
     cudaError_t e = cudaMalloc(&t->d_Zhi, hi.size() * sizeof(__nv_bfloat16));
@@ -775,8 +918,9 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
         c->err = std::string("tensor-core table upload: ") + cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? RTLB_E_OOM : RTLB_E_CUDA;
     }
-    if (!encode_z_map(&t->tmZhi, t->d_Zhi, N4, KP, n_phase) ||
-        (split && !encode_z_map(&t->tmZlo, t->d_Zlo, N4, KP, n_phase))) {
+    const int box_rows = pair ? N4 / 2 : N4;
+    if (!encode_z_map(&t->tmZhi, t->d_Zhi, N4, KP, n_phase, box_rows) ||
+        (split && !encode_z_map(&t->tmZlo, t->d_Zlo, N4, KP, n_phase, box_rows))) {
         free_tables(t);
         c->err = "tensor map encoding for the phase tables failed";
         return RTLB_E_CUDA;
@@ -786,11 +930,12 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
     t->KP = KP;
     t->C = C;
     t->n_phase = n_phase;
-    t->split = split;
-    t->n_pure = (int)pure.size();
+    t->mode = mode;
+    t->pair = pair;
+    t->n_pure = pair ? (int)pure.size() / 2 : (int)pure.size();
     t->n_mixed = (int)mixed.size();
     t->stages = stages;
-    t->smem = smem_bytes(N4, split, stages);
+    t->smem = pair ? smem_bytes_pair(N4, stages) : smem_bytes(N4, mode, stages);
     return RTLB_OK;
 }
 
@@ -824,16 +969,22 @@ rtlb_status tc_step(rtlb_ctx *c, const StepParams &p, cudaStream_t s)
         tp.n = p.n;
         tp.bcbits = pack_bc(p.bc);
         tp.err = t->d_err;
-        const int grid = std::min(t->sm_count, t->n_pure);
-        cudaError_t e;
-        if (t->split) {
-            e = cudaFuncSetAttribute(k_step_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem);
+        cudaError_t e = cudaSuccess;
+        if (t->pair) {
+            const int grid = 2 * std::min(t->sm_count / 2, t->n_pure);
+            e = cudaFuncSetAttribute(k_step_tc_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem);
             if (e == cudaSuccess)
-                k_step_tc<true><<<grid, kThreads, t->smem, s>>>(t->tmS[which], t->tmZhi, t->tmZlo, tp, t->N4, t->stages);
+                k_step_tc_pair<<<grid, kThreads, t->smem, s>>>(t->tmS[which], t->tmZhi, t->tmZlo, tp, t->N4, t->stages);
         } else {
-            e = cudaFuncSetAttribute(k_step_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem);
-            if (e == cudaSuccess)
-                k_step_tc<false><<<grid, kThreads, t->smem, s>>>(t->tmS[which], t->tmZhi, t->tmZlo, tp, t->N4, t->stages);
+            const int grid = std::min(t->sm_count, t->n_pure);
+            auto launch = [&](auto kern) {
+                e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem);
+                if (e == cudaSuccess)
+                    kern<<<grid, kThreads, t->smem, s>>>(t->tmS[which], t->tmZhi, t->tmZlo, tp, t->N4, t->stages);
+            };
+            if (t->mode == 3) launch(k_step_tc<3>);
+            else if (t->mode == 2) launch(k_step_tc<2>);
+            else launch(k_step_tc<1>);
         }
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) {

@@ -3,9 +3,10 @@
 #include "rtlb_internal.h"
 
 namespace rtlb {
-// True when the tensor-core kernel handles n directions (n in {8,16,32,64};
-// the split form must also fit its operands in shared memory).
-bool tc_shape_ok(int n, bool split);
+// True when a tensor-core kernel handles n directions in this precision
+// (n in {8,16,32,64}; the operands must fit in shared memory of one CTA, or of
+// a CTA pair for the split-table form).
+bool tc_shape_ok(int n, int precision);
 // Builds the bf16 operand tables (and low parts for the split form) and the
 // per-tile class lists from the float64 tables and the device class array
 // (may be NULL = class 0).  No-op for the FP32 precision.
