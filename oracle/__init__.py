@@ -54,6 +54,9 @@ def lib():
         L.orc_dop.argtypes = [_dp]
         L.orc_dop.restype = C.c_double
         L.orc_num_threads.restype = C.c_int
+        L.orc_adjoint.argtypes = [C.c_int, C.c_int, C.c_int, _ip, _ip, _dp, _dp, C.c_void_p, C.c_void_p,
+                                  _dp, C.c_int, C.c_int, C.c_int, _ip, _dp, _dp, C.c_int, _dp,
+                                  _dp, _dp, _dp, C.c_void_p]
         _lib = L
     return _lib
 
@@ -151,13 +154,12 @@ class Problem:
         self.cx = np.ascontiguousarray(cx, np.int32)
         self.cz = np.ascontiguousarray(cz, np.int32)
         shp = (self.nz, self.nx)
-        self.tau = np.ascontiguousarray(np.broadcast_to(tau, shp), np.float64)
-        self.albedo = np.ascontiguousarray(np.broadcast_to(albedo, shp), np.float64)
-        self.emission = (None if emission is None else
-                         np.ascontiguousarray(np.broadcast_to(emission, shp), np.float64))
-        self.cls = (None if cls is None else
-                    np.ascontiguousarray(np.broadcast_to(cls, shp), np.int32))
-        Z = np.asarray(Z, np.float64)
+        own = lambda a, dt: np.array(np.broadcast_to(a, shp), dt, order="C", copy=True)
+        self.tau = own(tau, np.float64)
+        self.albedo = own(albedo, np.float64)
+        self.emission = None if emission is None else own(emission, np.float64)
+        self.cls = None if cls is None else own(cls, np.int32)
+        Z = np.array(Z, np.float64, copy=True)
         if Z.ndim == 2:
             Z = Z[None]
         self.Z = np.ascontiguousarray(Z)
@@ -195,6 +197,23 @@ class Problem:
         r = C.c_double()
         t = lib().orc_run_to_steady(*self._args(), S, float(tol), int(max_steps), C.byref(r))
         return S, t, r.value
+
+    def adjoint(self, S0, nsteps, dL_dout, want_S0=False):
+        """Gradients of L = <dL_dout, radiance_out(top, S^N)> (S^N after
+        nsteps steps from S0) w.r.t. tau [nz][nx], albedo [nz][nx], the phase
+        tables [n_phase][4n][4n] and (optionally) S0."""
+        S0 = np.ascontiguousarray(S0, np.float64)
+        dl = np.ascontiguousarray(dL_dout, np.float64).reshape(self.nx, self.n, 4)
+        gt = np.zeros((self.nz, self.nx))
+        ga = np.zeros((self.nz, self.nx))
+        gZ = np.zeros_like(self.Z)
+        gS = np.zeros_like(S0) if want_S0 else None
+        e = self.emission.ctypes.data if self.emission is not None else None
+        c = self.cls.ctypes.data if self.cls is not None else None
+        lib().orc_adjoint(self.nx, self.nz, self.n, self.cx, self.cz, self.tau, self.albedo, e, c,
+                          self.Z, self.Z.shape[0], self.surv_mode, self.abs_mode, self.bc, self.inflow,
+                          S0, int(nsteps), dl, gt, ga, gZ, gS.ctypes.data if want_S0 else None)
+        return (gt, ga, gZ, gS) if want_S0 else (gt, ga, gZ)
 
     def radiance_out(self, S, side=SIDE_TOP) -> np.ndarray:
         S = np.ascontiguousarray(S, np.float64)

@@ -382,3 +382,111 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ adjoint */
+
+/* Derivatives of the per-site step coefficients alpha = A s, beta = A (1 - s)
+ * with respect to the extinction optical depth tau and the albedo w
+ * (k_abs dt = (1 - w) tau, k_scat dt = w tau; Sec. 2.1.4 and Eq. 11). */
+static void coef_derivatives(double tau, double w, int surv_mode, int abs_mode, double *alpha,
+                             double *beta, double *da_dt, double *da_dw, double *db_dt, double *db_dw)
+{
+    double kabs = (1.0 - w) * tau, ksca = w * tau;
+    double A, dA, s, ds;        /* dA = dA/dkabs, ds = ds/dksca */
+    if (abs_mode == ORC_ABS_TAYLOR) { A = 1.0 - kabs; dA = -1.0; }
+    else { A = exp(-kabs); dA = -A; }
+    if (surv_mode == ORC_SURV_EXP) { s = exp(-ksca); ds = -s; }
+    else { s = 1.0 - ksca; ds = -1.0; }
+    *alpha = A * s;
+    *beta = A * (1.0 - s);
+    /* dkabs/dtau = 1 - w, dkabs/dw = -tau, dksca/dtau = w, dksca/dw = tau */
+    *da_dt = dA * (1.0 - w) * s + A * ds * w;
+    *da_dw = dA * (-tau) * s + A * ds * tau;
+    *db_dt = dA * (1.0 - w) * (1.0 - s) - A * ds * w;
+    *db_dw = dA * (-tau) * (1.0 - s) - A * ds * tau;
+}
+
+/* Reverse-mode gradient of L = <dL_dout, radiance_out(top, S^N)> after
+ * nsteps steps from S0, with respect to tau and albedo per cell, every
+ * phase-table entry, and the initial state.  All intermediate states are
+ * kept (small lattices only).  The step is affine,
+ *   S^{t+1} = T (C S^t + c0) + b,  C = blockdiag(alpha I + beta Z_c),
+ * so lambda^t = C^T T^T lambda^{t+1}; T^T pulls from each entry's
+ * streaming target (zero when the vector left through a non-periodic side). */
+void orc_adjoint(int nx, int nz, int n, const int *cx, const int *cz,
+                 const double *tau, const double *albedo, const double *emis, const int *cls,
+                 const double *Z, int n_phase, int surv_mode, int abs_mode, const int *bc,
+                 const double *inflow, const double *S0, int nsteps, const double *dL_dout,
+                 double *grad_tau, double *grad_albedo, double *grad_Z, double *grad_S0)
+{
+    int K = 4 * n;
+    size_t nsite = (size_t)nx * nz, len = nsite * K;
+    double *states = (double *)malloc((size_t)(nsteps + 1) * len * sizeof(double));
+    memcpy(states, S0, len * sizeof(double));
+    for (int t = 0; t < nsteps; ++t)
+        orc_step(nx, nz, n, cx, cz, tau, albedo, emis, cls, Z, surv_mode, abs_mode, bc, inflow,
+                 states + (size_t)t * len, states + (size_t)(t + 1) * len);
+    double *lam = (double *)calloc(len, sizeof(double));
+    double *mu = (double *)malloc(len * sizeof(double));
+    double *ga = (double *)calloc(nsite, sizeof(double));
+    double *gb = (double *)calloc(nsite, sizeof(double));
+    memset(grad_Z, 0, (size_t)n_phase * K * K * sizeof(double));
+    /* seed: the top row's outgoing directions */
+    for (int x = 0; x < nx; ++x)
+        for (int d = 0; d < n; ++d)
+            if (cz[d] == 1)
+                for (int s = 0; s < 4; ++s)
+                    lam[(((size_t)(nz - 1) * nx + x) * n + d) * 4 + s] = dL_dout[((size_t)x * n + d) * 4 + s];
+    int per_x = bc[ORC_SIDE_LEFT] == ORC_BC_PERIODIC, per_z = bc[ORC_SIDE_TOP] == ORC_BC_PERIODIC;
+    double *Se = (double *)malloc((size_t)K * sizeof(double));
+    double *ZTm = (double *)malloc((size_t)K * sizeof(double));
+    for (int t = nsteps - 1; t >= 0; --t) {
+        const double *St = states + (size_t)t * len;
+        /* mu = T^T lambda */
+        for (int z = 0; z < nz; ++z)
+            for (int x = 0; x < nx; ++x)
+                for (int d = 0; d < n; ++d) {
+                    int xt = x + cx[d], zt = z + cz[d];
+                    if (per_x) xt = ((xt % nx) + nx) % nx;
+                    if (per_z) zt = ((zt % nz) + nz) % nz;
+                    double *dst = mu + (((size_t)z * nx + x) * n + d) * 4;
+                    int inside = xt >= 0 && xt < nx && zt >= 0 && zt < nz;
+                    for (int s = 0; s < 4; ++s)
+                        dst[s] = inside ? lam[(((size_t)zt * nx + xt) * n + d) * 4 + s] : 0.0;
+                }
+        /* lambda = C^T mu, and the parameter gradients of this step */
+        for (size_t st = 0; st < nsite; ++st) {
+            int c = cls ? cls[st] : 0;
+            const double *Zc = Z + (size_t)c * K * K;
+            double alpha, beta, a1, a2, b1, b2;
+            coef_derivatives(tau[st], albedo[st], surv_mode, abs_mode, &alpha, &beta, &a1, &a2, &b1, &b2);
+            const double *m = mu + st * K;
+            for (int j = 0; j < K; ++j) Se[j] = St[st * K + j];
+            for (int d = 0; d < n; ++d) Se[4 * d] += emis ? emis[st] : 0.0;
+            for (int k = 0; k < K; ++k) {
+                double acc = 0.0;
+                for (int row = 0; row < K; ++row) acc += Zc[(size_t)row * K + k] * m[row];
+                ZTm[k] = acc;
+            }
+            double sa = 0.0, sb = 0.0;
+            for (int k = 0; k < K; ++k) {
+                sa += m[k] * Se[k];
+                sb += ZTm[k] * Se[k];
+                lam[st * K + k] = alpha * m[k] + beta * ZTm[k];
+            }
+            ga[st] += sa;
+            gb[st] += sb;
+            double *G = grad_Z + (size_t)c * K * K;
+            for (int row = 0; row < K; ++row)
+                for (int k = 0; k < K; ++k) G[(size_t)row * K + k] += beta * m[row] * Se[k];
+        }
+    }
+    for (size_t st = 0; st < nsite; ++st) {
+        double alpha, beta, a1, a2, b1, b2;
+        coef_derivatives(tau[st], albedo[st], surv_mode, abs_mode, &alpha, &beta, &a1, &a2, &b1, &b2);
+        grad_tau[st] = ga[st] * a1 + gb[st] * b1;
+        grad_albedo[st] = ga[st] * a2 + gb[st] * b2;
+    }
+    if (grad_S0) memcpy(grad_S0, lam, len * sizeof(double));
+    free(states); free(lam); free(mu); free(ga); free(gb); free(Se); free(ZTm);
+}
