@@ -229,6 +229,43 @@ def accuracy(precisions, steps):
     return out
 
 
+def adjoint_ratio(steps: int, headline: str):
+    """Time rtlb_adjoint on the 1024x256, n = 32 workload (checkpoint every
+    50 steps, float32 replay) against the forward of the same number of steps
+    in float32 and in the headline precision."""
+    import torch
+    from paper_2609_23057_b300.solver import solver_for
+    w = W.adjoint(steps=steps)
+    out = {"workload": w.name, "steps": steps, "checkpoint_every": 50}
+    fwd = {}
+    for prec in ("fp32", headline):
+        if prec in fwd:
+            continue
+        s = solver_for(w, prec)
+        s.step(5)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        s.step(steps)
+        b.record()
+        torch.cuda.synchronize()
+        fwd[prec] = a.elapsed_time(b)
+        s.close()
+    s = solver_for(w, "fp32")
+    seed = torch.randn((w.nx, w.n, 4), device="cuda")
+    s.adjoint(20, seed, checkpoint_every=10)          # warm-up (allocation paths)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.adjoint(steps, seed, checkpoint_every=50)
+    torch.cuda.synchronize()
+    adj_ms = (time.perf_counter() - t0) * 1e3
+    s.close()
+    out.update({"adjoint_ms": adj_ms, "forward_ms": fwd,
+                "adjoint_over_forward": {p: adj_ms / v for p, v in fwd.items()},
+                "note": "the adjoint call includes its own float32 forward pass and the replay of every segment"})
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2609_23057_b300 import solver as SV
@@ -336,6 +373,10 @@ def run_ours(args):
             "compare": compare,
             "adjoint_over_forward": None,
         }
+        if ws == 1 and args.adjoint_steps > 0:
+            adj = adjoint_ratio(args.adjoint_steps, args.precision)
+            line["adjoint"] = adj
+            line["adjoint_over_forward"] = adj["adjoint_over_forward"]["fp32"]
         if ws == 1 and args.accuracy_steps > 0:
             precs = [args.precision] + [p for p in ("bf16", "fp32") if p != args.precision]
             line["accuracy"] = accuracy(precs, args.accuracy_steps)
@@ -357,6 +398,8 @@ def main():
                     help="headline form; bf16x2 is the tensor-core form that meets 1e-3 on the crop")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the FP32 comparison form")
+    ap.add_argument("--adjoint-steps", type=int, default=1000,
+                    help="steps of the 1024x256 adjoint timing (0 = skip)")
     ap.add_argument("--nx", type=int, default=2048, help="lattice width (profiling of smaller cases)")
     ap.add_argument("--nz", type=int, default=2048, help="lattice height (profiling of smaller cases)")
     ap.add_argument("--accuracy-steps", type=int, default=200,

@@ -148,6 +148,24 @@ rtlb_status rtlb_last_residual(rtlb_ctx *ctx, double *residual, void *stream);
  * that side, zero for the others. */
 rtlb_status rtlb_radiance_out(rtlb_ctx *ctx, int32_t side, float *out, void *stream);
 
+/* Reverse-mode gradients (adjoint of Eq. 2's step: transposed phase-matrix
+ * scattering and reversed streaming) of a loss L whose gradient with respect to
+ * the top radiance radiance_out(TOP) after nsteps steps is dL_dout[nx][n][4]
+ * (host or device).  Starting from the current state S^0 the call runs nsteps
+ * float32 steps (whatever the context's precision; the state afterwards is
+ * S^N, as after rtlb_step), keeping a checkpoint every checkpoint_every steps,
+ * then walks back segment by segment, recomputing each segment's states from
+ * its checkpoint.  Outputs (each may be NULL): grad_tau, grad_albedo [nz][nx]
+ * float32 (host or device) -- dL/dtau and dL/dalbedo per cell; grad_Z host
+ * float64 [n_phase][4n][4n] -- dL/dZ per class table entry (contract with
+ * rtlb_phase_hg's dZdg for dL/dg); grad_S0 [nz][nx][n][4] float32 (host or
+ * device) -- dL/dS^0.  Device memory: (ceil(nsteps/checkpoint_every) +
+ * checkpoint_every + 3) states plus the table-gradient accumulators.  n must be
+ * in {8, 16, 32, 64}.  Synchronizes. */
+rtlb_status rtlb_adjoint(rtlb_ctx *ctx, int32_t nsteps, int32_t checkpoint_every, const float *dL_dout,
+                         float *grad_tau, float *grad_albedo, double *grad_Z, float *grad_S0,
+                         void *stream);
+
 /* Total I over the lattice and directions, accumulated in float64 on the
  * device.  Synchronizes. */
 rtlb_status rtlb_total_intensity(rtlb_ctx *ctx, double *total, void *stream);

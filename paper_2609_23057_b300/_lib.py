@@ -27,7 +27,7 @@ EXPORTS = [
     "rtlb_step", "rtlb_run_to_steady", "rtlb_last_residual", "rtlb_radiance_out",
     "rtlb_total_intensity", "rtlb_steps_done", "rtlb_last_error", "rtlb_destroy",
     "rtlb_stream_offsets", "rtlb_phase_rayleigh", "rtlb_phase_hg", "rtlb_phase_mix",
-    "rtlb_residual_noalloc",
+    "rtlb_residual_noalloc", "rtlb_adjoint",
 ]
 
 
@@ -83,6 +83,7 @@ def lib() -> C.CDLL:
     L.rtlb_phase_hg.argtypes = [C.POINTER(Directions), C.c_double, C.c_double, vp, vp]
     L.rtlb_phase_mix.argtypes = [C.POINTER(Directions), C.c_double, C.c_double, C.c_double, vp]
     L.rtlb_residual_noalloc.argtypes = [vp, vp, C.c_size_t, vp, vp]
+    L.rtlb_adjoint.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         f = getattr(L, name)
         if f.restype is C.c_int:     # ctypes default: status codes are int32

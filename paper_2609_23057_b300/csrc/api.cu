@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -91,6 +92,9 @@ void free_ctx_buffers(rtlb_ctx *c)
     cudaFree(c->d_coef);
     cudaFree(c->d_cls);
     cudaFree(c->d_ZT);
+    cudaFree(c->d_Z);
+    cudaFree(c->d_tau);
+    cudaFree(c->d_alb);
     cudaFree(c->d_scratch);
     cudaFree(c->d_out);
     cudaFree(c->d_flags);
@@ -234,13 +238,16 @@ rtlb_status rtlb_set_medium(rtlb_ctx *c, const float *tau, const float *albedo, 
     uint8_t *tmp_cls = nullptr;
     float4 *coef = nullptr;
     uint8_t *cls_dev = nullptr;
-    float *ZT = nullptr;
+    float *ZT = nullptr, *Zr = nullptr, *tau_keep = nullptr, *alb_keep = nullptr;
     auto cleanup = [&]() {
         for (float *t : tmp) cudaFree(t);
         cudaFree(tmp_cls);
         cudaFree(coef);
         cudaFree(cls_dev);
         cudaFree(ZT);
+        cudaFree(Zr);
+        cudaFree(tau_keep);
+        cudaFree(alb_keep);
     };
     const float *in[3] = {tau, albedo, emission};
     const float *dev_in[3] = {nullptr, nullptr, nullptr};
@@ -265,15 +272,24 @@ rtlb_status rtlb_set_medium(rtlb_ctx *c, const float *tau, const float *albedo, 
             dev_cls = tmp_cls;
         }
     }
-    std::vector<float> zt((size_t)n_phase * tsz);
+    std::vector<float> zt((size_t)n_phase * tsz), zr((size_t)n_phase * tsz);
     for (int p = 0; p < n_phase; ++p)
         for (int row = 0; row < N4; ++row)
-            for (int col = 0; col < N4; ++col)
-                zt[(size_t)p * tsz + (size_t)col * N4 + row] = (float)phase_tables[(size_t)p * tsz + (size_t)row * N4 + col];
+            for (int col = 0; col < N4; ++col) {
+                const float v = (float)phase_tables[(size_t)p * tsz + (size_t)row * N4 + col];
+                zt[(size_t)p * tsz + (size_t)col * N4 + row] = v;
+                zr[(size_t)p * tsz + (size_t)row * N4 + col] = v;
+            }
     if (e == cudaSuccess) e = cudaMalloc(&coef, (size_t)ns * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&cls_dev, (size_t)ns);
     if (e == cudaSuccess) e = cudaMalloc(&ZT, zt.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpyAsync(ZT, zt.data(), zt.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMalloc(&Zr, zr.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Zr, zr.data(), zr.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMalloc(&tau_keep, (size_t)ns * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&alb_keep, (size_t)ns * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tau_keep, dev_in[0], (size_t)ns * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(alb_keep, dev_in[1], (size_t)ns * sizeof(float), cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_flags, 0, sizeof(int), s);
     if (e == cudaSuccess)
         e = launch_prep_medium(dev_in[0], dev_in[1], dev_in[2], dev_cls, coef, cls_dev, ns, n_phase,
@@ -303,9 +319,15 @@ rtlb_status rtlb_set_medium(rtlb_ctx *c, const float *tau, const float *albedo, 
     cudaFree(c->d_coef);
     cudaFree(c->d_cls);
     cudaFree(c->d_ZT);
+    cudaFree(c->d_Z);
+    cudaFree(c->d_tau);
+    cudaFree(c->d_alb);
     c->d_coef = coef;
     c->d_cls = cls_dev;
     c->d_ZT = ZT;
+    c->d_Z = Zr;
+    c->d_tau = tau_keep;
+    c->d_alb = alb_keep;
     c->n_phase = n_phase;
     c->medium_set = true;
     return RTLB_OK;
@@ -437,6 +459,129 @@ rtlb_status rtlb_run_to_steady(rtlb_ctx *c, double tol, int32_t max_steps, int32
     *steps_taken = taken;
     *residual = r;
     if (!(r < tol)) return fail(c, RTLB_E_NOT_CONVERGED, "residual %.3e after %d steps (tol %.3e)", r, taken, tol);
+    return RTLB_OK;
+}
+
+rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, const float *dL_dout,
+                         float *grad_tau, float *grad_albedo, double *grad_Z, float *grad_S0, void *stream)
+{
+    if (!c || !dL_dout) return fail(c, RTLB_E_ARG, "null argument");
+    if (nsteps < 1 || checkpoint_every < 1) return fail(c, RTLB_E_ARG, "need nsteps >= 1 and checkpoint_every >= 1");
+    if (!c->medium_set) return fail(c, RTLB_E_STATE, "rtlb_set_medium must come before rtlb_adjoint");
+    if (!adjoint_supported(c->n)) return fail(c, RTLB_E_UNSUPPORTED, "the adjoint needs n in {8, 16, 32, 64}");
+    rtlb_status st = require_boundary_pairs(c);
+    if (st != RTLB_OK) return st;
+    cudaStream_t s = S(stream);
+    const size_t L = c->state_floats(), bytes = L * sizeof(float), ns = c->nsites();
+    const int K = checkpoint_every, nseg = (nsteps + K - 1) / K, N4 = 4 * c->n;
+    const int nslots = adjoint_table_slots();
+    const size_t glen = (size_t)c->n_phase * N4 * N4;
+    float *ck = nullptr, *seg = nullptr, *lam = nullptr, *bm = nullptr, *dl = nullptr, *gtd = nullptr, *gad = nullptr;
+    float *gS = nullptr;
+    double *ga = nullptr, *gb = nullptr, *slots = nullptr, *G = nullptr;
+    auto release = [&]() {
+        cudaFree(ck); cudaFree(seg); cudaFree(lam); cudaFree(bm); cudaFree(dl); cudaFree(gtd); cudaFree(gad);
+        cudaFree(gS); cudaFree(ga); cudaFree(gb); cudaFree(slots); cudaFree(G);
+    };
+#define AK(call, what)                                \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) {                      \
+            release();                                \
+            return cuda_fail(c, e_, (what));          \
+        }                                             \
+    } while (0)
+    AK(cudaMalloc(&ck, (size_t)nseg * bytes), "adjoint checkpoints");
+    AK(cudaMalloc(&seg, (size_t)K * bytes), "adjoint segment states");
+    AK(cudaMalloc(&lam, 2 * bytes), "adjoint lambda");
+    AK(cudaMalloc(&bm, bytes), "adjoint beta mu");
+    AK(cudaMalloc(&ga, ns * sizeof(double)), "adjoint g_alpha");
+    AK(cudaMalloc(&gb, ns * sizeof(double)), "adjoint g_beta");
+    AK(cudaMalloc(&slots, (size_t)nslots * glen * sizeof(double)), "adjoint table slots");
+    AK(cudaMalloc(&G, glen * sizeof(double)), "adjoint table gradient");
+    const float *dl_dev = dL_dout;
+    const size_t dl_bytes = (size_t)c->nx * c->n * 4 * sizeof(float);
+    if (!is_device_ptr(dL_dout)) {
+        AK(cudaMalloc(&dl, dl_bytes), "adjoint seed staging");
+        AK(cudaMemcpyAsync(dl, dL_dout, dl_bytes, cudaMemcpyHostToDevice, s), "adjoint seed upload");
+        dl_dev = dl;
+    }
+    // forward in float32 with a checkpoint at the start of every segment
+    for (int g = 0; g < nseg; ++g) {
+        AK(cudaMemcpyAsync(ck + (size_t)g * L, c->S[c->cur], bytes, cudaMemcpyDeviceToDevice, s), "checkpoint");
+        const int len = std::min(K, nsteps - g * K);
+        for (int j = 0; j < len; ++j) {
+            AK(launch_step_fp32(make_params(c), s), "adjoint forward");
+            c->cur ^= 1;
+        }
+    }
+    c->steps += nsteps;
+    c->has_prev = true;
+    // reverse sweep
+    AK(cudaMemsetAsync(lam, 0, 2 * bytes, s), "lambda init");
+    AK(cudaMemsetAsync(ga, 0, ns * sizeof(double), s), "g_alpha init");
+    AK(cudaMemsetAsync(gb, 0, ns * sizeof(double), s), "g_beta init");
+    AK(cudaMemsetAsync(slots, 0, (size_t)nslots * glen * sizeof(double), s), "slots init");
+    AK(launch_adjoint_seed(lam, dl_dev, c->d_dir, c->nx, c->nz, c->n, s), "adjoint seed");
+    int lc = 0;
+    for (int g = nseg - 1; g >= 0; --g) {
+        const int len = std::min(K, nsteps - g * K);
+        AK(cudaMemcpyAsync(seg, ck + (size_t)g * L, bytes, cudaMemcpyDeviceToDevice, s), "segment start");
+        for (int j = 0; j + 1 < len; ++j) {
+            StepParams p = make_params(c);
+            p.S = seg + (size_t)j * L;
+            p.S_new = seg + (size_t)(j + 1) * L;
+            AK(launch_step_fp32(p, s), "adjoint recompute");
+        }
+        for (int j = len - 1; j >= 0; --j) {
+            AdjointParams ap;
+            ap.lam_next = lam + (size_t)lc * L;
+            ap.lam_out = lam + (size_t)(lc ^ 1) * L;
+            ap.beta_mu = bm;
+            ap.S = seg + (size_t)j * L;
+            ap.coef = c->d_coef;
+            ap.cls = c->d_cls;
+            ap.Z = c->d_Z;
+            ap.dir = c->d_dir;
+            ap.nx = c->nx;
+            ap.nz = c->nz;
+            ap.n = c->n;
+            ap.n_phase = c->n_phase;
+            for (int k = 0; k < 4; ++k) ap.bc[k] = c->bc[k];
+            ap.g_alpha = ga;
+            ap.g_beta = gb;
+            AK(launch_adjoint_step(ap, slots, s), "adjoint step");
+            lc ^= 1;
+        }
+    }
+    // outputs
+    if (grad_tau || grad_albedo) {
+        const bool dev_t = grad_tau && is_device_ptr(grad_tau), dev_a = grad_albedo && is_device_ptr(grad_albedo);
+        float *ot = dev_t ? grad_tau : nullptr, *oa = dev_a ? grad_albedo : nullptr;
+        if (!ot) { AK(cudaMalloc(&gtd, ns * sizeof(float)), "grad staging"); ot = gtd; }
+        if (!oa) { AK(cudaMalloc(&gad, ns * sizeof(float)), "grad staging"); oa = gad; }
+        AK(launch_adjoint_chain(ga, gb, c->d_tau, c->d_alb, (int)ns, c->opt.survival, c->opt.absorption, ot, oa, s),
+           "adjoint chain rule");
+        if (grad_tau && !dev_t) AK(cudaMemcpyAsync(grad_tau, gtd, ns * sizeof(float), cudaMemcpyDeviceToHost, s), "grad_tau");
+        if (grad_albedo && !dev_a)
+            AK(cudaMemcpyAsync(grad_albedo, gad, ns * sizeof(float), cudaMemcpyDeviceToHost, s), "grad_albedo");
+    }
+    if (grad_Z) {
+        AK(launch_adjoint_fold(slots, nslots, glen, G, s), "table gradient");
+        AK(cudaMemcpyAsync(grad_Z, G, glen * sizeof(double), cudaMemcpyDeviceToHost, s), "grad_Z");
+    }
+    if (grad_S0) {
+        if (is_device_ptr(grad_S0)) {
+            AK(launch_dm_to_user(lam + (size_t)lc * L, grad_S0, (int)ns, c->n, s), "grad_S0");
+        } else {
+            AK(cudaMalloc(&gS, bytes), "grad_S0 staging");
+            AK(launch_dm_to_user(lam + (size_t)lc * L, gS, (int)ns, c->n, s), "grad_S0");
+            AK(cudaMemcpyAsync(grad_S0, gS, bytes, cudaMemcpyDeviceToHost, s), "grad_S0 download");
+        }
+    }
+    AK(cudaStreamSynchronize(s), "adjoint sync");
+#undef AK
+    release();
     return RTLB_OK;
 }
 

@@ -37,6 +37,29 @@ struct StepParams {
     int n_tiles = 0, tile_span = 0;
 };
 
+// Everything one adjoint step needs (see adjoint.cu).
+struct AdjointParams {
+    const float *lam_next;  // lambda^{t+1}, direction-major
+    float *lam_out;         // lambda^t
+    float *beta_mu;         // beta * mu, input of the table-gradient GEMM
+    const float *S;         // S^t
+    const float4 *coef;
+    const uint8_t *cls;
+    const float *Z;         // [n_phase][4n][4n] row-major float32 (untransposed)
+    const int *dir;
+    int nx, nz, n, n_phase;
+    int bc[4];
+    double *g_alpha, *g_beta;  // [nsites] accumulated over the steps
+};
+
+bool adjoint_supported(int n);
+int adjoint_table_slots();
+cudaError_t launch_adjoint_step(const AdjointParams &p, double *slots, cudaStream_t s);
+cudaError_t launch_adjoint_seed(float *lam, const float *dL_dout, const int *dir, int nx, int nz, int n, cudaStream_t s);
+cudaError_t launch_adjoint_chain(const double *ga, const double *gb, const float *tau, const float *alb, int nsites,
+                                 int surv_mode, int abs_mode, float *g_tau, float *g_alb, cudaStream_t s);
+cudaError_t launch_adjoint_fold(const double *slots, int nslots, size_t len, double *out, cudaStream_t s);
+
 // ---- kernels (launchers return the launch error) ----
 cudaError_t launch_user_to_dm(const float *user, float *dm, int nsites, int n, cudaStream_t s);
 cudaError_t launch_dm_to_user(const float *dm, float *user, int nsites, int n, cudaStream_t s);
@@ -72,6 +95,9 @@ struct rtlb_ctx {
     float4 *d_coef = nullptr;
     uint8_t *d_cls = nullptr;
     float *d_ZT = nullptr;
+    float *d_Z = nullptr;         // untransposed float32 tables (adjoint)
+    float *d_tau = nullptr;       // medium kept for the adjoint's chain rule
+    float *d_alb = nullptr;
     int n_phase = 0;
     bool medium_set = false;
     double *d_scratch = nullptr;  // reduction partials

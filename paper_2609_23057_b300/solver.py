@@ -145,6 +145,7 @@ class Solver:
         self._check(lib().rtlb_set_medium(self._ctx, _ptr(conv[0]), _ptr(conv[1]), _ptr(conv[2]),
                                           tabs.shape[0], tabs.ctypes.data, _ptr(conv[3]),
                                           _stream(stream)))
+        self._n_phase = tabs.shape[0]
 
     def set_boundary(self, side, kind, inflow=None):
         side = SIDES[side] if isinstance(side, str) else int(side)
@@ -198,6 +199,25 @@ class Solver:
         self._check(lib().rtlb_radiance_out(self._ctx, side, _ptr(out), _stream(stream)))
         return out
 
+    def adjoint(self, nsteps: int, dL_dout, checkpoint_every: int = 50, want_S0: bool = False,
+                want_Z: bool = True, stream=None):
+        """Run nsteps float32 steps from the current state and return the
+        gradients of a loss whose gradient w.r.t. the final top radiance is
+        dL_dout [nx][n][4]: (grad_tau, grad_albedo) as cuda tensors [nz][nx],
+        grad_Z (numpy [n_phase][4n][4n] or None) and grad_S0 (cuda tensor or
+        None)."""
+        import torch
+        dl = dL_dout if hasattr(dL_dout, "data_ptr") else torch.as_tensor(np.asarray(dL_dout, np.float32))
+        dl = dl.to(device="cuda", dtype=torch.float32).contiguous()
+        gt = torch.empty((self.nz, self.nx), dtype=torch.float32, device="cuda")
+        ga = torch.empty_like(gt)
+        n_phase = self._n_phase
+        gZ = np.zeros((n_phase, 4 * self.n, 4 * self.n)) if want_Z else None
+        gS = torch.empty((self.nz, self.nx, self.n, 4), dtype=torch.float32, device="cuda") if want_S0 else None
+        self._check(lib().rtlb_adjoint(self._ctx, int(nsteps), int(checkpoint_every), _ptr(dl), _ptr(gt), _ptr(ga),
+                                       _ptr(gZ), _ptr(gS), _stream(stream)))
+        return gt, ga, gZ, gS
+
     @property
     def steps_done(self) -> int:
         return int(lib().rtlb_steps_done(self._ctx))
@@ -216,3 +236,63 @@ def solver_for(w, precision: str = "fp32") -> Solver:
         inflow = None if w.inflow is None else w.inflow[side]
         s.set_boundary(side, w.bc[side], inflow if w.bc[side] == 2 else None)
     return s
+
+
+def _tables_for(solver: Solver, specs, g_value=None, hg_index=None):
+    tabs, dZdg = [], None
+    for k, sp in enumerate(specs):
+        if k == hg_index:
+            Z, dZdg = phase_hg(solver.n_zen, solver.n_az, float(g_value), sp[2], with_dg=True)
+            tabs.append(Z)
+        else:
+            tabs.append(phase_table_spec(solver.n_zen, solver.n_az, sp))
+    return np.stack(tabs), dZdg
+
+
+def _make_top_radiance_fn():
+    import torch
+
+    class TopRadiance(torch.autograd.Function):
+        """top radiance [nx][n][4] after `nsteps` steps from a zero state, as a
+        differentiable function of per-cell extinction tau [nz][nx], albedo
+        [nz][nx] and the asymmetry g of the HG class `hg_index`.  Forward:
+        rtlb_set_medium + rtlb_step + rtlb_radiance_out.  Backward:
+        rtlb_adjoint (float32 forward replayed from checkpoints every
+        `checkpoint_every` steps), dL/dg = <dZ/dg, dL/dZ_hg>."""
+
+        @staticmethod
+        def forward(ctx, tau, albedo, g, solver, specs, hg_index, phase_index, nsteps, checkpoint_every):
+            tabs, dZdg = _tables_for(solver, specs, g.item(), hg_index)
+            solver.set_medium(tau.detach().float().contiguous(), albedo.detach().float().contiguous(), tabs,
+                              phase_index=phase_index)
+            zero = torch.zeros((solver.nz, solver.nx, solver.n, 4), dtype=torch.float32, device="cuda")
+            solver.set_state(zero)
+            solver.step(nsteps)
+            out = solver.radiance_out("top").clone()
+            ctx.solver, ctx.nsteps, ctx.K, ctx.hg_index, ctx.dZdg = solver, nsteps, checkpoint_every, hg_index, dZdg
+            ctx.zero = zero
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            s = ctx.solver
+            s.set_state(ctx.zero)
+            gt, ga, gZ, _ = s.adjoint(ctx.nsteps, grad_out.contiguous(), checkpoint_every=ctx.K)
+            gg = None
+            if ctx.hg_index is not None:
+                gg = torch.tensor(float(np.sum(ctx.dZdg * gZ[ctx.hg_index])), dtype=torch.float64, device="cuda")
+            return gt, ga, gg, None, None, None, None, None, None
+
+    return TopRadiance
+
+
+_TOP_RADIANCE = None
+
+
+def top_radiance(tau, albedo, g, solver: Solver, specs, hg_index=None, phase_index=None, nsteps=100,
+                 checkpoint_every=50):
+    """Differentiable top radiance (see TopRadiance); g is a scalar tensor."""
+    global _TOP_RADIANCE
+    if _TOP_RADIANCE is None:
+        _TOP_RADIANCE = _make_top_radiance_fn()
+    return _TOP_RADIANCE.apply(tau, albedo, g, solver, specs, hg_index, phase_index, nsteps, checkpoint_every)

@@ -1,0 +1,165 @@
+"""GPU adjoint (rtlb_adjoint) against the FP64 oracle adjoint, against central
+finite differences of the FP64 oracle, and an exact linearity identity at the
+full 1024x256 size.  Tolerance 1e-4 relative (float32 arithmetic accumulated
+over the steps; the oracle adjoint itself is pinned to finite differences at
+1e-6)."""
+import numpy as np
+import pytest
+
+from paper_2609_23057_b300 import workloads as W
+from _util import oracle_problem
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+def _rel(a, b):
+    return float(np.abs(np.asarray(a, np.float64) - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _gpu_adjoint(torch, w, S0, nsteps, seed, K):
+    from paper_2609_23057_b300.solver import solver_for
+    s = solver_for(w, "fp32")
+    s.set_state(torch.from_numpy(np.asarray(S0, np.float32)).cuda())
+    gt, ga, gZ, gS = s.adjoint(nsteps, torch.from_numpy(np.asarray(seed, np.float32)).cuda(), checkpoint_every=K,
+                               want_S0=True)
+    out = (gt.cpu().numpy(), ga.cpu().numpy(), gZ, gS.cpu().numpy(), s.get_state().cpu().numpy())
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("nx,nz,nzen,naz,bc,surv,absm,nph", [
+    (13, 9, 2, 4, (2, 0, 0, 0), 1, 0, 2),
+    (20, 7, 4, 4, (2, 0, 1, 1), 0, 0, 3),
+    (17, 11, 4, 8, (1, 1, 2, 0), 1, 1, 2),
+    (9, 6, 8, 8, (2, 2, 0, 0), 1, 0, 2),
+])
+def test_adjoint_matches_oracle(torch_cuda, orc, nx, nz, nzen, naz, bc, surv, absm, nph):
+    w = W.random_medium(nx, nz, nzen, naz, seed=nx * nz, bc=bc, n_phase=nph, steps=12, surv_mode=surv)
+    w.tau = np.minimum(w.tau, 0.9)
+    w.abs_mode = absm
+    P = oracle_problem(orc, w)
+    S0 = W.random_state(nz, nx, w.n, seed=4)
+    seed = np.random.default_rng(5).standard_normal((nx, w.n, 4)).astype(np.float32).astype(np.float64)
+    rt, ra, rZ, rS = P.adjoint(S0, w.steps, seed, want_S0=True)
+    gt, ga, gZ, gS, SN = _gpu_adjoint(torch_cuda, w, S0, w.steps, seed, K=5)
+    assert _rel(gt, rt) < TOL
+    assert _rel(ga, ra) < TOL
+    assert _rel(gZ, rZ) < TOL
+    assert _rel(gS, rS) < TOL
+    # the state afterwards is the forward result
+    assert _rel(SN, P.run(S0, w.steps)) < 1e-5
+
+
+def test_adjoint_crop_fd_and_g(torch_cuda, orc):
+    """16x16 crop of the 1024x256, n = 32 adjoint medium, 100 steps, loss =
+    squared error of the top I, Q, U against a seeded target: GPU adjoint vs
+    oracle adjoint, vs central differences (h = 1e-3) of the oracle forward at
+    64 random cells, and dL/dg of the cloud table (through dZ/dg) vs a central
+    difference in g."""
+    from paper_2609_23057_b300.solver import phase_hg
+    full = W.adjoint(steps=100)
+    w = full.crop(120, 136, 500, 516)
+    P = oracle_problem(orc, w)
+    S0 = np.zeros((w.nz, w.nx, w.n, 4))
+    ref_top = P.radiance_out(P.run(S0, w.steps), orc.SIDE_TOP)
+    rng = np.random.default_rng(2)
+    target = ref_top * (1.1 + 0.05 * rng.standard_normal(ref_top.shape))
+    m = np.zeros_like(ref_top)
+    m[..., :3] = 1.0
+
+    def loss(Pp):
+        top = Pp.radiance_out(Pp.run(S0, w.steps), orc.SIDE_TOP)
+        return float(np.sum(m * (top - target) ** 2))
+
+    seed = 2 * m * (ref_top - target)
+    rt, ra, rZ = P.adjoint(S0, w.steps, seed)
+    gt, ga, gZ, _, _ = _gpu_adjoint(torch_cuda, w, S0, w.steps, seed, K=30)
+    assert _rel(gt, rt) < TOL and _rel(ga, ra) < TOL and _rel(gZ, rZ) < TOL
+    cells = [tuple(c) for c in rng.integers(0, [w.nz, w.nx], size=(64, 2))]
+    h = 1e-3
+    for z, x in cells:
+        vals = []
+        for sgn in (1, -1):
+            Pp = oracle_problem(orc, w)
+            Pp.tau[z, x] += sgn * h
+            vals.append(loss(Pp))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - gt[z, x]) <= TOL * np.abs(gt).max() + 1e-6 * abs(fd)
+    # cloud g (class 1 is HG with g = 0.85): dL/dg = <dZ/dg, dL/dZ_cloud>.
+    # The loss curves strongly in g near the forward peak: a central
+    # difference with h = 1e-3 carries ~2e-4 relative truncation error, so
+    # the check uses h = 1e-4 (truncation ~2e-6) and the exact oracle adjoint.
+    _, dZdg = phase_hg(w.n_zen, w.n_az, 0.85, -0.1, with_dg=True)
+    g_adj = float(np.sum(dZdg * gZ[1]))
+    assert g_adj == pytest.approx(float(np.sum(dZdg * rZ[1])), rel=TOL)
+    hg = 1e-4
+    vals = []
+    for sgn in (1, -1):
+        ww = full.crop(120, 136, 500, 516)
+        ww.phase_specs = [("rayleigh",), ("hg", 0.85 + sgn * hg, -0.1)]
+        vals.append(loss(oracle_problem(orc, ww)))
+    g_fd = (vals[0] - vals[1]) / (2 * hg)
+    assert g_adj == pytest.approx(g_fd, rel=TOL)
+
+
+def test_adjoint_full_size_linearity(torch_cuda):
+    """1024x256, n = 32, 1000 steps, checkpoint every 50: the map S^0 -> top
+    radiance is affine, so for any direction dS, <grad_S0, dS> equals the
+    change of <seed, top radiance> when S^0 moves by dS."""
+    from paper_2609_23057_b300.solver import solver_for
+    w = W.adjoint(steps=1000)
+    rng = np.random.default_rng(3)
+    seed = rng.standard_normal((w.nx, w.n, 4)).astype(np.float32)
+    dS = torch_cuda.from_numpy(W.random_state(w.nz, w.nx, w.n, seed=7, dtype=np.float32)).cuda()
+    s = solver_for(w, "fp32")
+    zero = torch_cuda.zeros_like(dS)
+    s.set_state(zero)
+    gt, ga, gZ, gS = s.adjoint(w.steps, torch_cuda.from_numpy(seed).cuda(), checkpoint_every=50, want_S0=True)
+    top0 = s.radiance_out("top").cpu().numpy().astype(np.float64)
+    s.set_state(dS)
+    s.step(w.steps)
+    top1 = s.radiance_out("top").cpu().numpy().astype(np.float64)
+    s.close()
+    lhs = float(np.sum(seed * (top1 - top0)))
+    rhs = float(torch_cuda.sum(gS.double() * dS.double()).item())
+    assert np.isfinite(gt.cpu().numpy()).all() and np.isfinite(ga.cpu().numpy()).all()
+    assert rhs == pytest.approx(lhs, rel=1e-4)
+
+
+def test_autograd_function(torch_cuda, orc):
+    """torch.autograd through top_radiance: gradients equal the oracle
+    adjoint for tau and albedo and a central difference for g."""
+    from paper_2609_23057_b300.solver import Solver, top_radiance
+    w = W.adjoint(steps=60).crop(118, 134, 40, 60)
+    s = Solver(w.nx, w.nz, w.n_zen, w.n_az, precision="fp32", survival="exp")
+    s.set_boundary("top", "inflow", w.inflow[0])
+    tau = torch_cuda.tensor(w.tau, dtype=torch_cuda.float32, device="cuda", requires_grad=True)
+    alb = torch_cuda.tensor(w.albedo, dtype=torch_cuda.float32, device="cuda", requires_grad=True)
+    g = torch_cuda.tensor(0.85, dtype=torch_cuda.float64, device="cuda", requires_grad=True)
+    out = top_radiance(tau, alb, g, s, w.phase_specs, hg_index=1, phase_index=w.phase_index, nsteps=w.steps,
+                       checkpoint_every=20)
+    weight = torch_cuda.linspace(0.5, 1.5, out.numel(), device="cuda").reshape(out.shape)
+    (out * weight).sum().backward()
+    P = oracle_problem(orc, w)
+    rt, ra, _ = P.adjoint(np.zeros((w.nz, w.nx, w.n, 4)), w.steps, weight.cpu().numpy().astype(np.float64))
+    assert _rel(tau.grad.cpu().numpy(), rt) < TOL
+    assert _rel(alb.grad.cpu().numpy(), ra) < TOL
+    h = 1e-4
+    vals = []
+    for sgn in (1, -1):
+        ww = W.adjoint(steps=60).crop(118, 134, 40, 60)
+        ww.phase_specs = [("rayleigh",), ("hg", 0.85 + sgn * h, -0.1)]
+        Pp = oracle_problem(orc, ww)
+        top = Pp.radiance_out(Pp.run(np.zeros((w.nz, w.nx, w.n, 4)), w.steps), orc.SIDE_TOP)
+        vals.append(float(np.sum(weight.cpu().numpy() * top)))
+    assert g.grad.item() == pytest.approx((vals[0] - vals[1]) / (2 * h), rel=1e-4)
+    s.close()
