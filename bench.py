@@ -94,6 +94,22 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def job_value(local_ms: float, sdu_per_rank: float, device=None):
+    """Whole-job throughput: every rank advances its own lattice (no data-path
+    collective); the job time is the slowest rank's (max-reduced), the value
+    is all ranks' site-direction updates over that time.  Returns (t_max_ms,
+    value)."""
+    import torch
+    import torch.distributed as dist
+    ws = dist.get_world_size() if dist.is_initialized() else 1
+    t_max = float(local_ms)
+    if ws > 1:
+        t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    return t_max, ws * sdu_per_rank / (t_max * 1e-3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -315,13 +331,7 @@ def run_ours(args):
     per_launch, total_ms = _time_steps(torch, s, stream, args.steps)
     barrier()
     clocks = sampler.stop()
-    t_max = total_ms
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = ws * sdu_per_step * args.steps / (t_max * 1e-3)
+    t_max, value = job_value(total_ms, sdu_per_step * args.steps, device=dev)
 
     # end to end through the public API with host buffers: each step uploads
     # the state from pinned host memory, advances one step and reads the top
