@@ -209,8 +209,17 @@ rtlb_status rtlb_stream_offsets(const rtlb_directions *dirs, int32_t *cx, int32_
 /* Normalized Rayleigh table (Eq. 13-17 with Eq. 16 and the rotation of Eq. 21):
  * Z_out[4n][4n] host float64.  Block (o, i) = R(-psi_o) P~(theta) R(psi_i)
  * divided by sum_o' P~11(theta(o', i)); psi is the angle between the local
- * meridian plane and the scattering plane. */
-rtlb_status rtlb_phase_rayleigh(const rtlb_directions *dirs, double *Z_out);
+ * meridian plane and the scattering plane.  depol in [0, 0.5): molecular
+ * depolarization factor (Hansen & Travis 1974 form of the Rayleigh matrix; 0
+ * gives Eq. 16 exactly); otherwise RTLB_E_RANGE. */
+rtlb_status rtlb_phase_rayleigh(const rtlb_directions *dirs, double depol, double *Z_out);
+
+/* Intensity-conserving correction of a normalized table Z[4n][4n] (host,
+ * in place): on a discrete angular grid the I rows of the Q, U, V columns do
+ * not sum to zero, so polarized light changes the total intensity even at
+ * albedo 1; each such I-row entry Z(o, i)_{I,k} loses Z(o, i)_{I,I} times its
+ * column sum, which makes the sums vanish and keeps sum_o Z_{I,I} = 1. */
+rtlb_status rtlb_phase_conserve_intensity(int32_t n, double *Z_inout);
 
 /* Henyey-Greenstein weighted Mueller table for cloud cells: HG(theta; g) times
  * [[1,p,0,0],[p,1,0,0],[0,0,q,0],[0,0,0,q]], p = pol_amp sin^2(theta),

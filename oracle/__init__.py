@@ -20,7 +20,7 @@ SURV_LINEAR, SURV_EXP = 0, 1
 ABS_BEER_LAMBERT, ABS_TAYLOR = 0, 1
 BC_VACUUM, BC_PERIODIC, BC_INFLOW = 0, 1, 2
 SIDE_TOP, SIDE_BOTTOM, SIDE_LEFT, SIDE_RIGHT = 0, 1, 2, 3
-PHASE_RAYLEIGH, PHASE_HG = 0, 1
+PHASE_RAYLEIGH, PHASE_HG, PHASE_RAYLEIGH_DEPOL = 0, 1, 2
 
 _lib = None
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -54,6 +54,8 @@ def lib():
         L.orc_dop.argtypes = [_dp]
         L.orc_dop.restype = C.c_double
         L.orc_num_threads.restype = C.c_int
+        L.orc_rayleigh_depol_matrix.argtypes = [C.c_double, C.c_double, _dp]
+        L.orc_conserve_intensity.argtypes = [C.c_int, _dp]
         L.orc_adjoint.argtypes = [C.c_int, C.c_int, C.c_int, _ip, _ip, _dp, _dp, C.c_void_p, C.c_void_p,
                                   _dp, C.c_int, C.c_int, C.c_int, _ip, _dp, _dp, C.c_int, _dp,
                                   _dp, _dp, _dp, C.c_void_p]
@@ -105,6 +107,19 @@ def hg_matrix(cos_t: float, g: float, pol_amp: float) -> np.ndarray:
     return P.reshape(4, 4)
 
 
+def rayleigh_depol_matrix(cos_t: float, rho: float) -> np.ndarray:
+    P = np.zeros(16)
+    lib().orc_rayleigh_depol_matrix(float(cos_t), float(rho), P)
+    return P.reshape(4, 4)
+
+
+def conserve_intensity(Z) -> np.ndarray:
+    """Intensity-conserving copy of a normalized table (see the C source)."""
+    Z = np.array(Z, np.float64, order="C", copy=True)
+    lib().orc_conserve_intensity(Z.shape[0] // 4, Z)
+    return Z
+
+
 def rpr_block(mu_o, phi_o, mu_i, phi_i, kind=PHASE_RAYLEIGH, g=0.0, pol_amp=0.0):
     """Un-normalized rotation-phase-rotation block M(o, i) and its scalar weight."""
     M = np.zeros(16)
@@ -125,10 +140,13 @@ def phase_table(mu, phi, kind=PHASE_RAYLEIGH, g=0.0, pol_amp=0.0) -> np.ndarray:
 
 
 def phase_table_spec(mu, phi, spec) -> np.ndarray:
-    """Table for a phase-class spec tuple: ("rayleigh",), ("hg", g, pol_amp) or
-    ("mix", m, g, pol_amp) = m * rayleigh + (1 - m) * hg (both normalized)."""
+    """Table for a phase-class spec tuple: ("rayleigh",) or ("rayleigh", rho)
+    with depolarization factor rho, ("hg", g, pol_amp) or ("mix", m, g,
+    pol_amp) = m * rayleigh + (1 - m) * hg (both normalized)."""
     kind = spec[0]
     if kind == "rayleigh":
+        if len(spec) > 1 and spec[1]:
+            return phase_table(mu, phi, PHASE_RAYLEIGH_DEPOL, spec[1])
         return phase_table(mu, phi, PHASE_RAYLEIGH)
     if kind == "hg":
         return phase_table(mu, phi, PHASE_HG, spec[1], spec[2])

@@ -44,7 +44,7 @@ enum { ORC_SURV_LINEAR = 0, ORC_SURV_EXP = 1 };
 enum { ORC_ABS_BEER_LAMBERT = 0, ORC_ABS_TAYLOR = 1 };
 enum { ORC_BC_VACUUM = 0, ORC_BC_PERIODIC = 1, ORC_BC_INFLOW = 2 };
 enum { ORC_SIDE_TOP = 0, ORC_SIDE_BOTTOM = 1, ORC_SIDE_LEFT = 2, ORC_SIDE_RIGHT = 3 };
-enum { ORC_PHASE_RAYLEIGH = 0, ORC_PHASE_HG = 1 };
+enum { ORC_PHASE_RAYLEIGH = 0, ORC_PHASE_HG = 1, ORC_PHASE_RAYLEIGH_DEPOL = 2 };
 
 /* ------------------------------------------------------------------ geometry */
 
@@ -128,6 +128,27 @@ void orc_hg_matrix(double cos_t, double g, double pol_amp, double P[16])
     P[15] = h * q;
 }
 
+/* Rayleigh matrix with molecular depolarization factor rho (Hansen & Travis
+ * 1974, Sec. 2): with D = (1 - rho) / (1 + rho / 2) and D' = (1 - 2 rho) /
+ * (1 - rho), and in the normalization of Eq. 16's P~ (2/3 of the phase matrix
+ * whose (1,1) element averages to one over the sphere),
+ *   P11 = D (1 + c^2) / 2 + (2/3)(1 - D),  P12 = P21 = -D (1 - c^2) / 2,
+ *   P22 = D (1 + c^2) / 2,  P33 = D c,  P44 = D D' c.
+ * rho = 0 gives Eq. 16. */
+void orc_rayleigh_depol_matrix(double cos_t, double rho, double P[16])
+{
+    double D = (1.0 - rho) / (1.0 + 0.5 * rho);
+    double Dp = (1.0 - 2.0 * rho) / (1.0 - rho);
+    double c2 = cos_t * cos_t;
+    memset(P, 0, 16 * sizeof(double));
+    P[0] = 0.5 * D * (1.0 + c2) + (2.0 / 3.0) * (1.0 - D);
+    P[1] = -0.5 * D * (1.0 - c2);
+    P[4] = P[1];
+    P[5] = 0.5 * D * (1.0 + c2);
+    P[10] = D * cos_t;
+    P[15] = D * Dp * cos_t;
+}
+
 static void matmul4(const double A[16], const double B[16], double C[16])
 {
     double T[16];
@@ -171,6 +192,7 @@ void orc_rpr_block(double mu_o, double phi_o, double mu_i, double phi_i,
     if (cos_t > 1.0) cos_t = 1.0;
     if (cos_t < -1.0) cos_t = -1.0;
     if (kind == ORC_PHASE_RAYLEIGH) orc_rayleigh_matrix(cos_t, P);
+    else if (kind == ORC_PHASE_RAYLEIGH_DEPOL) orc_rayleigh_depol_matrix(cos_t, g, P);   /* g carries rho */
     else orc_hg_matrix(cos_t, g, pol_amp, P);
     *w = P[0];
     n[0] = vi[1] * vo[2] - vi[2] * vo[1];
@@ -211,6 +233,23 @@ void orc_phase_table(int n, const double *mu, const double *phi,
             for (int k = 0; k < 4; ++k)
                 Z[(size_t)row * K + 4 * i + k] /= wcol[i];
     free(wcol);
+}
+
+/* Intensity-conserving variant of a normalized table: on a discrete grid the
+ * Q -> I column sums sum_o Z12(o, i) are not zero, so polarized light changes
+ * the total intensity at albedo 1.  Subtract Z11(o, i) * sum_o' Z12(o', i) from
+ * every Z12(o, i) (and likewise for the U and V columns), which makes those
+ * sums vanish while keeping sum_o Z11 = 1. */
+void orc_conserve_intensity(int n, double *Z)
+{
+    int K = 4 * n;
+    for (int i = 0; i < n; ++i)
+        for (int k = 1; k < 4; ++k) {
+            double sum = 0.0;
+            for (int o = 0; o < n; ++o) sum += Z[(size_t)(4 * o) * K + 4 * i + k];
+            for (int o = 0; o < n; ++o)
+                Z[(size_t)(4 * o) * K + 4 * i + k] -= Z[(size_t)(4 * o) * K + 4 * i] * sum;
+        }
 }
 
 /* ---------------------------------------------------------------- time step */

@@ -27,7 +27,7 @@ EXPORTS = [
     "rtlb_step", "rtlb_run_to_steady", "rtlb_last_residual", "rtlb_radiance_out",
     "rtlb_total_intensity", "rtlb_steps_done", "rtlb_last_error", "rtlb_destroy",
     "rtlb_stream_offsets", "rtlb_phase_rayleigh", "rtlb_phase_hg", "rtlb_phase_mix",
-    "rtlb_residual_noalloc", "rtlb_adjoint",
+    "rtlb_residual_noalloc", "rtlb_adjoint", "rtlb_phase_conserve_intensity",
 ]
 
 
@@ -79,7 +79,8 @@ def lib() -> C.CDLL:
     L.rtlb_destroy.argtypes = [vp]
     L.rtlb_destroy.restype = None
     L.rtlb_stream_offsets.argtypes = [C.POINTER(Directions), vp, vp]
-    L.rtlb_phase_rayleigh.argtypes = [C.POINTER(Directions), vp]
+    L.rtlb_phase_rayleigh.argtypes = [C.POINTER(Directions), C.c_double, vp]
+    L.rtlb_phase_conserve_intensity.argtypes = [i32, vp]
     L.rtlb_phase_hg.argtypes = [C.POINTER(Directions), C.c_double, C.c_double, vp, vp]
     L.rtlb_phase_mix.argtypes = [C.POINTER(Directions), C.c_double, C.c_double, C.c_double, vp]
     L.rtlb_residual_noalloc.argtypes = [vp, vp, C.c_size_t, vp, vp]

@@ -633,14 +633,23 @@ rtlb_status rtlb_stream_offsets(const rtlb_directions *dirs, int32_t *cx, int32_
     return RTLB_OK;
 }
 
-rtlb_status rtlb_phase_rayleigh(const rtlb_directions *dirs, double *Z_out)
+rtlb_status rtlb_phase_rayleigh(const rtlb_directions *dirs, double depol, double *Z_out)
 {
     if (!Z_out) return RTLB_E_ARG;
+    if (!(depol >= 0.0 && depol < 0.5)) return RTLB_E_RANGE;
     std::vector<double> mu, phi;
     std::vector<int> x, z;
     rtlb_status st = build_dirs(dirs, mu, phi, x, z, nullptr);
     if (st != RTLB_OK && st != RTLB_E_AMBIGUOUS_STREAM) return st;
-    phase_rayleigh(mu, phi, Z_out);
+    phase_rayleigh(mu, phi, depol, Z_out);
+    return RTLB_OK;
+}
+
+rtlb_status rtlb_phase_conserve_intensity(int32_t n, double *Z_inout)
+{
+    if (!Z_inout) return RTLB_E_ARG;
+    if (n < 1 || n > kMaxDirs) return RTLB_E_SHAPE;
+    conserve_intensity(n, Z_inout);
     return RTLB_OK;
 }
 
@@ -666,7 +675,7 @@ rtlb_status rtlb_phase_mix(const rtlb_directions *dirs, double m, double g, doub
     if (st != RTLB_OK && st != RTLB_E_AMBIGUOUS_STREAM) return st;
     const size_t len = 16 * mu.size() * mu.size();
     std::vector<double> zr(len), zh(len);
-    phase_rayleigh(mu, phi, zr.data());
+    phase_rayleigh(mu, phi, 0.0, zr.data());
     phase_hg(mu, phi, g, pol_amp, zh.data(), nullptr);
     for (size_t j = 0; j < len; ++j) Z_out[j] = m * zr[j] + (1.0 - m) * zh[j];
     return RTLB_OK;

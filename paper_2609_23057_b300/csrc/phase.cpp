@@ -96,16 +96,24 @@ void frame_cs(const Vec3 &nrm, const Dir &d, double *c2, double *s2)
     *s2 = 2.0 * s * c;
 }
 
-// Single-scattering matrix in the scattering plane, stored as its four
-// distinct entries: [[a,b,0,0],[b,a,0,0],[0,0,cu,0],[0,0,0,cv]].
+// Single-scattering matrix in the scattering plane, stored as its distinct
+// entries: [[a,b,0,0],[b,a2,0,0],[0,0,cu,0],[0,0,0,cv]].
 struct Scat {
-    double a, b, cu, cv;
+    double a, b, a2, cu, cv;
 };
 
-Scat rayleigh(double ct)
+// Rayleigh matrix with molecular depolarization rho in the normalization of
+// Eq. 16's P~ (Hansen & Travis 1974): the anisotropic part is weighted by
+// D = (1 - rho) / (1 + rho / 2), an isotropic (2/3)(1 - D) joins the (1,1)
+// element, and circular polarization is further reduced by
+// D' = (1 - 2 rho) / (1 - rho).  rho = 0 is Eq. 16.
+Scat rayleigh(double ct, double rho)
 {
     const double c2 = ct * ct;
-    return {0.5 * (1.0 + c2), -0.5 * (1.0 - c2), ct, ct};
+    const double D = (1.0 - rho) / (1.0 + 0.5 * rho);
+    const double Dv = D * (1.0 - 2.0 * rho) / (1.0 - rho);
+    const double an = 0.5 * D * (1.0 + c2);
+    return {an + (2.0 / 3.0) * (1.0 - D), -0.5 * D * (1.0 - c2), an, D * ct, Dv * ct};
 }
 
 double hg_phase(double ct, double g) { return (1.0 - g * g) / std::pow(1.0 + g * g - 2.0 * g * ct, 1.5); }
@@ -125,12 +133,12 @@ void rotated_block(const Scat &S, double ci, double si, double co, double so, do
     M[2] = S.b * si;
     M[3] = 0.0;
     M[4] = co * S.b;
-    M[5] = co * S.a * ci + so * S.cu * si;
-    M[6] = co * S.a * si - so * S.cu * ci;
+    M[5] = co * S.a2 * ci + so * S.cu * si;
+    M[6] = co * S.a2 * si - so * S.cu * ci;
     M[7] = 0.0;
     M[8] = so * S.b;
-    M[9] = so * S.a * ci - co * S.cu * si;
-    M[10] = so * S.a * si + co * S.cu * ci;
+    M[9] = so * S.a2 * ci - co * S.cu * si;
+    M[10] = so * S.a2 * si + co * S.cu * ci;
     M[11] = 0.0;
     M[12] = 0.0;
     M[13] = 0.0;
@@ -143,7 +151,7 @@ enum Kind { kRayleigh, kHG };
 // Fills the un-normalized blocks (and optionally their g-derivative, HG only),
 // then normalizes each incoming column.
 void build_table(const std::vector<double> &mu, const std::vector<double> &phi, Kind kind,
-                 double g, double pol_amp, double *Z, double *dZ)
+                 double g, double pol_amp, double rho, double *Z, double *dZ)
 {
     const int n = (int)mu.size();
     const size_t K = 4 * (size_t)n;
@@ -167,12 +175,12 @@ void build_table(const std::vector<double> &mu, const std::vector<double> &phi, 
             Scat S;
             double weight, weight_dg = 0.0;
             if (kind == kRayleigh) {
-                S = rayleigh(ct);
+                S = rayleigh(ct, rho);
                 weight = S.a;
             } else {
                 const double p = pol_amp * (1.0 - ct * ct);
                 const double q = std::sqrt(std::fmax(0.0, 1.0 - p * p));
-                S = {1.0, p, q, q};
+                S = {1.0, p, 1.0, q, q};
                 weight = hg_phase(ct, g);
                 weight_dg = hg_phase_dg(ct, g);
             }
@@ -205,15 +213,30 @@ void build_table(const std::vector<double> &mu, const std::vector<double> &phi, 
 
 }  // namespace
 
-void phase_rayleigh(const std::vector<double> &mu, const std::vector<double> &phi, double *Z)
+void phase_rayleigh(const std::vector<double> &mu, const std::vector<double> &phi, double rho, double *Z)
 {
-    build_table(mu, phi, kRayleigh, 0.0, 0.0, Z, nullptr);
+    build_table(mu, phi, kRayleigh, 0.0, 0.0, rho, Z, nullptr);
+}
+
+void conserve_intensity(int n, double *Z)
+{
+    // Per incoming (direction, Stokes k = Q, U, V) column, remove the part of
+    // the I row that does not sum to zero, in proportion to the I -> I
+    // weights (which sum to one).
+    const size_t K = 4 * (size_t)n;
+    for (int i = 0; i < n; ++i)
+        for (int k = 1; k < 4; ++k) {
+            const size_t col = 4 * (size_t)i + k, col_i = 4 * (size_t)i;
+            double excess = 0.0;
+            for (int o = 0; o < n; ++o) excess += Z[4 * (size_t)o * K + col];
+            for (int o = 0; o < n; ++o) Z[4 * (size_t)o * K + col] -= excess * Z[4 * (size_t)o * K + col_i];
+        }
 }
 
 void phase_hg(const std::vector<double> &mu, const std::vector<double> &phi, double g,
               double pol_amp, double *Z, double *dZdg)
 {
-    build_table(mu, phi, kHG, g, pol_amp, Z, dZdg);
+    build_table(mu, phi, kHG, g, pol_amp, 0.0, Z, dZdg);
 }
 
 }  // namespace rtlb

@@ -14,7 +14,8 @@ namespace rtlb {
 // ---- host geometry / tables (phase.cpp) ----
 void direction_grid(int n_zen, int n_az, std::vector<double> &mu, std::vector<double> &phi);
 int stream_offset(double mu, double phi, int *cx, int *cz);  // 1 = tie
-void phase_rayleigh(const std::vector<double> &mu, const std::vector<double> &phi, double *Z);
+void phase_rayleigh(const std::vector<double> &mu, const std::vector<double> &phi, double rho, double *Z);
+void conserve_intensity(int n, double *Z);
 void phase_hg(const std::vector<double> &mu, const std::vector<double> &phi, double g,
               double pol_amp, double *Z, double *dZdg);
 

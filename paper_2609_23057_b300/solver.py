@@ -39,11 +39,18 @@ def stream_offsets(n_zen: int, n_az: int, mu=None, phi=None):
     return cx, cz
 
 
-def phase_rayleigh(n_zen: int, n_az: int, mu=None, phi=None) -> np.ndarray:
+def phase_rayleigh(n_zen: int, n_az: int, mu=None, phi=None, depol: float = 0.0) -> np.ndarray:
     n = n_zen * n_az
     d, keep = _dirs(n_zen, n_az, mu, phi)
     Z = np.zeros((4 * n, 4 * n))
-    check(lib().rtlb_phase_rayleigh(C.byref(d), Z.ctypes.data))
+    check(lib().rtlb_phase_rayleigh(C.byref(d), float(depol), Z.ctypes.data))
+    return Z
+
+
+def conserve_intensity(Z) -> np.ndarray:
+    """Intensity-conserving copy of a normalized table (rtlb_phase_conserve_intensity)."""
+    Z = np.array(Z, np.float64, order="C", copy=True)
+    check(lib().rtlb_phase_conserve_intensity(Z.shape[0] // 4, Z.ctypes.data))
     return Z
 
 
@@ -66,10 +73,10 @@ def phase_mix(n_zen: int, n_az: int, m: float, g: float, pol_amp: float, mu=None
 
 
 def phase_table_spec(n_zen: int, n_az: int, spec, mu=None, phi=None) -> np.ndarray:
-    """Library table for a phase-class spec: ("rayleigh",), ("hg", g, pol_amp),
-    ("mix", m, g, pol_amp)."""
+    """Library table for a phase-class spec: ("rayleigh",), ("rayleigh", rho),
+    ("hg", g, pol_amp), ("mix", m, g, pol_amp)."""
     if spec[0] == "rayleigh":
-        return phase_rayleigh(n_zen, n_az, mu, phi)
+        return phase_rayleigh(n_zen, n_az, mu, phi, depol=spec[1] if len(spec) > 1 else 0.0)
     if spec[0] == "hg":
         return phase_hg(n_zen, n_az, spec[1], spec[2], mu, phi)
     if spec[0] == "mix":

@@ -50,7 +50,7 @@ def test_tie_is_rejected():
 
 
 @pytest.mark.parametrize("nzen,naz", [(2, 4), (4, 8), (8, 8), (3, 6)])
-@pytest.mark.parametrize("spec", [("rayleigh",), ("hg", 0.85, -0.1), ("mix", 0.4, 0.6, -0.1)])
+@pytest.mark.parametrize("spec", [("rayleigh",), ("rayleigh", 0.0279), ("hg", 0.85, -0.1), ("mix", 0.4, 0.6, -0.1)])
 def test_tables_match_oracle(orc, nzen, naz, spec):
     mu, phi = orc.direction_grid(nzen, naz)
     Zl = S.phase_table_spec(nzen, naz, spec)
@@ -83,9 +83,18 @@ def test_host_helper_argument_errors():
     L = _lib.lib()
     d = _lib.Directions(0, 4, None, None)
     Z = np.zeros(16)
-    assert L.rtlb_phase_rayleigh(C.byref(d), Z.ctypes.data) == 2           # RTLB_E_SHAPE
+    assert L.rtlb_phase_rayleigh(C.byref(d), 0.0, Z.ctypes.data) == 2      # RTLB_E_SHAPE
     d = _lib.Directions(2, 4, None, None)
     assert L.rtlb_phase_hg(C.byref(d), 1.5, -0.1, Z.ctypes.data, None) == 3  # RTLB_E_RANGE
-    assert L.rtlb_phase_rayleigh(C.byref(d), None) == 1                     # RTLB_E_ARG
+    assert L.rtlb_phase_rayleigh(C.byref(d), 0.0, None) == 1                # RTLB_E_ARG
+    assert L.rtlb_phase_rayleigh(C.byref(d), 0.7, Z.ctypes.data) == 3       # RTLB_E_RANGE
     big = _lib.Directions(32, 16, None, None)
     assert L.rtlb_stream_offsets(C.byref(big), Z.ctypes.data, Z.ctypes.data) == 2
+
+
+def test_conserve_intensity_matches_oracle(orc):
+    mu, phi = orc.direction_grid(4, 8)
+    for spec in [("rayleigh",), ("hg", 0.85, -0.1)]:
+        Zl = S.conserve_intensity(S.phase_table_spec(4, 8, spec))
+        Zo = orc.conserve_intensity(orc.phase_table_spec(mu, phi, spec))
+        assert np.abs(Zl - Zo).max() <= 1e-14 * max(1.0, np.abs(Zo).max())

@@ -472,3 +472,49 @@ def test_residual_and_radiance_out(orc):
     left = P.radiance_out(S, orc.SIDE_LEFT)
     for d in range(8):
         assert np.array_equal(left[:, d], S[:, 0, d] if P.cx[d] == -1 else 0 * S[:, 0, d])
+
+
+# ----------------------------------------------------------- table variants
+
+def test_depolarized_rayleigh_limits(orc):
+    """Hansen & Travis (1974) depolarized Rayleigh matrix: rho = 0 is Eq. 16;
+    the (1,1) element stays normalized over the sphere; unpolarized light
+    scattered at 90 deg has degree of polarization (1 - rho) / (1 + rho)."""
+    for c in (-0.7, 0.0, 0.3, 1.0):
+        assert np.allclose(orc.rayleigh_depol_matrix(c, 0.0), orc.rayleigh_matrix(c), atol=1e-15)
+    x, wq = np.polynomial.legendre.leggauss(64)
+    for rho in (0.0, 0.0279, 0.1):
+        vals = np.array([orc.rayleigh_depol_matrix(c, rho)[0, 0] for c in x])
+        assert abs(2 * math.pi * np.sum(wq * vals) * 3 / (8 * math.pi) - 1.0) < 1e-13
+        P = orc.rayleigh_depol_matrix(0.0, rho)
+        assert abs(abs(P[0, 1]) / P[0, 0] - (1 - rho) / (1 + rho)) < 1e-14
+
+
+def test_depolarized_table_keeps_normalization_and_cone(orc):
+    mu, phi = orc.direction_grid(4, 8)
+    Z = orc.phase_table_spec(mu, phi, ("rayleigh", 0.0279))
+    for i in range(32):
+        assert abs(Z[0::4, 4 * i].sum() - 1.0) < 1e-13
+    rng = np.random.default_rng(1)
+    v = rng.standard_normal((3, 100))
+    S = np.vstack([np.ones(100), v / np.linalg.norm(v, axis=0)])
+    for o in range(0, 32, 5):
+        for i in range(0, 32, 3):
+            out = Z[4 * o:4 * o + 4, 4 * i:4 * i + 4] @ S
+            assert np.all(out[0] + 1e-14 >= np.linalg.norm(out[1:], axis=0))
+
+
+def test_conservative_table_conserves_polarized_intensity(orc):
+    """With the intensity-conserving correction the total intensity is
+    conserved exactly at albedo 1 even for polarized light (the plain table
+    drifts by sum (1-s) (sum_o Z12) Q per step)."""
+    mu, phi = orc.direction_grid(2, 4)
+    Z = orc.conserve_intensity(orc.phase_table(mu, phi))
+    for i in range(8):
+        assert abs(Z[0::4, 4 * i].sum() - 1.0) < 1e-14
+        for k in (1, 2, 3):
+            assert abs(Z[0::4, 4 * i + k].sum()) < 1e-14
+    P = orc.Problem(5, 4, mu, phi, 0.4, 1.0, None, None, Z, bc=(1, 1, 1, 1))
+    S = W.random_state(4, 5, 8, seed=4)
+    tot0 = S[..., 0].sum()
+    assert P.run(S, 20)[..., 0].sum() == pytest.approx(tot0, rel=1e-13)

@@ -179,3 +179,35 @@ def test_error_codes(torch_cuda):
     with pytest.raises(_lib.RtlbError) as ei:
         s.set_boundary("top", "inflow", None)
     assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_table_variants(torch_cuda, orc, prec):
+    """Depolarized Rayleigh (rho = 0.0279) and the intensity-conserving
+    correction of an HG table: the library's own tables, run on the GPU,
+    against the oracle's tables and step."""
+    from paper_2609_23057_b300 import solver as SV
+    w = W.random_medium(150, 8, 4, 8, seed=13, bc=(2, 0, 1, 1), n_phase=2, steps=4)
+    w.phase_index = (np.arange(w.nz)[:, None] % 2 * np.ones((1, w.nx))).astype(np.uint8)
+    mu, phi = orc.direction_grid(4, 8)
+    Zo = np.stack([orc.phase_table_spec(mu, phi, ("rayleigh", 0.0279)),
+                   orc.conserve_intensity(orc.phase_table_spec(mu, phi, ("hg", 0.85, -0.1)))])
+    Zl = np.stack([SV.phase_rayleigh(4, 8, depol=0.0279),
+                   SV.conserve_intensity(SV.phase_hg(4, 8, 0.85, -0.1))])
+    P = orc.Problem(w.nx, w.nz, mu, phi, w.tau, w.albedo, w.emission, w.phase_index.astype(np.int32), Zo,
+                    surv_mode=w.surv_mode, bc=w.bc, inflow=w.inflow)
+    S0 = W.random_state(w.nz, w.nx, w.n, seed=14)
+    ref = P.run(S0, w.steps)
+    s = SV.Solver(w.nx, w.nz, 4, 8, precision=prec, survival="exp")
+    s.set_medium(w.tau.astype(np.float32), w.albedo.astype(np.float32), Zl,
+                 emission=w.emission.astype(np.float32), phase_index=w.phase_index)
+    for side in range(4):
+        s.set_boundary(side, w.bc[side], w.inflow[side] if w.bc[side] == 2 else None)
+    s.set_state(torch_cuda.from_numpy(S0.astype(np.float32)).cuda())
+    s.step(w.steps)
+    s.total_intensity()
+    got = s.get_state().cpu().numpy().astype(np.float64)
+    s.close()
+    tol = TOL_I if prec == "fp32" else 5e-5
+    assert rel_err_I(got, ref) < tol
+    assert abs_err_dop(got, ref) < tol
