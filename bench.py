@@ -282,6 +282,37 @@ def adjoint_ratio(steps: int, headline: str):
     return out
 
 
+def batch_throughput(steps: int, count: int = 256):
+    """256 independent spectral channels (lattices from {64..512} x {64..256},
+    n in {8, 16, 32}, per-channel Rayleigh/HG mixtures), bf16 scattering with
+    float32 state, one persistent launch per step replayed from a CUDA graph;
+    pipeline depth from the autotuner.  Returns site-direction updates/s."""
+    import torch
+    from paper_2609_23057_b300.solver import Batch, autotune_batch, solver_for
+    ws = W.channels(count=count, steps=steps)
+    ss = [solver_for(w, "bf16") for w in ws]
+    b = Batch(ss)
+    stages = autotune_batch(b)
+    b.step(4)
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    b.step(steps)
+    e.record()
+    torch.cuda.synchronize()
+    b.check()
+    ms = a.elapsed_time(e)
+    sdu = b.site_direction_updates_per_step * steps
+    out = {"workload": f"{count} channels, n in {{8,16,32}}, bf16", "steps": steps, "ms": ms,
+           "value": sdu / (ms * 1e-3), "unit": UNIT, "stages": stages,
+           "sdu_per_step": b.site_direction_updates_per_step,
+           "gbs_algorithmic": sum((32.0 + 16.0 / s.n) * s.nx * s.nz * s.n for s in ss) * steps / (ms * 1e-3) / 1e9}
+    b.close()
+    for s in ss:
+        s.close()
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2609_23057_b300 import solver as SV
@@ -383,6 +414,8 @@ def run_ours(args):
             "compare": compare,
             "adjoint_over_forward": None,
         }
+        if ws == 1 and args.batch_steps > 0:
+            line["batch"] = batch_throughput(args.batch_steps)
         if ws == 1 and args.adjoint_steps > 0:
             adj = adjoint_ratio(args.adjoint_steps, args.precision)
             line["adjoint"] = adj
@@ -408,6 +441,8 @@ def main():
                     help="headline form; bf16x2 is the tensor-core form that meets 1e-3 on the crop")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the FP32 comparison form")
+    ap.add_argument("--batch-steps", type=int, default=500,
+                    help="steps of the 256-channel batch timing (0 = skip)")
     ap.add_argument("--adjoint-steps", type=int, default=1000,
                     help="steps of the 1024x256 adjoint timing (0 = skip)")
     ap.add_argument("--nx", type=int, default=2048, help="lattice width (profiling of smaller cases)")

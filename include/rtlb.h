@@ -176,6 +176,38 @@ int64_t rtlb_steps_done(const rtlb_ctx *ctx);
 const char *rtlb_last_error(const rtlb_ctx *ctx);
 void rtlb_destroy(rtlb_ctx *ctx);
 
+/* ---- many lattices in one launch ----
+ *
+ * A batch advances many independent contexts (e.g. spectral channels with
+ * their own grid, n, medium and tables) with one persistent tensor-core
+ * launch per step: the single-class 128-site tiles of all channels form one
+ * work list, each item fetching its channel's pointers, TMA maps and tables
+ * from a descriptor.  All channels must use the same tensor-core precision
+ * (BF16 or BF16X2), n in {8, 16, 32} (n = 8, 16, 32 may be mixed), have a
+ * medium set, live on the same device and stand at the same step parity.
+ * Tiles mixing phase classes run on the CUDA-core kernel in the same step.
+ * Channels keep working as ordinary contexts (get_state, radiance_out, ...);
+ * stepping one alone desynchronizes the batch (rtlb_batch_step then returns
+ * RTLB_E_STATE).  Changing a channel's medium or boundaries requires a new
+ * batch. */
+typedef struct rtlb_batch rtlb_batch;
+rtlb_status rtlb_batch_create(int32_t count, rtlb_ctx *const *channels, rtlb_batch **out);
+
+/* Shared-memory pipeline depth of the batch kernel (16-KB state stages, 2..8;
+ * default 4).  Results do not depend on it. */
+rtlb_status rtlb_batch_configure(rtlb_batch *batch, int32_t stages);
+
+/* Advance every channel nsteps steps on `stream`; pairs of steps replay a
+ * captured CUDA graph (one persistent launch per step plus any mixed-tile
+ * launches). */
+rtlb_status rtlb_batch_step(rtlb_batch *batch, int32_t nsteps, void *stream);
+
+/* Reads (synchronizing) and clears the batch kernel's error flag:
+ * RTLB_E_TIMEOUT when a bounded wait gave up. */
+rtlb_status rtlb_batch_check(rtlb_batch *batch, void *stream);
+const char *rtlb_batch_last_error(const rtlb_batch *batch);
+void rtlb_batch_destroy(rtlb_batch *batch);
+
 /* ---- residual without allocation (the paper has no counterpart) ----
  *
  * Same float64 residual as rtlb_last_residual, for callers that must not

@@ -41,27 +41,14 @@
 #include "step_common.cuh"
 #include "tc.h"
 #include "tc_ptx.cuh"
+#include "tc_common.cuh"
 
 namespace rtlb {
 
 namespace {
 
 using namespace tcptx;
-
-constexpr int kTileM = 128;
-constexpr int kWarps = 14;
-constexpr int kEpiWarps = 8;
-constexpr int kConvWarp0 = 8;
-constexpr int kProdWarp = 12;
-constexpr int kMmaWarp = 13;
-constexpr int kThreads = kWarps * 32;
-constexpr int kDirsPerStage = 8;                    // directions per state chunk
-constexpr int kStageBytes = kDirsPerStage * kTileM * 16;
-constexpr int kHalfSites = 64;                      // sites per TMA box row (256 floats)
-constexpr int kSmemLimit = 232448;                  // max dynamic smem per block
-
-
-enum ErrCode { kErrTimeoutProducer = 1, kErrTimeoutConverter = 2, kErrTimeoutMma = 4, kErrTimeoutEpilogue = 8 };
+using namespace tccommon;
 
 struct TcState {
     int N4 = 0, KP = 0, C = 0, n_phase = 0;
@@ -97,96 +84,6 @@ struct TcParams {
     int *err;
 };
 
-// Converter work for one tile (one site row per thread, TMEM lane r).  For
-// each 64-wide K chunk of the A operand (16 directions = two staging slots)
-// it first drains both slots into registers -- writing the float32 part
-// (alpha_hi + alpha_lo + beta c_d) S~ into the TMEM accumulator and packing
-// beta S~ to bf16 -- and releases them, so the producer keeps loading while
-// the converter then waits for the MMA to free that A chunk.  Returns false
-// when a bounded wait gave up.
-template <bool ALO>
-__device__ __forceinline__ bool convert_tile(const float4 *coef_site, const float *fwd, int nsites, int site, int r,
-                                             int lane, int n, int groups, int stages, uint32_t &g, int i,
-                                             uint32_t acc, uint8_t *sA, uint8_t *sAlo, const uint8_t *sStage,
-                                             uint64_t *st_full, uint64_t *st_empty, uint64_t *a_empty,
-                                             uint32_t a_chunk, volatile int *abort_flag, int *err)
-{
-    const float4 cf = site < nsites ? *coef_site : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int half = r / kHalfSites, hr = r % kHalfSites;
-    const int C = (4 * n + 63) / 64;
-    for (int c = 0; c < C; ++c) {
-        const int d_beg = 16 * c, d_end = min(n, 16 * c + 16);
-        float fw[16];
-#pragma unroll
-        for (int k = 0; k < 16; k += 4) {
-            const float4 f = (d_beg + k < d_end) ? __ldg(reinterpret_cast<const float4 *>(fwd + d_beg + k))
-                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-            fw[k] = f.x;
-            fw[k + 1] = f.y;
-            fw[k + 2] = f.z;
-            fw[k + 3] = f.w;
-        }
-        uint4 packed[8], packed_lo[8];
-#pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-            const int j = 2 * c + jj;
-            if (j >= groups) break;
-            const int s = g % stages;
-            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&st_full[s]), (g / stages) & 1, abort_flag, err,
-                                                   kErrTimeoutConverter)))
-                return false;
-            const float4 *stg = reinterpret_cast<const float4 *>(sStage + (size_t)s * kStageBytes) +
-                                half * (kDirsPerStage * kHalfSites) + hr;
-#pragma unroll
-            for (int dl = 0; dl < kDirsPerStage; dl += 2) {
-                const int d = j * kDirsPerStage + dl;
-                float4 v0 = stg[dl * kHalfSites], v1 = stg[(dl + 1) * kHalfSites];
-                v0.x += cf.w;                               // emission (I only)
-                v1.x += cf.w;
-                const float sv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-                const int fi = jj * kDirsPerStage + dl;
-                const float g0 = fmaf(cf.z, fw[fi], cf.y), g1 = fmaf(cf.z, fw[fi + 1], cf.y);
-                float init[8], bs[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    init[k] = fmaf(cf.x, sv[k], (k < 4 ? g0 : g1) * sv[k]);   // exact float32 part
-                    bs[k] = cf.z * sv[k];                                       // beta S~ (MMA operand)
-                }
-                tmem_st8(acc + 4 * d, init);
-                uint4 hi;
-                hi.x = pack_bf16(bs[0], bs[1]);
-                hi.y = pack_bf16(bs[2], bs[3]);
-                hi.z = pack_bf16(bs[4], bs[5]);
-                hi.w = pack_bf16(bs[6], bs[7]);
-                packed[fi >> 1] = hi;
-                if (ALO) {
-                    const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&hi);
-                    uint32_t *lw = reinterpret_cast<uint32_t *>(&packed_lo[fi >> 1]);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const float2 f = __bfloat1622float2(h2[k]);
-                        lw[k] = pack_bf16(bs[2 * k] - f.x, bs[2 * k + 1] - f.y);
-                    }
-                }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&st_empty[s]));
-            ++g;
-        }
-        // A chunk c is free once the previous tile's MMAs on it completed
-        if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&a_empty[c]), (i & 1) ^ 1, abort_flag, err, kErrTimeoutConverter)))
-            return false;
-#pragma unroll
-        for (int gi = 0; gi < 8; ++gi) {
-            if (d_beg + 2 * gi >= d_end) break;
-            const uint32_t off = c * a_chunk + r * 128u + (((uint32_t)gi ^ (uint32_t)(r & 7)) << 4);
-            *reinterpret_cast<uint4 *>(sA + off) = packed[gi];
-            if (ALO) *reinterpret_cast<uint4 *>(sAlo + off) = packed_lo[gi];
-        }
-    }
-    return true;
-}
-
 // MODE 1: bf16 operands; 2: bf16 state operand, table as bf16 hi + lo (two
 // MMAs); 3: both operands hi + lo (three MMAs).
 template <int MODE>
@@ -218,7 +115,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *acc_empty = acc_full + 2;        // [2]
     uint64_t *z_full = acc_empty + 2;          // [1]
     uint64_t *drain = z_full + 1;              // [1]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    uint64_t *z_free = drain + 1;              // [1]  the resident table's last MMAs completed
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(z_free + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     int8_t *s_cx = reinterpret_cast<int8_t *>(tmem_slot + 2);   // [n]
     int8_t *s_cz = s_cx + kMaxDirs;                              // [n]
@@ -239,6 +137,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         mbar_init(smem_u32(z_full), 1);
         mbar_init(smem_u32(drain), 1);
+        mbar_init(smem_u32(z_free), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -261,14 +160,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             int prev_cls = -1;
-            uint32_t g = 0;
+            uint32_t g = 0, zr = 0;
             bool ok = true;
             for (int i = 0; i < T && ok; ++i) {
                 const int e = p.tiles[t_begin + i];
                 const int tile = e & 0xFFFFFF, cls = e >> 24;
                 if (cls != prev_cls) {
-                    if (i > 0)
-                        ok = mbar_wait(smem_u32(&acc_full[(i - 1) & 1]), ((i - 1) >> 1) & 1, abort_flag, p.err, kErrTimeoutProducer);
+                    // the MMA thread signals z_free once per table switch, after
+                    // the previous table's last MMAs (one phase per switch, so
+                    // the wait cannot alias however far ahead this thread runs)
+                    if (i > 0) ok = mbar_wait(smem_u32(z_free), (zr++) & 1, abort_flag, p.err, kErrTimeoutProducer);
                     if (!ok) break;
                     const uint32_t zb = smem_u32(z_full);
                     mbar_expect_tx(zb, (ZLO ? 2u : 1u) * C * z_chunk);
@@ -338,6 +239,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mma_commit(smem_u32(&a_empty[c]));
                 }
                 mma_commit(smem_u32(&acc_full[b]));
+                if (i + 1 < T && (p.tiles[t_begin + i + 1] >> 24) != cls) mma_commit(smem_u32(z_free));
                 issued = true;
             }
             if (issued) {
@@ -468,7 +370,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     uint64_t *acc_empty = acc_full + 2;        // [2]   local epilogue warps
     uint64_t *z_full = acc_empty + 2;          // [1]   even CTA: own TMA + odd CTA's forward
     uint64_t *drain = z_full + 1;              // [1]   multicast commit
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    uint64_t *z_free = drain + 1;              // [1]   multicast commit: the resident table is no longer read
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(z_free + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     int8_t *s_cx = reinterpret_cast<int8_t *>(tmem_slot + 2);
     int8_t *s_cz = s_cx + kMaxDirs;
@@ -489,6 +392,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         }
         mbar_init(smem_u32(z_full), leader ? 2 : 1);
         mbar_init(smem_u32(drain), 1);
+        mbar_init(smem_u32(z_free), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -514,13 +418,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     if (warp == kProdWarp) {
         if (lane == 0) {
             int prev_cls = -1;
-            uint32_t g = 0, zl = 0;
+            uint32_t g = 0, zl = 0, zr = 0;
             bool ok = true;
             for (int i = 0; i < T && ok; ++i) {
                 const int tile = my_tile(i), cls = pair_cls(i);
                 if (cls != prev_cls) {
-                    if (i > 0)
-                        ok = mbar_wait(smem_u32(&acc_full[(i - 1) & 1]), ((i - 1) >> 1) & 1, abort_flag, p.err, kErrTimeoutProducer);
+                    if (i > 0) ok = mbar_wait(smem_u32(z_free), (zr++) & 1, abort_flag, p.err, kErrTimeoutProducer);
                     if (!ok) break;
                     const uint32_t zb = smem_u32(z_full);
                     mbar_expect_tx(zb, 2u * C * z_chunk);
@@ -585,6 +488,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     mma_commit_pair(smem_u32(&a_empty[c]), 0x3);
                 }
                 mma_commit_pair(smem_u32(&acc_full[b]), 0x3);
+                if (i + 1 < T && pair_cls(i + 1) != cls) mma_commit_pair(smem_u32(z_free), 0x3);
                 issued = true;
             }
             if (issued) mma_commit_pair(smem_u32(drain), 0x3);
@@ -739,7 +643,7 @@ size_t smem_bytes(int N4, int mode, int stages)
 {
     const int C = (N4 + 63) / 64;
     size_t b = (size_t)C * N4 * 128 * (mode >= 2 ? 2 : 1) + (size_t)C * kTileM * 128 * (mode == 3 ? 2 : 1) +
-               (size_t)stages * kStageBytes + (size_t)(2 * stages + C + 8) * 8 + 16 + 2 * kMaxDirs;
+               (size_t)stages * kStageBytes + (size_t)(2 * stages + C + 9) * 8 + 16 + 2 * kMaxDirs;
     return b + 1024;  // alignment slack
 }
 
@@ -747,7 +651,7 @@ size_t smem_bytes_pair(int N4, int stages)
 {
     const int C = (N4 + 63) / 64;
     size_t b = (size_t)C * (N4 / 2) * 128 * 2 + (size_t)C * kTileM * 128 + (size_t)stages * kStageBytes +
-               (size_t)(2 * stages + C + 8) * 8 + 16 + 2 * kMaxDirs;
+               (size_t)(2 * stages + C + 9) * 8 + 16 + 2 * kMaxDirs;
     return b + 1024;
 }
 
@@ -1018,6 +922,33 @@ rtlb_status tc_check_error(rtlb_ctx *c, cudaStream_t s)
         return RTLB_E_TIMEOUT;
     }
     return RTLB_OK;
+}
+
+bool tc_encode_state_map(CUtensorMap *m, const float *S, size_t nsites, int n) { return encode_state_map(m, S, nsites, n); }
+
+bool tc_table_maps(const rtlb_ctx *c, CUtensorMap *zhi, CUtensorMap *zlo, const float **fwd)
+{
+    const TcState *t = static_cast<const TcState *>(c->tc);
+    if (!t || !t->d_Zhi || t->pair) return false;
+    *zhi = t->tmZhi;
+    *zlo = t->tmZlo;
+    *fwd = t->d_fwd;
+    return true;
+}
+
+bool tc_pure_tiles(const rtlb_ctx *c, std::vector<int> &out)
+{
+    const TcState *t = static_cast<const TcState *>(c->tc);
+    if (!t || t->pair) return false;
+    out.assign(t->n_pure, 0);
+    return t->n_pure == 0 || cudaMemcpy(out.data(), t->d_pure, t->n_pure * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+}
+
+void tc_mixed_list(const rtlb_ctx *c, const int **list, int *count)
+{
+    const TcState *t = static_cast<const TcState *>(c->tc);
+    *list = t ? t->d_mixed : nullptr;
+    *count = t ? t->n_mixed : 0;
 }
 
 int tc_mixed_tiles(const rtlb_ctx *c)

@@ -1,5 +1,8 @@
 // Tensor-core (tcgen05) forms of the fused step: operand tables and launch.
 #pragma once
+#include <cuda.h>
+#include <vector>
+
 #include "rtlb_internal.h"
 
 namespace rtlb {
@@ -19,4 +22,10 @@ rtlb_status tc_step(rtlb_ctx *c, const StepParams &p, cudaStream_t s);
 rtlb_status tc_check_error(rtlb_ctx *c, cudaStream_t s);
 int tc_mixed_tiles(const rtlb_ctx *c);
 void tc_release(rtlb_ctx *c);
+
+// For the multi-channel batch (single-CTA layout only, n <= 32):
+bool tc_encode_state_map(CUtensorMap *m, const float *S, size_t nsites, int n);
+bool tc_table_maps(const rtlb_ctx *c, CUtensorMap *zhi, CUtensorMap *zlo, const float **fwd);
+bool tc_pure_tiles(const rtlb_ctx *c, std::vector<int> &out);      // tile | class << 24
+void tc_mixed_list(const rtlb_ctx *c, const int **list, int *count);
 }  // namespace rtlb

@@ -70,7 +70,7 @@ __device__ __forceinline__ unsigned long long global_ns()
 // Bounded wait on one mbarrier phase.  Returns false (after raising the CTA's
 // abort flag and recording `code`) when the wait times out or another role
 // has already aborted.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err, int code)
+static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err, int code)
 {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
@@ -256,7 +256,7 @@ __device__ __forceinline__ bool mbar_try_cluster(uint32_t bar, uint32_t parity)
 }
 
 // Bounded wait with cluster-scope acquire (arrivals come from the peer CTA).
-__device__ __noinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err, int code)
+static __device__ __noinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err, int code)
 {
     if (mbar_try_cluster(bar, parity)) return true;
     const unsigned long long t0 = global_ns();

@@ -303,3 +303,97 @@ def top_radiance(tau, albedo, g, solver: Solver, specs, hg_index=None, phase_ind
     if _TOP_RADIANCE is None:
         _TOP_RADIANCE = _make_top_radiance_fn()
     return _TOP_RADIANCE.apply(tau, albedo, g, solver, specs, hg_index, phase_index, nsteps, checkpoint_every)
+
+
+class Batch:
+    """Several Solvers (same tensor-core precision, n <= 32) advanced by one
+    persistent launch per step (rtlb_batch_*)."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[s._ctx for s in self.solvers])
+        b = C.c_void_p()
+        check(lib().rtlb_batch_create(len(self.solvers), arr, C.byref(b)))
+        self._b = b
+        self.stages = 4
+
+    def _check(self, st):
+        if st != _lib.RTLB_OK:
+            raw = lib().rtlb_batch_last_error(self._b)
+            raise _lib.RtlbError(st, raw.decode() if raw else "")
+
+    def configure(self, stages: int):
+        self._check(lib().rtlb_batch_configure(self._b, int(stages)))
+        self.stages = int(stages)
+
+    def step(self, nsteps: int = 1, stream=None):
+        self._check(lib().rtlb_batch_step(self._b, int(nsteps), _stream(stream)))
+
+    def check(self, stream=None):
+        self._check(lib().rtlb_batch_check(self._b, _stream(stream)))
+
+    @property
+    def site_direction_updates_per_step(self) -> int:
+        return sum(s.nx * s.nz * s.n for s in self.solvers)
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().rtlb_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _tune_cache_path():
+    import os
+    return os.environ.get("RTLB_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "rtlb_tune.json")
+
+
+def autotune_batch(batch: Batch, candidates=(2, 3, 4, 6, 8), trial_steps: int = 4, cache_path=None) -> int:
+    """Pick the batch kernel's pipeline depth by timing `trial_steps` real
+    steps per candidate (every candidate computes the same result, so the
+    channels simply advance), remember the choice in a JSON cache keyed by
+    device, precision and workload shape, and apply it."""
+    import json
+    import os
+
+    import torch
+    path = cache_path or _tune_cache_path()
+    sig = {"device": torch.cuda.get_device_name(), "precision": batch.solvers[0].precision,
+           "n": sorted({s.n for s in batch.solvers}), "channels": len(batch.solvers),
+           "sdu_per_step_log2": int(np.log2(max(1, batch.site_direction_updates_per_step)))}
+    key = json.dumps(sig, sort_keys=True)
+    try:
+        with open(path) as f:
+            cache = json.load(f)
+    except (OSError, ValueError):
+        cache = {}
+    if key in cache:
+        batch.configure(cache[key]["stages"])
+        return cache[key]["stages"]
+    best, best_ms = None, float("inf")
+    for st in candidates:
+        try:
+            batch.configure(st)
+        except _lib.RtlbError:
+            continue
+        batch.step(2)                          # capture + warm
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        batch.step(trial_steps)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / trial_steps
+        if ms < best_ms:
+            best, best_ms = st, ms
+    batch.configure(best)
+    cache[key] = {"stages": best, "ms_per_step": best_ms}
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    with open(path, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    return best
