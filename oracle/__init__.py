@@ -21,6 +21,7 @@ ABS_BEER_LAMBERT, ABS_TAYLOR = 0, 1
 BC_VACUUM, BC_PERIODIC, BC_INFLOW = 0, 1, 2
 SIDE_TOP, SIDE_BOTTOM, SIDE_LEFT, SIDE_RIGHT = 0, 1, 2, 3
 PHASE_RAYLEIGH, PHASE_HG, PHASE_RAYLEIGH_DEPOL = 0, 1, 2
+PLANE_XZ, PLANE_XY = 0, 1
 
 _lib = None
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -36,13 +37,19 @@ def lib():
         L.orc_direction_grid.argtypes = [C.c_int, C.c_int, _dp, _dp]
         L.orc_stream_offset.argtypes = [C.c_double, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.orc_stream_offset.restype = C.c_int
+        L.orc_plane_offset.argtypes = [C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.orc_plane_offset.restype = C.c_int
+        L.orc_lattice_projection.argtypes = [C.c_double, C.c_double, C.c_int, C.POINTER(C.c_double),
+                                             C.POINTER(C.c_double)]
+        L.orc_bilinear_taps.argtypes = [C.c_double, C.c_double, C.c_int, _ip, _ip, _dp,
+                                        C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.orc_rotation.argtypes = [C.c_double, _dp]
         L.orc_rayleigh_matrix.argtypes = [C.c_double, _dp]
         L.orc_hg_matrix.argtypes = [C.c_double, C.c_double, C.c_double, _dp]
         L.orc_rpr_block.argtypes = [C.c_double] * 4 + [C.c_int, C.c_double, C.c_double, _dp,
                                                        C.POINTER(C.c_double)]
         L.orc_phase_table.argtypes = [C.c_int, _dp, _dp, C.c_int, C.c_double, C.c_double, _dp]
-        step_args = [C.c_int, C.c_int, C.c_int, _ip, _ip, _dp, _dp, C.c_void_p, C.c_void_p,
+        step_args = [C.c_int, C.c_int, C.c_int, C.c_int, _ip, _ip, _dp, _dp, _dp, C.c_void_p, C.c_void_p,
                      _dp, C.c_int, C.c_int, _ip, _dp]
         L.orc_step.argtypes = step_args + [_dp, _dp]
         L.orc_run.argtypes = step_args + [_dp, C.c_int]
@@ -56,9 +63,9 @@ def lib():
         L.orc_num_threads.restype = C.c_int
         L.orc_rayleigh_depol_matrix.argtypes = [C.c_double, C.c_double, _dp]
         L.orc_conserve_intensity.argtypes = [C.c_int, _dp]
-        L.orc_adjoint.argtypes = [C.c_int, C.c_int, C.c_int, _ip, _ip, _dp, _dp, C.c_void_p, C.c_void_p,
-                                  _dp, C.c_int, C.c_int, C.c_int, _ip, _dp, _dp, C.c_int, _dp,
-                                  _dp, _dp, _dp, C.c_void_p]
+        L.orc_adjoint.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _ip, _ip, _dp, _ip, _dp, _dp,
+                                  C.c_void_p, C.c_void_p, _dp, C.c_int, C.c_int, C.c_int, _ip, _dp, _dp,
+                                  C.c_int, _dp, _dp, _dp, _dp, C.c_void_p]
         _lib = L
     return _lib
 
@@ -77,16 +84,40 @@ def direction_grid(n_zen: int, n_az: int):
     return mu, phi
 
 
-def stream_offsets(mu, phi):
+def stream_offsets(mu, phi, plane=PLANE_XZ):
     """Integer D2Q9 offsets (cx, cz) per direction; raises on a tie."""
     n = len(mu)
     cx, cz = np.zeros(n, np.int32), np.zeros(n, np.int32)
     for d in range(n):
         a, b = C.c_int(), C.c_int()
-        if lib().orc_stream_offset(float(mu[d]), float(phi[d]), C.byref(a), C.byref(b)):
+        if lib().orc_plane_offset(float(mu[d]), float(phi[d]), int(plane), C.byref(a), C.byref(b)):
             raise ValueError(f"direction {d} lies exactly between two lattice offsets")
         cx[d], cz[d] = a.value, b.value
     return cx, cz
+
+
+def lattice_projection(mu, phi, plane=PLANE_XZ):
+    """(px, pz) arrays: each direction's projection on the lattice plane."""
+    px, pz = np.zeros(len(mu)), np.zeros(len(mu))
+    for d in range(len(mu)):
+        a, b = C.c_double(), C.c_double()
+        lib().orc_lattice_projection(float(mu[d]), float(phi[d]), int(plane), C.byref(a), C.byref(b))
+        px[d], pz[d] = a.value, b.value
+    return px, pz
+
+
+def bilinear_taps(mu, phi, plane=PLANE_XZ):
+    """Semi-Lagrangian taps (Eq. 33-34): offsets ox, oz [n][4] (int32),
+    weights w [n][4] and the displacement lx, lz [n]."""
+    n = len(mu)
+    ox, oz, w = np.zeros((n, 4), np.int32), np.zeros((n, 4), np.int32), np.zeros((n, 4))
+    lx, lz = np.zeros(n), np.zeros(n)
+    for d in range(n):
+        a, b, c = np.zeros(4, np.int32), np.zeros(4, np.int32), np.zeros(4)
+        x, z = C.c_double(), C.c_double()
+        lib().orc_bilinear_taps(float(mu[d]), float(phi[d]), int(plane), a, b, c, C.byref(x), C.byref(z))
+        ox[d], oz[d], w[d], lx[d], lz[d] = a, b, c, x.value, z.value
+    return ox, oz, w, lx, lz
 
 
 def rotation(psi: float) -> np.ndarray:
@@ -160,17 +191,38 @@ def phase_table_spec(mu, phi, spec) -> np.ndarray:
 # ------------------------------------------------------------------ solver
 
 class Problem:
-    """Medium, geometry and boundaries of one lattice, in oracle form (float64)."""
+    """Medium, geometry and boundaries of one lattice, in oracle form (float64).
+
+    scheme "nearest" streams each direction to its nearest D2Q9 offset;
+    "bilinear" uses the four weighted translations of Eq. 34.  plane selects
+    the lattice plane the directions are projected on (PLANE_XZ or PLANE_XY).
+    """
 
     def __init__(self, nx, nz, mu, phi, tau, albedo, emission, cls, Z,
                  surv_mode=SURV_LINEAR, abs_mode=ABS_BEER_LAMBERT,
-                 bc=(BC_VACUUM,) * 4, inflow=None, offsets=None):
+                 bc=(BC_VACUUM,) * 4, inflow=None, offsets=None, scheme="nearest", plane=PLANE_XZ):
         self.nx, self.nz, self.n = int(nx), int(nz), len(mu)
         self.mu = np.ascontiguousarray(mu, np.float64)
         self.phi = np.ascontiguousarray(phi, np.float64)
-        cx, cz = offsets if offsets is not None else stream_offsets(self.mu, self.phi)
-        self.cx = np.ascontiguousarray(cx, np.int32)
-        self.cz = np.ascontiguousarray(cz, np.int32)
+        self.scheme, self.plane = scheme, int(plane)
+        if scheme == "nearest":
+            cx, cz = offsets if offsets is not None else stream_offsets(self.mu, self.phi, self.plane)
+            self.cx = np.ascontiguousarray(cx, np.int32)
+            self.cz = np.ascontiguousarray(cz, np.int32)
+            self.ntap = 1
+            self.tx, self.tz = self.cx.copy(), self.cz.copy()
+            self.tw = np.ones(self.n)
+        elif scheme == "bilinear":
+            ox, oz, w, lx, lz = bilinear_taps(self.mu, self.phi, self.plane)
+            self.ntap = 4
+            self.tx = np.ascontiguousarray(ox.ravel(), np.int32)
+            self.tz = np.ascontiguousarray(oz.ravel(), np.int32)
+            self.tw = np.ascontiguousarray(w.ravel(), np.float64)
+            # sense of motion per axis, for the readout and the adjoint seed
+            self.cx = np.ascontiguousarray(np.sign(lx), np.int32)
+            self.cz = np.ascontiguousarray(np.sign(lz), np.int32)
+        else:
+            raise ValueError(f"unknown streaming scheme {scheme!r}")
         shp = (self.nz, self.nx)
         own = lambda a, dt: np.array(np.broadcast_to(a, shp), dt, order="C", copy=True)
         self.tau = own(tau, np.float64)
@@ -193,7 +245,7 @@ class Problem:
     def _args(self):
         e = self.emission.ctypes.data if self.emission is not None else None
         c = self.cls.ctypes.data if self.cls is not None else None
-        return (self.nx, self.nz, self.n, self.cx, self.cz, self.tau, self.albedo, e, c,
+        return (self.nx, self.nz, self.n, self.ntap, self.tx, self.tz, self.tw, self.tau, self.albedo, e, c,
                 self.Z, self.surv_mode, self.abs_mode, self.bc, self.inflow)
 
     def zero_state(self) -> np.ndarray:
@@ -228,7 +280,8 @@ class Problem:
         gS = np.zeros_like(S0) if want_S0 else None
         e = self.emission.ctypes.data if self.emission is not None else None
         c = self.cls.ctypes.data if self.cls is not None else None
-        lib().orc_adjoint(self.nx, self.nz, self.n, self.cx, self.cz, self.tau, self.albedo, e, c,
+        lib().orc_adjoint(self.nx, self.nz, self.n, self.ntap, self.tx, self.tz, self.tw, self.cz,
+                          self.tau, self.albedo, e, c,
                           self.Z, self.Z.shape[0], self.surv_mode, self.abs_mode, self.bc, self.inflow,
                           S0, int(nsteps), dl, gt, ga, gZ, gS.ctypes.data if want_S0 else None)
         return (gt, ga, gZ, gS) if want_S0 else (gt, ga, gZ)

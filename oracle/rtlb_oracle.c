@@ -45,6 +45,7 @@ enum { ORC_ABS_BEER_LAMBERT = 0, ORC_ABS_TAYLOR = 1 };
 enum { ORC_BC_VACUUM = 0, ORC_BC_PERIODIC = 1, ORC_BC_INFLOW = 2 };
 enum { ORC_SIDE_TOP = 0, ORC_SIDE_BOTTOM = 1, ORC_SIDE_LEFT = 2, ORC_SIDE_RIGHT = 3 };
 enum { ORC_PHASE_RAYLEIGH = 0, ORC_PHASE_HG = 1, ORC_PHASE_RAYLEIGH_DEPOL = 2 };
+enum { ORC_PLANE_XZ = 0, ORC_PLANE_XY = 1 };
 
 /* ------------------------------------------------------------------ geometry */
 
@@ -67,15 +68,29 @@ static void unit_vector(double mu, double phi, double v[3])
     v[2] = mu;
 }
 
+/* Projection of a direction onto the lattice plane.  ORC_PLANE_XZ: the lattice
+ * spans x and the vertical z (the stratification axis), projection
+ * (sin(theta) cos(phi), mu).  ORC_PLANE_XY: the lattice is horizontal, as in
+ * the paper's 2D experiments (Sec. 3.2), projection (sin(theta) cos(phi),
+ * sin(theta) sin(phi)).  The second lattice axis is called z in both cases. */
+void orc_lattice_projection(double mu, double phi, int plane, double *px, double *pz)
+{
+    double v[3];
+    unit_vector(mu, phi, v);
+    *px = v[0];
+    *pz = (plane == ORC_PLANE_XY) ? v[1] : v[2];
+}
+
 /* D2Q9 streaming offset of one direction (Sec. 2.1, Fig. 1b/2: propagation along
- * (-1, 0, 1) on both lattice axes).  Returns 1 when the projection lies exactly
- * between two neighbour offsets (no nearest one), else 0. */
-int orc_stream_offset(double mu, double phi, int *cx, int *cz)
+ * (-1, 0, 1) on both lattice axes): the neighbour offset nearest by angle to
+ * the direction's projection on the lattice plane.  Returns 1 when the
+ * projection lies exactly between two neighbour offsets (no nearest one). */
+int orc_plane_offset(double mu, double phi, int plane, int *cx, int *cz)
 {
     static const int ox[8] = {1, 1, 0, -1, -1, -1, 0, 1};
     static const int oz[8] = {0, 1, 1, 1, 0, -1, -1, -1};
-    double px = sqrt(fmax(0.0, 1.0 - mu * mu)) * cos(phi);
-    double pz = mu;
+    double px, pz;
+    orc_lattice_projection(mu, phi, plane, &px, &pz);
     if (hypot(px, pz) < 1e-12) { *cx = 0; *cz = 0; return 0; }
     double t = atan2(pz, px) * (180.0 / ORC_PI) / 45.0;   /* angle in units of 45 deg */
     double f = t - floor(t);
@@ -85,6 +100,47 @@ int orc_stream_offset(double mu, double phi, int *cx, int *cz)
     *cx = ox[k];
     *cz = oz[k];
     return 0;
+}
+
+/* The same on the (x, z) plane. */
+int orc_stream_offset(double mu, double phi, int *cx, int *cz)
+{
+    return orc_plane_offset(mu, phi, ORC_PLANE_XZ, cx, cz);
+}
+
+/* Semi-Lagrangian bilinear streaming (Eq. 33-34).  Over one step a direction
+ * moves l = v dt / dx lattice units; with dt = dx / c (the paper's
+ * dt = min(1/N_x, 1/N_y) on a unit domain) l is the direction's projection on
+ * the lattice plane.  Per axis the move splits into an integer base n0 and a
+ * fraction f in [0, 1): n0 = floor(l), f = l - n0 (Eq. 34 asks 0 <= f < 1,
+ * which truncation towards zero would violate for l < 0).  The streamed field
+ * is sum over b_x, b_z in {0, 1} of w_x(b_x) w_z(b_z) T_(n0x + b_x, n0z + b_z),
+ * w(0) = 1 - f, w(1) = f, where T_c moves content by c cells (the value at x
+ * comes from x - c).  A component within 1e-12 of an integer is taken as that
+ * integer.  Outputs the four taps in the order (b_x, b_z) = (0,0), (1,0),
+ * (0,1), (1,1) and the displacement itself. */
+void orc_bilinear_taps(double mu, double phi, int plane, int ox[4], int oz[4], double w[4],
+                       double *lx_out, double *lz_out)
+{
+    double l[2];
+    orc_lattice_projection(mu, phi, plane, &l[0], &l[1]);
+    int base[2];
+    double frac[2];
+    for (int a = 0; a < 2; ++a) {
+        double r = floor(l[a] + 0.5);
+        if (fabs(l[a] - r) < 1e-12) l[a] = r;
+        base[a] = (int)floor(l[a]);
+        frac[a] = l[a] - base[a];
+    }
+    for (int bz = 0; bz < 2; ++bz)
+        for (int bx = 0; bx < 2; ++bx) {
+            int k = 2 * bz + bx;
+            ox[k] = base[0] + bx;
+            oz[k] = base[1] + bz;
+            w[k] = (bx ? frac[0] : 1.0 - frac[0]) * (bz ? frac[1] : 1.0 - frac[1]);
+        }
+    *lx_out = l[0];
+    *lz_out = l[1];
 }
 
 /* ----------------------------------------------------- Mueller matrices (4x4) */
@@ -295,9 +351,13 @@ static const double *upstream(int nx, int nz, int n, int x, int z, int d, int cx
 }
 
 /* One full step S_in -> S_out (emission, absorption, scattering, streaming).
- * bc[4] = kinds of top, bottom, left, right; periodic must be set on both
- * sides of an axis.  inflow[4][n][4] holds the ghost Stokes vectors. */
-void orc_step(int nx, int nz, int n, const int *cx, const int *cz,
+ * Streaming of direction d is the weighted sum of ntap translations: tap k
+ * moves content by (tx, tz)[d * ntap + k] cells with weight tw[d * ntap + k]
+ * (one tap of weight 1 for the nearest-offset scheme, the four taps of
+ * orc_bilinear_taps for the semi-Lagrangian one).  bc[4] = kinds of top,
+ * bottom, left, right; periodic must be set on both sides of an axis.
+ * inflow[4][n][4] holds the ghost Stokes vectors. */
+void orc_step(int nx, int nz, int n, int ntap, const int *tx, const int *tz, const double *tw,
               const double *tau, const double *albedo, const double *emis, const int *cls,
               const double *Z, int surv_mode, int abs_mode, const int *bc,
               const double *inflow, const double *S_in, double *S_out)
@@ -322,15 +382,20 @@ void orc_step(int nx, int nz, int n, const int *cx, const int *cz,
     for (int z = 0; z < nz; ++z)
         for (int x = 0; x < nx; ++x)
             for (int d = 0; d < n; ++d) {
-                const double *src = upstream(nx, nz, n, x, z, d, cx[d], cz[d], bc, inflow, P);
                 double *dst = S_out + (((size_t)z * nx + x) * n + d) * 4;
-                for (int s = 0; s < 4; ++s) dst[s] = src ? src[s] : 0.0;
+                for (int s = 0; s < 4; ++s) dst[s] = 0.0;
+                for (int k = 0; k < ntap; ++k) {
+                    int j = d * ntap + k;
+                    const double *src = upstream(nx, nz, n, x, z, d, tx[j], tz[j], bc, inflow, P);
+                    if (src)
+                        for (int s = 0; s < 4; ++s) dst[s] += tw[j] * src[s];
+                }
             }
     free(P);
 }
 
 /* Run nsteps steps in place on S (ping-pong through a scratch copy). */
-void orc_run(int nx, int nz, int n, const int *cx, const int *cz,
+void orc_run(int nx, int nz, int n, int ntap, const int *tx, const int *tz, const double *tw,
              const double *tau, const double *albedo, const double *emis, const int *cls,
              const double *Z, int surv_mode, int abs_mode, const int *bc,
              const double *inflow, double *S, int nsteps)
@@ -338,7 +403,7 @@ void orc_run(int nx, int nz, int n, const int *cx, const int *cz,
     size_t len = (size_t)nx * nz * n * 4;
     double *T = (double *)malloc(len * sizeof(double));
     for (int t = 0; t < nsteps; ++t) {
-        orc_step(nx, nz, n, cx, cz, tau, albedo, emis, cls, Z, surv_mode, abs_mode, bc,
+        orc_step(nx, nz, n, ntap, tx, tz, tw, tau, albedo, emis, cls, Z, surv_mode, abs_mode, bc,
                  inflow, S, T);
         memcpy(S, T, len * sizeof(double));
     }
@@ -359,8 +424,8 @@ double orc_residual(size_t len, const double *S_old, const double *S_new)
 
 /* Iterate to the steady state of Eq. 1 (time derivative zero): step until the
  * residual falls below tol or max_steps is reached.  Returns steps taken. */
-int orc_run_to_steady(int nx, int nz, int n, const int *cx, const int *cz,
-                      const double *tau, const double *albedo, const double *emis,
+int orc_run_to_steady(int nx, int nz, int n, int ntap, const int *tx, const int *tz,
+                      const double *tw, const double *tau, const double *albedo, const double *emis,
                       const int *cls, const double *Z, int surv_mode, int abs_mode,
                       const int *bc, const double *inflow, double *S, double tol,
                       int max_steps, double *residual)
@@ -370,7 +435,7 @@ int orc_run_to_steady(int nx, int nz, int n, const int *cx, const int *cz,
     int t = 0;
     double r = INFINITY;
     while (t < max_steps) {
-        orc_step(nx, nz, n, cx, cz, tau, albedo, emis, cls, Z, surv_mode, abs_mode, bc,
+        orc_step(nx, nz, n, ntap, tx, tz, tw, tau, albedo, emis, cls, Z, surv_mode, abs_mode, bc,
                  inflow, S, T);
         r = orc_residual(len, S, T);
         memcpy(S, T, len * sizeof(double));
@@ -383,8 +448,10 @@ int orc_run_to_steady(int nx, int nz, int n, const int *cx, const int *cz,
 }
 
 /* Outgoing radiance on one side: the state on the boundary row/column for the
- * directions whose streaming offset leaves the domain through that side; zero
- * for the other directions.  out[len][n][4], len = nx (top/bottom) or nz. */
+ * directions that move out through that side; zero for the other directions.
+ * (cx, cz) is each direction's sense of motion per axis (-1, 0, +1): its
+ * offset in the nearest-offset scheme, the sign of its displacement in the
+ * bilinear one.  out[len][n][4], len = nx (top/bottom) or nz. */
 void orc_radiance_out(int nx, int nz, int n, const int *cx, const int *cz, int side,
                       const double *S, double *out)
 {
@@ -450,10 +517,12 @@ static void coef_derivatives(double tau, double w, int surv_mode, int abs_mode, 
  * phase-table entry, and the initial state.  All intermediate states are
  * kept (small lattices only).  The step is affine,
  *   S^{t+1} = T (C S^t + c0) + b,  C = blockdiag(alpha I + beta Z_c),
- * so lambda^t = C^T T^T lambda^{t+1}; T^T pulls from each entry's
- * streaming target (zero when the vector left through a non-periodic side). */
-void orc_adjoint(int nx, int nz, int n, const int *cx, const int *cz,
-                 const double *tau, const double *albedo, const double *emis, const int *cls,
+ * so lambda^t = C^T T^T lambda^{t+1}; T^T pulls from each entry's streaming
+ * targets with the taps' weights (zero where the content left through a
+ * non-periodic side).  Taps as in orc_step; sense_z[d] = +1 marks the
+ * directions that leave through the top (the radiance_out rows). */
+void orc_adjoint(int nx, int nz, int n, int ntap, const int *tx, const int *tz, const double *tw,
+                 const int *sense_z, const double *tau, const double *albedo, const double *emis, const int *cls,
                  const double *Z, int n_phase, int surv_mode, int abs_mode, const int *bc,
                  const double *inflow, const double *S0, int nsteps, const double *dL_dout,
                  double *grad_tau, double *grad_albedo, double *grad_Z, double *grad_S0)
@@ -463,8 +532,8 @@ void orc_adjoint(int nx, int nz, int n, const int *cx, const int *cz,
     double *states = (double *)malloc((size_t)(nsteps + 1) * len * sizeof(double));
     memcpy(states, S0, len * sizeof(double));
     for (int t = 0; t < nsteps; ++t)
-        orc_step(nx, nz, n, cx, cz, tau, albedo, emis, cls, Z, surv_mode, abs_mode, bc, inflow,
-                 states + (size_t)t * len, states + (size_t)(t + 1) * len);
+        orc_step(nx, nz, n, ntap, tx, tz, tw, tau, albedo, emis, cls, Z, surv_mode, abs_mode, bc,
+                 inflow, states + (size_t)t * len, states + (size_t)(t + 1) * len);
     double *lam = (double *)calloc(len, sizeof(double));
     double *mu = (double *)malloc(len * sizeof(double));
     double *ga = (double *)calloc(nsite, sizeof(double));
@@ -473,7 +542,7 @@ void orc_adjoint(int nx, int nz, int n, const int *cx, const int *cz,
     /* seed: the top row's outgoing directions */
     for (int x = 0; x < nx; ++x)
         for (int d = 0; d < n; ++d)
-            if (cz[d] == 1)
+            if (sense_z[d] == 1)
                 for (int s = 0; s < 4; ++s)
                     lam[(((size_t)(nz - 1) * nx + x) * n + d) * 4 + s] = dL_dout[((size_t)x * n + d) * 4 + s];
     int per_x = bc[ORC_SIDE_LEFT] == ORC_BC_PERIODIC, per_z = bc[ORC_SIDE_TOP] == ORC_BC_PERIODIC;
@@ -485,13 +554,17 @@ void orc_adjoint(int nx, int nz, int n, const int *cx, const int *cz,
         for (int z = 0; z < nz; ++z)
             for (int x = 0; x < nx; ++x)
                 for (int d = 0; d < n; ++d) {
-                    int xt = x + cx[d], zt = z + cz[d];
-                    if (per_x) xt = ((xt % nx) + nx) % nx;
-                    if (per_z) zt = ((zt % nz) + nz) % nz;
                     double *dst = mu + (((size_t)z * nx + x) * n + d) * 4;
-                    int inside = xt >= 0 && xt < nx && zt >= 0 && zt < nz;
-                    for (int s = 0; s < 4; ++s)
-                        dst[s] = inside ? lam[(((size_t)zt * nx + xt) * n + d) * 4 + s] : 0.0;
+                    for (int s = 0; s < 4; ++s) dst[s] = 0.0;
+                    for (int k = 0; k < ntap; ++k) {
+                        int j = d * ntap + k;
+                        int xt = x + tx[j], zt = z + tz[j];
+                        if (per_x) xt = ((xt % nx) + nx) % nx;
+                        if (per_z) zt = ((zt % nz) + nz) % nz;
+                        if (xt >= 0 && xt < nx && zt >= 0 && zt < nz)
+                            for (int s = 0; s < 4; ++s)
+                                dst[s] += tw[j] * lam[(((size_t)zt * nx + xt) * n + d) * 4 + s];
+                    }
                 }
         /* lambda = C^T mu, and the parameter gradients of this step */
         for (size_t st = 0; st < nsite; ++st) {

@@ -58,6 +58,8 @@ class Workload:
     abs_mode: int = ABS_BEER_LAMBERT
     steps: int = 1
     seed: int = 0
+    scheme: str = "nearest"          # streaming: "nearest" (D2Q9 offset) | "bilinear" (Eq. 34)
+    plane: str = "xz"                # lattice plane the directions project on: "xz" | "xy"
 
     @property
     def n(self) -> int:

@@ -10,7 +10,8 @@ def oracle_problem(orc, w, offsets=None):
     cls = None if w.phase_index is None else w.phase_index.astype(np.int32)
     return orc.Problem(w.nx, w.nz, mu, phi, w.tau, w.albedo, w.emission, cls, Z,
                        surv_mode=w.surv_mode, abs_mode=w.abs_mode, bc=w.bc,
-                       inflow=w.inflow, offsets=offsets)
+                       inflow=w.inflow, offsets=offsets, scheme=w.scheme,
+                       plane={"xz": orc.PLANE_XZ, "xy": orc.PLANE_XY}[w.plane])
 
 
 def rel_err_I(S, R, floor_frac=1e-6):

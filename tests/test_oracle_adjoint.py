@@ -68,3 +68,40 @@ def test_adjoint_dot_product_identity(orc):
     lhs = np.sum(y * P.radiance_out(P.step(x), orc.SIDE_TOP))   # linear: no inflow, no emission
     rhs = np.sum(x * gS)
     assert lhs == pytest.approx(rhs, rel=1e-13)
+
+
+@pytest.mark.parametrize("plane,bc", [("xz", (2, 0, 0, 0)), ("xy", (1, 1, 2, 0))])
+def test_bilinear_adjoint_matches_central_differences(orc, plane, bc):
+    """Semi-Lagrangian streaming (Eq. 34): the transposed step spreads each
+    entry back over its four taps."""
+    w = W.random_medium(7, 6, 2, 4, seed=77, bc=bc, n_phase=2, steps=5, surv_mode=1)
+    w.tau = np.minimum(w.tau, 0.9)
+    w.scheme, w.plane = "bilinear", plane
+    P = oracle_problem(orc, w)
+    rng = np.random.default_rng(8)
+    S0 = W.random_state(w.nz, w.nx, w.n, seed=9)
+    wt = rng.standard_normal((w.nx, w.n, 4))
+    gt, ga, gZ, gS = P.adjoint(S0, w.steps, wt, want_S0=True)
+
+    def fd(mutate):
+        h = 1e-6
+        vals = []
+        for sgn in (1, -1):
+            Pp = oracle_problem(orc, w)
+            S = S0.copy()
+            mutate(Pp, S, sgn * h)
+            vals.append(_loss(orc, Pp, S, w.steps, wt))
+        return (vals[0] - vals[1]) / (2 * h)
+
+    for z, x in [(0, 0), (w.nz - 1, 3), (2, w.nx - 1), (3, 4)]:
+        def mt(Pp, S, h, z=z, x=x):
+            Pp.tau[z, x] += h
+        assert fd(mt) == pytest.approx(gt[z, x], rel=1e-6, abs=1e-9)
+    for c, r, k in [(0, 0, 0), (1, 5, 9), (0, 13, 2)]:
+        def mz(Pp, S, h, c=c, r=r, k=k):
+            Pp.Z[c, r, k] += h
+        assert fd(mz) == pytest.approx(gZ[c, r, k], rel=1e-6, abs=1e-9)
+    for idx in [(0, 0, 0, 0), (5, 6, 4, 1), (2, 3, 7, 2)]:
+        def ms(Pp, S, h, idx=idx):
+            S[idx] += h
+        assert fd(ms) == pytest.approx(gS[idx], rel=1e-6, abs=1e-9)
