@@ -83,19 +83,42 @@ typedef struct {
     const double *phi; /* host, optional, length n */
 } rtlb_directions;
 
+/* Streaming of each direction after the collision.
+ *  NEAREST8 -- the D2Q9 neighbour offset nearest (by angle) to the direction's
+ *              projection on the lattice plane (Sec. 2.1.6).
+ *  BILINEAR -- semi-Lagrangian bilinear streaming (Eq. 33-38): over one step a
+ *              direction moves l = its projection on the lattice plane (the
+ *              paper's dt = dx / c); per axis n0 = floor(l), f = l - n0, and
+ *              the field arriving at x is the sum over b_x, b_z in {0, 1} of
+ *              w_x(b_x) w_z(b_z) P(x - (n0x + b_x), z - (n0z + b_z)), with
+ *              w(0) = 1 - f, w(1) = f.  Components within 1e-12 of an integer
+ *              are taken as that integer.  Sources outside the lattice take the
+ *              side's ghost value exactly as in NEAREST8.
+ * Lattice plane: XZ -- x horizontal, z vertical (the Stokes reference axis),
+ * projection (sin(theta) cos(phi), mu); XY -- a horizontal lattice as in the
+ * paper's 2D runs (Sec. 3.2), projection (sin(theta) cos(phi),
+ * sin(theta) sin(phi)).  Either way the second lattice axis is called z here
+ * and "top" is its last row. */
+typedef enum { RTLB_STREAM_NEAREST8 = 0, RTLB_STREAM_BILINEAR = 1 } rtlb_streaming;
+typedef enum { RTLB_PLANE_XZ = 0, RTLB_PLANE_XY = 1 } rtlb_plane;
+
+/* All-zero options are the defaults: FP32, LINEAR, BEER_LAMBERT, NEAREST8, XZ. */
 typedef struct {
     int32_t precision;  /* rtlb_precision  */
     int32_t survival;   /* rtlb_survival   */
     int32_t absorption; /* rtlb_absorption */
+    int32_t streaming;  /* rtlb_streaming  */
+    int32_t plane;      /* rtlb_plane      */
 } rtlb_options;
 
-/* Create a context on the current CUDA device.  Computes each direction's
- * D2Q9 streaming offset: the neighbour offset nearest (by angle) to the (x, z)
- * projection (sin(theta) cos(phi), mu); a zero projection rests.  Returns
- * RTLB_E_AMBIGUOUS_STREAM when a projection lies within 1e-9 (in units of 45
- * degrees) of the midpoint between two offsets.  1 <= nx, nz <= 65535;
- * 1 <= n <= 256.  opts may be NULL (FP32, LINEAR, BEER_LAMBERT).  Allocates
- * two state buffers of nx*nz*n*16 bytes (the state starts at zero). */
+/* Create a context on the current CUDA device.  With NEAREST8 streaming,
+ * computes each direction's D2Q9 offset: the neighbour offset nearest (by
+ * angle) to its projection on the lattice plane; a zero projection rests.
+ * Returns RTLB_E_AMBIGUOUS_STREAM when a projection lies within 1e-9 (in
+ * units of 45 degrees) of the midpoint between two offsets (BILINEAR has no
+ * such case).  1 <= nx, nz <= 65535; 1 <= n <= 256.  opts may be NULL (all
+ * defaults).  Allocates two state buffers of nx*nz*n*16 bytes (the state
+ * starts at zero); BILINEAR adds a third on the first step. */
 rtlb_status rtlb_create(const rtlb_grid *grid, const rtlb_directions *dirs,
                         const rtlb_options *opts, rtlb_ctx **out);
 
@@ -144,8 +167,9 @@ rtlb_status rtlb_last_residual(rtlb_ctx *ctx, double *residual, void *stream);
 
 /* Radiance leaving through one side: out[len][n][4] float32 (host or device),
  * len = nx for top/bottom and nz for left/right: the state on the boundary row
- * or column for the directions whose offset points out of the domain through
- * that side, zero for the others. */
+ * or column for the directions that move out of the domain through that side
+ * (NEAREST8: the offset points out; BILINEAR: the displacement component
+ * across that side is nonzero and points out), zero for the others. */
 rtlb_status rtlb_radiance_out(rtlb_ctx *ctx, int32_t side, float *out, void *stream);
 
 /* Reverse-mode gradients (adjoint of Eq. 2's step: transposed phase-matrix
@@ -159,9 +183,11 @@ rtlb_status rtlb_radiance_out(rtlb_ctx *ctx, int32_t side, float *out, void *str
  * float32 (host or device) -- dL/dtau and dL/dalbedo per cell; grad_Z host
  * float64 [n_phase][4n][4n] -- dL/dZ per class table entry (contract with
  * rtlb_phase_hg's dZdg for dL/dg); grad_S0 [nz][nx][n][4] float32 (host or
- * device) -- dL/dS^0.  Device memory: (ceil(nsteps/checkpoint_every) +
- * checkpoint_every + 3) states plus the table-gradient accumulators.  n must be
- * in {8, 16, 32, 64}.  Synchronizes. */
+ * device) -- dL/dS^0.  With BILINEAR streaming the reversed streaming
+ * gathers each entry from its four streaming targets with the same weights.
+ * Device memory: (ceil(nsteps/checkpoint_every) + checkpoint_every + 3)
+ * states (one more for BILINEAR) plus the table-gradient accumulators.  n must
+ * be in {8, 16, 32, 64}.  Synchronizes. */
 rtlb_status rtlb_adjoint(rtlb_ctx *ctx, int32_t nsteps, int32_t checkpoint_every, const float *dL_dout,
                          float *grad_tau, float *grad_albedo, double *grad_Z, float *grad_S0,
                          void *stream);
@@ -183,8 +209,9 @@ void rtlb_destroy(rtlb_ctx *ctx);
  * launch per step: the single-class 128-site tiles of all channels form one
  * work list, each item fetching its channel's pointers, TMA maps and tables
  * from a descriptor.  All channels must use the same tensor-core precision
- * (BF16 or BF16X2), n in {8, 16, 32} (n = 8, 16, 32 may be mixed), have a
- * medium set, live on the same device and stand at the same step parity.
+ * (BF16 or BF16X2), n in {8, 16, 32} (n = 8, 16, 32 may be mixed), NEAREST8
+ * streaming (RTLB_E_UNSUPPORTED otherwise), have a medium set, live on the
+ * same device and stand at the same step parity.
  * Tiles mixing phase classes run on the CUDA-core kernel in the same step.
  * Channels keep working as ordinary contexts (get_state, radiance_out, ...);
  * stepping one alone desynchronizes the batch (rtlb_batch_step then returns
@@ -235,8 +262,17 @@ rtlb_status rtlb_residual_noalloc(const float *S_old, const float *S_new, size_t
 
 /* ---- host helpers (float64, no GPU needed) ---- */
 
-/* Per-direction D2Q9 offsets cx[n], cz[n] (host int32) of the grid. */
+/* Per-direction D2Q9 offsets cx[n], cz[n] (host int32) of the grid on the
+ * (x, z) plane (NEAREST8). */
 rtlb_status rtlb_stream_offsets(const rtlb_directions *dirs, int32_t *cx, int32_t *cz);
+
+/* Streaming taps of every direction for a scheme and plane (rtlb_streaming,
+ * rtlb_plane): tap k of direction d moves content by (ox, oz)[4d + k] cells
+ * with weight w[4d + k] (host int32 / float64, [n][4]).  BILINEAR lists
+ * (b_x, b_z) = (0,0), (1,0), (0,1), (1,1); NEAREST8 puts the offset in tap 0
+ * with weight 1 and zero weight on taps 1-3.  Errors as rtlb_create. */
+rtlb_status rtlb_stream_taps(const rtlb_directions *dirs, int32_t streaming, int32_t plane, int32_t *ox,
+                             int32_t *oz, double *w);
 
 /* Normalized Rayleigh table (Eq. 13-17 with Eq. 16 and the rotation of Eq. 21):
  * Z_out[4n][4n] host float64.  Block (o, i) = R(-psi_o) P~(theta) R(psi_i)

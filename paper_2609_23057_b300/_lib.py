@@ -29,7 +29,7 @@ EXPORTS = [
     "rtlb_stream_offsets", "rtlb_phase_rayleigh", "rtlb_phase_hg", "rtlb_phase_mix",
     "rtlb_residual_noalloc", "rtlb_adjoint", "rtlb_phase_conserve_intensity",
     "rtlb_batch_create", "rtlb_batch_configure", "rtlb_batch_step", "rtlb_batch_check",
-    "rtlb_batch_last_error", "rtlb_batch_destroy",
+    "rtlb_batch_last_error", "rtlb_batch_destroy", "rtlb_stream_taps",
 ]
 
 
@@ -43,7 +43,8 @@ class Directions(C.Structure):
 
 
 class Options(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("survival", C.c_int32), ("absorption", C.c_int32)]
+    _fields_ = [("precision", C.c_int32), ("survival", C.c_int32), ("absorption", C.c_int32),
+                ("streaming", C.c_int32), ("plane", C.c_int32)]
 
 
 class RtlbError(RuntimeError):
@@ -81,6 +82,7 @@ def lib() -> C.CDLL:
     L.rtlb_destroy.argtypes = [vp]
     L.rtlb_destroy.restype = None
     L.rtlb_stream_offsets.argtypes = [C.POINTER(Directions), vp, vp]
+    L.rtlb_stream_taps.argtypes = [C.POINTER(Directions), i32, i32, vp, vp, vp]
     L.rtlb_phase_rayleigh.argtypes = [C.POINTER(Directions), C.c_double, vp]
     L.rtlb_phase_conserve_intensity.argtypes = [i32, vp]
     L.rtlb_phase_hg.argtypes = [C.POINTER(Directions), C.c_double, C.c_double, vp, vp]

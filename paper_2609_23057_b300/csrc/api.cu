@@ -12,6 +12,7 @@
 #include <new>
 
 #include "rtlb_internal.h"
+#include "step_common.cuh"
 #include "tc.h"
 
 using namespace rtlb;
@@ -55,10 +56,18 @@ bool is_device_ptr(const void *p)
 
 inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
-rtlb_status build_dirs(const rtlb_directions *dirs, std::vector<double> &mu, std::vector<double> &phi,
-                       std::vector<int> &cx, std::vector<int> &cz, rtlb_ctx *ctx)
+// Direction set, and per direction its streaming description: for NEAREST8
+// the D2Q9 offset (cx, cz) and a single unit tap; for BILINEAR the four taps of
+// Eq. 34 and, in (cx, cz), the sign of each displacement component (the sense
+// of motion, used by the boundary readout and the adjoint seed).
+rtlb_status build_dirs(const rtlb_directions *dirs, int streaming, int plane, std::vector<double> &mu,
+                       std::vector<double> &phi, std::vector<int> &cx, std::vector<int> &cz,
+                       std::vector<int> &tap_o, std::vector<double> &tap_w, rtlb_ctx *ctx)
 {
     if (!dirs) return fail(ctx, RTLB_E_ARG, "directions is NULL");
+    if (streaming != RTLB_STREAM_NEAREST8 && streaming != RTLB_STREAM_BILINEAR)
+        return fail(ctx, RTLB_E_ARG, "unknown streaming scheme %d", streaming);
+    if (plane != RTLB_PLANE_XZ && plane != RTLB_PLANE_XY) return fail(ctx, RTLB_E_ARG, "unknown lattice plane %d", plane);
     if (dirs->n_zen < 1 || dirs->n_az < 1 || (int64_t)dirs->n_zen * dirs->n_az > kMaxDirs)
         return fail(ctx, RTLB_E_SHAPE, "need 1 <= n_zen*n_az <= %d (got %d x %d)", kMaxDirs, dirs->n_zen,
                     dirs->n_az);
@@ -76,18 +85,38 @@ rtlb_status build_dirs(const rtlb_directions *dirs, std::vector<double> &mu, std
     }
     cx.assign(n, 0);
     cz.assign(n, 0);
-    for (int d = 0; d < n; ++d)
-        if (stream_offset(mu[d], phi[d], &cx[d], &cz[d]))
-            return fail(ctx, RTLB_E_AMBIGUOUS_STREAM,
-                        "direction %d (mu=%.17g, phi=%.17g) lies between two lattice offsets", d, mu[d], phi[d]);
+    tap_o.assign((size_t)8 * n, 0);
+    tap_w.assign((size_t)4 * n, 0.0);
+    for (int d = 0; d < n; ++d) {
+        if (streaming == RTLB_STREAM_NEAREST8) {
+            if (stream_offset(mu[d], phi[d], plane, &cx[d], &cz[d]))
+                return fail(ctx, RTLB_E_AMBIGUOUS_STREAM,
+                            "direction %d (mu=%.17g, phi=%.17g) lies between two lattice offsets", d, mu[d],
+                            phi[d]);
+            tap_o[8 * d] = cx[d];
+            tap_o[8 * d + 4] = cz[d];
+            tap_w[4 * d] = 1.0;
+        } else {
+            int sense[2];
+            bilinear_taps(mu[d], phi[d], plane, &tap_o[8 * d], &tap_o[8 * d + 4], &tap_w[4 * d], sense);
+            cx[d] = sense[0];
+            cz[d] = sense[1];
+        }
+    }
     return RTLB_OK;
 }
+
+bool bilinear(const rtlb_ctx *c) { return c->opt.streaming == RTLB_STREAM_BILINEAR; }
 
 void free_ctx_buffers(rtlb_ctx *c)
 {
     cudaFree(c->S[0]);
     cudaFree(c->S[1]);
     cudaFree(c->d_dir);
+    cudaFree(c->d_dir0);
+    cudaFree(c->d_tap_o);
+    cudaFree(c->d_tap_w);
+    cudaFree(c->d_post);
     cudaFree(c->d_inflow);
     cudaFree(c->d_coef);
     cudaFree(c->d_cls);
@@ -119,6 +148,12 @@ rtlb_status ensure_stage(rtlb_ctx *c)
     return RTLB_OK;
 }
 
+rtlb_status ensure_post(rtlb_ctx *c)
+{
+    if (!c->d_post) CK(c, cudaMalloc(&c->d_post, c->state_floats() * sizeof(float)), "post-collision buffer");
+    return RTLB_OK;
+}
+
 StepParams make_params(rtlb_ctx *c)
 {
     StepParams p;
@@ -137,6 +172,22 @@ StepParams make_params(rtlb_ctx *c)
     return p;
 }
 
+// One float32 CUDA-core step from S_in to S_out with the context's streaming
+// scheme (the adjoint's forward and replay).
+cudaError_t fp32_step_into(rtlb_ctx *c, const float *S_in, float *S_out, cudaStream_t s)
+{
+    StepParams p = make_params(c);
+    p.S = S_in;
+    p.S_new = S_out;
+    if (!bilinear(c)) return launch_step_fp32(p, s);
+    p.dir = c->d_dir0;
+    p.S_new = c->d_post;
+    cudaError_t e = launch_step_fp32(p, s);
+    if (e != cudaSuccess) return e;
+    return launch_stream_bilinear(c->d_post, S_out, c->d_tap_o, c->d_tap_w, c->d_inflow, c->nx, c->nz, c->n,
+                                  pack_bc(c->bc), s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -148,13 +199,14 @@ rtlb_status rtlb_create(const rtlb_grid *grid, const rtlb_directions *dirs, cons
     *out = nullptr;
     if (!grid || !dirs) return RTLB_E_ARG;
     if (grid->nx < 1 || grid->nz < 1 || grid->nx > 65535 || grid->nz > 65535) return RTLB_E_SHAPE;
-    rtlb_options o = opts ? *opts : rtlb_options{RTLB_PREC_FP32, RTLB_SURV_LINEAR, RTLB_ABS_BEER_LAMBERT};
+    rtlb_options o{};
+    if (opts) o = *opts;
     if (o.precision < RTLB_PREC_FP32 || o.precision > RTLB_PREC_BF16X2 || o.survival < 0 || o.survival > 1 ||
         o.absorption < 0 || o.absorption > 1)
         return RTLB_E_ARG;
-    std::vector<double> mu, phi;
-    std::vector<int> cx, cz;
-    rtlb_status st = build_dirs(dirs, mu, phi, cx, cz, nullptr);
+    std::vector<double> mu, phi, tap_w;
+    std::vector<int> cx, cz, tap_o;
+    rtlb_status st = build_dirs(dirs, o.streaming, o.plane, mu, phi, cx, cz, tap_o, tap_w, nullptr);
     if (st != RTLB_OK) return st;
     if (o.precision != RTLB_PREC_FP32 && !tc_shape_ok(dirs->n_zen * dirs->n_az, o.precision))
         return RTLB_E_UNSUPPORTED;
@@ -171,6 +223,8 @@ rtlb_status rtlb_create(const rtlb_grid *grid, const rtlb_directions *dirs, cons
     c->phi = phi;
     c->cx = cx;
     c->cz = cz;
+    c->tap_o = tap_o;
+    c->tap_w.assign(tap_w.begin(), tap_w.end());
     c->opt = o;
     c->inflow.assign((size_t)4 * c->n * 4, 0.0f);
     const size_t bytes = c->state_floats() * sizeof(float);
@@ -185,6 +239,9 @@ rtlb_status rtlb_create(const rtlb_grid *grid, const rtlb_directions *dirs, cons
     if (e == cudaSuccess) e = cudaMalloc(&c->S[0], bytes);
     if (e == cudaSuccess) e = cudaMalloc(&c->S[1], bytes);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_dir, dirbuf.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_dir0, dirbuf.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_tap_o, c->tap_o.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_tap_w, c->tap_w.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_inflow, c->inflow.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_scratch, (size_t)3 * nblk * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_out, 8 * sizeof(double));
@@ -194,6 +251,11 @@ rtlb_status rtlb_create(const rtlb_grid *grid, const rtlb_directions *dirs, cons
     if (e == cudaSuccess) e = cudaMemset(c->S[0], 0, bytes);
     if (e == cudaSuccess) e = cudaMemset(c->S[1], 0, bytes);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_dir, dirbuf.data(), dirbuf.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(c->d_dir0, 0, dirbuf.size() * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_tap_o, c->tap_o.data(), c->tap_o.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_tap_w, c->tap_w.data(), c->tap_w.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(c->d_inflow, c->inflow.data(), c->inflow.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -396,8 +458,18 @@ rtlb_status rtlb_step(rtlb_ctx *c, int32_t nsteps, void *stream)
     rtlb_status st = require_boundary_pairs(c);
     if (st != RTLB_OK) return st;
     cudaStream_t s = S(stream);
+    if (bilinear(c)) {
+        st = ensure_post(c);
+        if (st != RTLB_OK) return st;
+    }
     for (int t = 0; t < nsteps; ++t) {
         StepParams p = make_params(c);
+        if (bilinear(c)) {
+            // collision in place (zero offsets) into the post-collision buffer,
+            // then the four-tap streaming into the next state
+            p.dir = c->d_dir0;
+            p.S_new = c->d_post;
+        }
         cudaError_t e;
         if (c->opt.precision == RTLB_PREC_FP32) {
             e = launch_step_fp32(p, s);
@@ -406,6 +478,9 @@ rtlb_status rtlb_step(rtlb_ctx *c, int32_t nsteps, void *stream)
             if (st != RTLB_OK) return st;
             e = cudaSuccess;
         }
+        if (e == cudaSuccess && bilinear(c))
+            e = launch_stream_bilinear(c->d_post, c->S[c->cur ^ 1], c->d_tap_o, c->d_tap_w, c->d_inflow, c->nx, c->nz,
+                                       c->n, pack_bc(c->bc), s);
         if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
         c->cur ^= 1;
         c->has_prev = true;
@@ -479,9 +554,10 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
     float *ck = nullptr, *seg = nullptr, *lam = nullptr, *bm = nullptr, *dl = nullptr, *gtd = nullptr, *gad = nullptr;
     float *gS = nullptr;
     double *ga = nullptr, *gb = nullptr, *slots = nullptr, *G = nullptr;
+    int *tapT = nullptr;
     auto release = [&]() {
         cudaFree(ck); cudaFree(seg); cudaFree(lam); cudaFree(bm); cudaFree(dl); cudaFree(gtd); cudaFree(gad);
-        cudaFree(gS); cudaFree(ga); cudaFree(gb); cudaFree(slots); cudaFree(G);
+        cudaFree(gS); cudaFree(ga); cudaFree(gb); cudaFree(slots); cudaFree(G); cudaFree(tapT);
     };
 #define AK(call, what)                                \
     do {                                              \
@@ -499,6 +575,19 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
     AK(cudaMalloc(&gb, ns * sizeof(double)), "adjoint g_beta");
     AK(cudaMalloc(&slots, (size_t)nslots * glen * sizeof(double)), "adjoint table slots");
     AK(cudaMalloc(&G, glen * sizeof(double)), "adjoint table gradient");
+    int bcT[4];
+    for (int k = 0; k < 4; ++k) bcT[k] = c->bc[k] == RTLB_BC_PERIODIC ? RTLB_BC_PERIODIC : RTLB_BC_VACUUM;
+    if (bilinear(c)) {
+        st = ensure_post(c);
+        if (st != RTLB_OK) {
+            release();
+            return st;
+        }
+        std::vector<int> neg(c->tap_o.size());
+        for (size_t k = 0; k < neg.size(); ++k) neg[k] = -c->tap_o[k];
+        AK(cudaMalloc(&tapT, neg.size() * sizeof(int)), "adjoint taps");
+        AK(cudaMemcpy(tapT, neg.data(), neg.size() * sizeof(int), cudaMemcpyHostToDevice), "adjoint taps");
+    }
     const float *dl_dev = dL_dout;
     const size_t dl_bytes = (size_t)c->nx * c->n * 4 * sizeof(float);
     if (!is_device_ptr(dL_dout)) {
@@ -511,7 +600,7 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
         AK(cudaMemcpyAsync(ck + (size_t)g * L, c->S[c->cur], bytes, cudaMemcpyDeviceToDevice, s), "checkpoint");
         const int len = std::min(K, nsteps - g * K);
         for (int j = 0; j < len; ++j) {
-            AK(launch_step_fp32(make_params(c), s), "adjoint forward");
+            AK(fp32_step_into(c, c->S[c->cur], c->S[c->cur ^ 1], s), "adjoint forward");
             c->cur ^= 1;
         }
     }
@@ -527,22 +616,27 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
     for (int g = nseg - 1; g >= 0; --g) {
         const int len = std::min(K, nsteps - g * K);
         AK(cudaMemcpyAsync(seg, ck + (size_t)g * L, bytes, cudaMemcpyDeviceToDevice, s), "segment start");
-        for (int j = 0; j + 1 < len; ++j) {
-            StepParams p = make_params(c);
-            p.S = seg + (size_t)j * L;
-            p.S_new = seg + (size_t)(j + 1) * L;
-            AK(launch_step_fp32(p, s), "adjoint recompute");
-        }
+        for (int j = 0; j + 1 < len; ++j)
+            AK(fp32_step_into(c, seg + (size_t)j * L, seg + (size_t)(j + 1) * L, s), "adjoint recompute");
         for (int j = len - 1; j >= 0; --j) {
             AdjointParams ap;
             ap.lam_next = lam + (size_t)lc * L;
+            if (bilinear(c)) {
+                // transposed streaming first: each entry gathers from its four
+                // streaming targets (negated taps); content that left through a
+                // non-periodic side contributes nothing
+                AK(launch_stream_bilinear(lam + (size_t)lc * L, c->d_post, tapT, c->d_tap_w, c->d_inflow, c->nx,
+                                          c->nz, c->n, pack_bc(bcT), s),
+                   "adjoint transposed streaming");
+                ap.lam_next = c->d_post;
+            }
             ap.lam_out = lam + (size_t)(lc ^ 1) * L;
             ap.beta_mu = bm;
             ap.S = seg + (size_t)j * L;
             ap.coef = c->d_coef;
             ap.cls = c->d_cls;
             ap.Z = c->d_Z;
-            ap.dir = c->d_dir;
+            ap.dir = bilinear(c) ? c->d_dir0 : c->d_dir;
             ap.nx = c->nx;
             ap.nz = c->nz;
             ap.n = c->n;
@@ -622,9 +716,9 @@ rtlb_status rtlb_total_intensity(rtlb_ctx *c, double *total, void *stream)
 rtlb_status rtlb_stream_offsets(const rtlb_directions *dirs, int32_t *cx, int32_t *cz)
 {
     if (!cx || !cz) return RTLB_E_ARG;
-    std::vector<double> mu, phi;
-    std::vector<int> x, z;
-    rtlb_status st = build_dirs(dirs, mu, phi, x, z, nullptr);
+    std::vector<double> mu, phi, tw;
+    std::vector<int> x, z, to;
+    rtlb_status st = build_dirs(dirs, RTLB_STREAM_NEAREST8, RTLB_PLANE_XZ, mu, phi, x, z, to, tw, nullptr);
     if (st != RTLB_OK) return st;
     for (size_t d = 0; d < x.size(); ++d) {
         cx[d] = x[d];
@@ -633,14 +727,31 @@ rtlb_status rtlb_stream_offsets(const rtlb_directions *dirs, int32_t *cx, int32_
     return RTLB_OK;
 }
 
+rtlb_status rtlb_stream_taps(const rtlb_directions *dirs, int32_t streaming, int32_t plane, int32_t *ox, int32_t *oz,
+                             double *w)
+{
+    if (!ox || !oz || !w) return RTLB_E_ARG;
+    std::vector<double> mu, phi, tw;
+    std::vector<int> x, z, to;
+    rtlb_status st = build_dirs(dirs, streaming, plane, mu, phi, x, z, to, tw, nullptr);
+    if (st != RTLB_OK) return st;
+    for (size_t d = 0; d < x.size(); ++d)
+        for (int k = 0; k < 4; ++k) {
+            ox[4 * d + k] = to[8 * d + k];
+            oz[4 * d + k] = to[8 * d + 4 + k];
+            w[4 * d + k] = tw[4 * d + k];
+        }
+    return RTLB_OK;
+}
+
 rtlb_status rtlb_phase_rayleigh(const rtlb_directions *dirs, double depol, double *Z_out)
 {
     if (!Z_out) return RTLB_E_ARG;
     if (!(depol >= 0.0 && depol < 0.5)) return RTLB_E_RANGE;
-    std::vector<double> mu, phi;
-    std::vector<int> x, z;
-    rtlb_status st = build_dirs(dirs, mu, phi, x, z, nullptr);
-    if (st != RTLB_OK && st != RTLB_E_AMBIGUOUS_STREAM) return st;
+    std::vector<double> mu, phi, tw;
+    std::vector<int> x, z, to;
+    rtlb_status st = build_dirs(dirs, RTLB_STREAM_BILINEAR, RTLB_PLANE_XZ, mu, phi, x, z, to, tw, nullptr);
+    if (st != RTLB_OK) return st;
     phase_rayleigh(mu, phi, depol, Z_out);
     return RTLB_OK;
 }
@@ -657,10 +768,10 @@ rtlb_status rtlb_phase_hg(const rtlb_directions *dirs, double g, double pol_amp,
 {
     if (!Z_out) return RTLB_E_ARG;
     if (!(g > -1.0 && g < 1.0) || !(std::fabs(pol_amp) <= 1.0)) return RTLB_E_RANGE;
-    std::vector<double> mu, phi;
-    std::vector<int> x, z;
-    rtlb_status st = build_dirs(dirs, mu, phi, x, z, nullptr);
-    if (st != RTLB_OK && st != RTLB_E_AMBIGUOUS_STREAM) return st;
+    std::vector<double> mu, phi, tw;
+    std::vector<int> x, z, to;
+    rtlb_status st = build_dirs(dirs, RTLB_STREAM_BILINEAR, RTLB_PLANE_XZ, mu, phi, x, z, to, tw, nullptr);
+    if (st != RTLB_OK) return st;
     phase_hg(mu, phi, g, pol_amp, Z_out, dZdg_out);
     return RTLB_OK;
 }
@@ -669,10 +780,10 @@ rtlb_status rtlb_phase_mix(const rtlb_directions *dirs, double m, double g, doub
 {
     if (!Z_out) return RTLB_E_ARG;
     if (!(m >= 0.0 && m <= 1.0) || !(g > -1.0 && g < 1.0) || !(std::fabs(pol_amp) <= 1.0)) return RTLB_E_RANGE;
-    std::vector<double> mu, phi;
-    std::vector<int> x, z;
-    rtlb_status st = build_dirs(dirs, mu, phi, x, z, nullptr);
-    if (st != RTLB_OK && st != RTLB_E_AMBIGUOUS_STREAM) return st;
+    std::vector<double> mu, phi, tw;
+    std::vector<int> x, z, to;
+    rtlb_status st = build_dirs(dirs, RTLB_STREAM_BILINEAR, RTLB_PLANE_XZ, mu, phi, x, z, to, tw, nullptr);
+    if (st != RTLB_OK) return st;
     const size_t len = 16 * mu.size() * mu.size();
     std::vector<double> zr(len), zh(len);
     phase_rayleigh(mu, phi, 0.0, zr.data());

@@ -379,7 +379,7 @@ rtlb_status rtlb_batch_create(int32_t count, rtlb_ctx *const *channels, rtlb_bat
     for (int k = 0; k < count; ++k) {
         rtlb_ctx *c = channels[k];
         if (!c || c->opt.precision != prec || !c->medium_set || c->n > 32 || c->n % 8 != 0 || c->cur != channels[0]->cur ||
-            c->dev != channels[0]->dev) {
+            c->dev != channels[0]->dev || c->opt.streaming != RTLB_STREAM_NEAREST8) {
             delete b;
             return c && !c->medium_set ? RTLB_E_STATE : RTLB_E_UNSUPPORTED;
         }

@@ -33,13 +33,20 @@ void direction_grid(int n_zen, int n_az, std::vector<double> &mu, std::vector<do
     }
 }
 
+void lattice_projection(double mu, double phi, int plane, double *px, double *pz)
+{
+    const double st = std::sqrt(std::fmax(0.0, 1.0 - mu * mu));
+    *px = st * std::cos(phi);
+    *pz = plane == RTLB_PLANE_XY ? st * std::sin(phi) : mu;
+}
+
 // Nearest D2Q9 offset by angle, found by folding the projection into the first
 // octant: the smaller-over-larger component angle delta in [0, 45] deg picks an
 // axis offset (delta < 22.5) or a diagonal one (delta > 22.5).
-int stream_offset(double mu, double phi, int *cx, int *cz)
+int stream_offset(double mu, double phi, int plane, int *cx, int *cz)
 {
-    const double px = std::sqrt(std::fmax(0.0, 1.0 - mu * mu)) * std::cos(phi);
-    const double pz = mu;
+    double px, pz;
+    lattice_projection(mu, phi, plane, &px, &pz);
     const double ax = std::fabs(px), az = std::fabs(pz);
     if (std::sqrt(ax * ax + az * az) < 1e-12) {
         *cx = 0;
@@ -62,6 +69,30 @@ int stream_offset(double mu, double phi, int *cx, int *cz)
         *cz = sz;
     }
     return 0;
+}
+
+// Semi-Lagrangian taps: per axis the displacement l (snapped to an integer
+// when within 1e-12 of one) splits into n0 = floor(l) and f = l - n0; the two
+// axis stencils {n0: 1 - f, n0 + 1: f} multiply into four taps, b_x fastest.
+void bilinear_taps(double mu, double phi, int plane, int ox[4], int oz[4], double w[4], int sense[2])
+{
+    double l[2];
+    lattice_projection(mu, phi, plane, &l[0], &l[1]);
+    int n0[2];
+    double f[2];
+    for (int a = 0; a < 2; ++a) {
+        const double r = std::nearbyint(l[a]);
+        if (std::fabs(l[a] - r) < 1e-12) l[a] = r;
+        n0[a] = (int)std::floor(l[a]);
+        f[a] = l[a] - n0[a];
+        sense[a] = l[a] > 0.0 ? 1 : (l[a] < 0.0 ? -1 : 0);
+    }
+    for (int k = 0; k < 4; ++k) {
+        const int bx = k & 1, bz = k >> 1;
+        ox[k] = n0[0] + bx;
+        oz[k] = n0[1] + bz;
+        w[k] = (bx ? f[0] : 1.0 - f[0]) * (bz ? f[1] : 1.0 - f[1]);
+    }
 }
 
 namespace {

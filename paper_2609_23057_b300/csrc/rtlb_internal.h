@@ -13,7 +13,9 @@ namespace rtlb {
 
 // ---- host geometry / tables (phase.cpp) ----
 void direction_grid(int n_zen, int n_az, std::vector<double> &mu, std::vector<double> &phi);
-int stream_offset(double mu, double phi, int *cx, int *cz);  // 1 = tie
+void lattice_projection(double mu, double phi, int plane, double *px, double *pz);
+int stream_offset(double mu, double phi, int plane, int *cx, int *cz);  // 1 = tie
+void bilinear_taps(double mu, double phi, int plane, int ox[4], int oz[4], double w[4], int sense[2]);
 void phase_rayleigh(const std::vector<double> &mu, const std::vector<double> &phi, double rho, double *Z);
 void conserve_intensity(int n, double *Z);
 void phase_hg(const std::vector<double> &mu, const std::vector<double> &phi, double g,
@@ -76,6 +78,10 @@ cudaError_t launch_total_I(const float *dm, size_t nvec, double *partials, int n
 cudaError_t launch_radiance_out(const float *dm, float *out, int nx, int nz, int n,
                                 const int *dir, int side, cudaStream_t s);
 cudaError_t launch_fill(float *p, size_t count, float v, cudaStream_t s);
+// bilinear streaming (k_stream.cu): S(x, d) = sum_k w[d][k] P(x - o[d][k], d) with
+// the ghost rule of the boundary kinds; taps_o = [n][8] (ox0..3, oz0..3), taps_w = [n][4]
+cudaError_t launch_stream_bilinear(const float *P, float *S, const int *taps_o, const float *taps_w,
+                                   const float *inflow, int nx, int nz, int n, int bcbits, cudaStream_t s);
 
 }  // namespace rtlb
 
@@ -83,7 +89,9 @@ struct rtlb_ctx {
     int dev = 0;
     int nx = 0, nz = 0, n = 0, n_zen = 0, n_az = 0;
     std::vector<double> mu, phi;
-    std::vector<int> cx, cz;
+    std::vector<int> cx, cz;      // NEAREST8: offsets; BILINEAR: sense of motion (sign of l)
+    std::vector<int> tap_o;       // [n][8] ox0..3, oz0..3 (BILINEAR)
+    std::vector<float> tap_w;     // [n][4]
     rtlb_options opt{};
     int bc[4] = {0, 0, 0, 0};
     std::vector<float> inflow;  // [4][n][4]
@@ -91,7 +99,11 @@ struct rtlb_ctx {
     // device buffers
     float *S[2] = {nullptr, nullptr};  // direction-major [n][nsites][4]
     int cur = 0;
-    int *d_dir = nullptr;
+    int *d_dir = nullptr;         // [2n] cx then cz (see cx, cz above)
+    int *d_dir0 = nullptr;        // [2n] zeros: the collision pass of BILINEAR streaming
+    int *d_tap_o = nullptr;
+    float *d_tap_w = nullptr;
+    float *d_post = nullptr;      // BILINEAR: post-collision field before streaming
     float *d_inflow = nullptr;
     float4 *d_coef = nullptr;
     uint8_t *d_cls = nullptr;

@@ -16,6 +16,8 @@ SURVIVAL = {"linear": 0, "exp": 1}
 ABSORPTION = {"beer_lambert": 0, "taylor": 1}
 SIDES = {"top": 0, "bottom": 1, "left": 2, "right": 3}
 BCS = {"vacuum": 0, "periodic": 1, "inflow": 2}
+STREAMING = {"nearest": 0, "bilinear": 1}
+PLANES = {"xz": 0, "xy": 1}
 
 
 def _dirs(n_zen: int, n_az: int, mu=None, phi=None):
@@ -37,6 +39,16 @@ def stream_offsets(n_zen: int, n_az: int, mu=None, phi=None):
     cx, cz = np.zeros(n, np.int32), np.zeros(n, np.int32)
     check(lib().rtlb_stream_offsets(C.byref(d), cx.ctypes.data, cz.ctypes.data))
     return cx, cz
+
+
+def stream_taps(n_zen: int, n_az: int, streaming: str = "bilinear", plane: str = "xz", mu=None, phi=None):
+    """(ox, oz, w) [n][4] of the library's streaming taps (rtlb_stream_taps)."""
+    n = n_zen * n_az
+    d, keep = _dirs(n_zen, n_az, mu, phi)
+    ox, oz, w = np.zeros((n, 4), np.int32), np.zeros((n, 4), np.int32), np.zeros((n, 4))
+    check(lib().rtlb_stream_taps(C.byref(d), STREAMING[streaming], PLANES[plane], ox.ctypes.data, oz.ctypes.data,
+                                 w.ctypes.data))
+    return ox, oz, w
 
 
 def phase_rayleigh(n_zen: int, n_az: int, mu=None, phi=None, depol: float = 0.0) -> np.ndarray:
@@ -107,15 +119,18 @@ class Solver:
     """One lattice, one medium, one state, on the current CUDA device."""
 
     def __init__(self, nx: int, nz: int, n_zen: int, n_az: int, precision: str = "fp32",
-                 survival: str = "linear", absorption: str = "beer_lambert", mu=None, phi=None):
+                 survival: str = "linear", absorption: str = "beer_lambert", mu=None, phi=None,
+                 streaming: str = "nearest", plane: str = "xz"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("librtlb needs a CUDA device")
         self.nx, self.nz, self.n_zen, self.n_az = nx, nz, n_zen, n_az
         self.n = n_zen * n_az
         self.precision = precision
+        self.streaming, self.plane = streaming, plane
         d, self._keep = _dirs(n_zen, n_az, mu, phi)
-        opts = Options(PRECISIONS[precision], SURVIVAL[survival], ABSORPTION[absorption])
+        opts = Options(PRECISIONS[precision], SURVIVAL[survival], ABSORPTION[absorption], STREAMING[streaming],
+                       PLANES[plane])
         ctx = C.c_void_p()
         check(lib().rtlb_create(C.byref(Grid(nx, nz)), C.byref(d), C.byref(opts), C.byref(ctx)))
         self._ctx = ctx
@@ -234,7 +249,8 @@ def solver_for(w, precision: str = "fp32") -> Solver:
     """Solver set up for a workloads.Workload (medium, tables, boundaries)."""
     surv = "exp" if w.surv_mode == 1 else "linear"
     absm = "taylor" if w.abs_mode == 1 else "beer_lambert"
-    s = Solver(w.nx, w.nz, w.n_zen, w.n_az, precision=precision, survival=surv, absorption=absm)
+    s = Solver(w.nx, w.nz, w.n_zen, w.n_az, precision=precision, survival=surv, absorption=absm,
+               streaming=getattr(w, "scheme", "nearest"), plane=getattr(w, "plane", "xz"))
     tabs = np.stack([phase_table_spec(w.n_zen, w.n_az, sp) for sp in w.phase_specs])
     s.set_medium(w.tau.astype(np.float32), w.albedo.astype(np.float32), tabs,
                  emission=None if w.emission is None else w.emission.astype(np.float32),

@@ -98,3 +98,48 @@ def test_conserve_intensity_matches_oracle(orc):
         Zl = S.conserve_intensity(S.phase_table_spec(4, 8, spec))
         Zo = orc.conserve_intensity(orc.phase_table_spec(mu, phi, spec))
         assert np.abs(Zl - Zo).max() <= 1e-14 * max(1.0, np.abs(Zo).max())
+
+
+@pytest.mark.parametrize("plane", ["xz", "xy"])
+@pytest.mark.parametrize("nzen,naz", [(2, 4), (4, 8), (8, 8), (3, 6), (1, 4), (5, 7)])
+def test_bilinear_taps_match_oracle(orc, nzen, naz, plane):
+    mu, phi = orc.direction_grid(nzen, naz)
+    pl = {"xz": orc.PLANE_XZ, "xy": orc.PLANE_XY}[plane]
+    ox, oz, w = S.stream_taps(nzen, naz, "bilinear", plane)
+    rx, rz, rw, _, _ = orc.bilinear_taps(mu, phi, pl)
+    assert np.array_equal(ox, rx) and np.array_equal(oz, rz)
+    assert np.abs(w - rw).max() < 1e-15
+
+
+def test_nearest_taps_and_xy_offsets_match_oracle(orc):
+    for nzen, naz in [(2, 4), (4, 8), (3, 6)]:
+        mu, phi = orc.direction_grid(nzen, naz)
+        for plane, pl in (("xz", orc.PLANE_XZ), ("xy", orc.PLANE_XY)):
+            ox, oz, w = S.stream_taps(nzen, naz, "nearest", plane)
+            cx, cz = orc.stream_offsets(mu, phi, pl)
+            assert np.array_equal(ox[:, 0], cx) and np.array_equal(oz[:, 0], cz)
+            assert (w[:, 0] == 1).all() and not w[:, 1:].any()
+
+
+def test_offset_azimuths_need_bilinear_streaming(orc):
+    """Table 1's azimuths offset by 22.5 deg on the horizontal lattice lie
+    between two D2Q9 offsets: the nearest scheme rejects them, the bilinear
+    one streams them."""
+    mu = np.array([-0.5] * 4 + [0.5] * 4)
+    phi = np.radians([22.5, 112.5, 202.5, 292.5] * 2)
+    with pytest.raises(_lib.RtlbError) as ei:
+        S.stream_taps(2, 4, "nearest", "xy", mu, phi)
+    assert ei.value.status == 4
+    ox, oz, w = S.stream_taps(2, 4, "bilinear", "xy", mu, phi)
+    rx, rz, rw, _, _ = orc.bilinear_taps(mu, phi, orc.PLANE_XY)
+    assert np.array_equal(ox, rx) and np.array_equal(oz, rz) and np.abs(w - rw).max() < 1e-15
+
+
+def test_stream_taps_argument_errors():
+    L = _lib.lib()
+    d = _lib.Directions(2, 4, None, None)
+    o = np.zeros(32, np.int32)
+    w = np.zeros(32)
+    assert L.rtlb_stream_taps(C.byref(d), 2, 0, o.ctypes.data, o.ctypes.data, w.ctypes.data) == 1
+    assert L.rtlb_stream_taps(C.byref(d), 1, 5, o.ctypes.data, o.ctypes.data, w.ctypes.data) == 1
+    assert L.rtlb_stream_taps(C.byref(d), 1, 0, None, o.ctypes.data, w.ctypes.data) == 1
