@@ -313,6 +313,32 @@ def batch_throughput(steps: int, count: int = 256):
     return out
 
 
+def bilinear_throughput(precision: str, steps: int, nearest_ms: float, peaks, src):
+    """The same workload with semi-Lagrangian bilinear streaming (Eq. 34):
+    an in-place collision pass, then the four-tap gather kernel."""
+    import torch
+    from paper_2609_23057_b300.solver import solver_for
+    w = W.precision(seed=1, steps=steps)
+    w.scheme = "bilinear"
+    s = solver_for(w, precision)
+    s.step(3)
+    torch.cuda.synchronize()
+    per, tot = _time_steps(torch, s, torch.cuda.current_stream(), steps)
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    sdu = w.sites * w.n
+    ms = tot / len(per)
+    gather_ms = ms - nearest_ms
+    gbs = 32.0 * sdu / (gather_ms * 1e-3) / 1e9 if gather_ms > 0 else None
+    return {"workload": w.name + "_bilinear", "precision": precision, "value": sdu * len(per) / (tot * 1e-3),
+            "unit": UNIT, "ms_per_step": ms, "steps": len(per), "gpu_launches_per_step": 2,
+            "gather_ms_estimate": gather_ms,
+            "gather_roofline": {"bound": "hbm", "achieved": gbs, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                                "frac": None if gbs is None else gbs / float(peaks["hbm_gbs"]),
+                                "note": "32 B per site-direction over (bilinear step - nearest step) time"}}
+
+
 def run_ours(args):
     import torch
     from paper_2609_23057_b300 import solver as SV
@@ -414,6 +440,8 @@ def run_ours(args):
             "compare": compare,
             "adjoint_over_forward": None,
         }
+        if ws == 1 and args.bilinear_steps > 0 and args.nx == 2048 and args.nz == 2048:
+            line["bilinear"] = bilinear_throughput(args.precision, args.bilinear_steps, t_max / args.steps, peaks, src)
         if ws == 1 and args.batch_steps > 0:
             line["batch"] = batch_throughput(args.batch_steps)
         if ws == 1 and args.adjoint_steps > 0:
@@ -441,6 +469,8 @@ def main():
                     help="headline form; bf16x2 is the tensor-core form that meets 1e-3 on the crop")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the FP32 comparison form")
+    ap.add_argument("--bilinear-steps", type=int, default=50,
+                    help="steps of the bilinear-streaming timing (0 = skip)")
     ap.add_argument("--batch-steps", type=int, default=500,
                     help="steps of the 256-channel batch timing (0 = skip)")
     ap.add_argument("--adjoint-steps", type=int, default=1000,
