@@ -198,20 +198,28 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         uint32_t g = 0;
         bool ok = true;
+        // the next item's coefficients are fetched a tile ahead (see load_coef)
+        auto coef_of = [&](int k) {
+            const int2 it = items[t_begin + k];
+            const ChanDesc *d = descs + it.x;
+            return load_coef(d->coef, (it.y & 0xFFFFFF) * kTileM + r, d->nx * d->nz);
+        };
+        float4 cf_next = T > 0 ? coef_of(0) : float4{};
         for (int i = 0; i < T && ok; ++i) {
             const int2 it = items[t_begin + i];
             const ChanDesc *d = descs + it.x;
-            const int tile = it.y & 0xFFFFFF, cls = it.y >> 24;
-            const int n = d->n, nsites = d->nx * d->nz;
+            const int cls = it.y >> 24;
+            const int n = d->n;
             const int b = i & 1;
-            const int site = tile * kTileM + r;
+            const float4 cf = cf_next;
+            if (i + 1 < T) cf_next = coef_of(i + 1);
             ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_empty[b]), ((i >> 1) & 1) ^ 1, abort_flag, err,
                                                    kErrTimeoutConverter));
             if (!ok) break;
             tc_fence_after();
             const uint32_t acc = tmem + lane_base + (uint32_t)(b * kMaxN4);
-            ok = convert_tile<false>(d->coef + site, d->fwd + (size_t)cls * n, nsites, site, r, lane, n, n / kDirsPerStage,
-                                     stages, g, i, acc, sA, sA, sStage, st_full, st_empty, a_empty, a_chunk, abort_flag, err);
+            ok = convert_tile<false>(cf, d->fwd + (size_t)cls * n, r, lane, n, n / kDirsPerStage, stages, g, i, acc, sA,
+                                     sA, sStage, st_full, st_empty, a_empty, a_chunk, abort_flag, err);
             if (!ok) break;
             tmem_wait_st();
             fence_proxy_async();

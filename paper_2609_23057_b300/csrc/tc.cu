@@ -258,19 +258,25 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         uint32_t g = 0;
         bool ok = true;
+        // tile entries two ahead, coefficients one ahead (see load_coef)
+        int e_next = T > 0 ? p.tiles[t_begin] : 0, e_after = T > 1 ? p.tiles[t_begin + 1] : 0;
+        float4 cf_next = T > 0 ? load_coef(p.coef, (e_next & 0xFFFFFF) * kTileM + r, nsites) : float4{};
         for (int i = 0; i < T && ok; ++i) {
-            const int entry = p.tiles[t_begin + i];
-            const int tile = entry & 0xFFFFFF;
+            const int entry = e_next;
+            const float4 cf = cf_next;
             const int b = i & 1;
-            const int site = tile * kTileM + r;
+            if (i + 1 < T) {
+                e_next = e_after;
+                cf_next = load_coef(p.coef, (e_next & 0xFFFFFF) * kTileM + r, nsites);
+                if (i + 2 < T) e_after = p.tiles[t_begin + i + 2];
+            }
             ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_empty[b]), ((i >> 1) & 1) ^ 1, abort_flag, p.err,
                                                    kErrTimeoutConverter));
             if (!ok) break;
             tc_fence_after();
             const uint32_t acc = tmem + lane_base + (uint32_t)(b * N4);
-            ok = convert_tile<ALO>(p.coef + site, p.fwd + (size_t)(entry >> 24) * n, nsites, site, r, lane, n, groups,
-                                   stages, g, i, acc, sA, sAlo, sStage, st_full, st_empty, a_empty, a_chunk, abort_flag,
-                                   p.err);
+            ok = convert_tile<ALO>(cf, p.fwd + (size_t)(entry >> 24) * n, r, lane, n, groups, stages, g, i, acc, sA,
+                                   sAlo, sStage, st_full, st_empty, a_empty, a_chunk, abort_flag, p.err);
             if (!ok) break;
             tmem_wait_st();
             fence_proxy_async();
@@ -338,9 +344,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 // TMEM init, epilogue exactly as above) and holds rows [r N/2, (r+1) N/2) of
 // the table's hi and lo parts.  The even CTA issues M = 256 MMAs that read A
 // from both CTAs and B halves from each; their commits are multicast to both
-// CTAs' barriers.  The odd CTA's converter reports a ready tile to the even
-// CTA with a remote mbarrier arrive, and its producer forwards the completion
-// of its half of the table the same way.
+// CTAs' barriers.  The odd CTA's converter warps report a ready tile on a
+// local barrier; one thread of its otherwise idle MMA warp forwards it to the
+// even CTA with a single remote (cluster-scope release) arrive, which keeps
+// that microsecond-long release off the converters' path.  Its producer
+// forwards the completion of its half of the table the same way.
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     k_step_tc_pair(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmZhi,
                    const __grid_constant__ CUtensorMap tmZlo, TcParams p, int N4, int stages)
@@ -371,7 +379,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     uint64_t *z_full = acc_empty + 2;          // [1]   even CTA: own TMA + odd CTA's forward
     uint64_t *drain = z_full + 1;              // [1]   multicast commit
     uint64_t *z_free = drain + 1;              // [1]   multicast commit: the resident table is no longer read
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(z_free + 1);
+    uint64_t *t_local = z_free + 1;            // [2]   odd CTA: its 4 converter warps, forwarded to the even CTA
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(t_local + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     int8_t *s_cx = reinterpret_cast<int8_t *>(tmem_slot + 2);
     int8_t *s_cz = s_cx + kMaxDirs;
@@ -386,7 +395,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         }
         for (int c = 0; c < C; ++c) mbar_init(smem_u32(&a_empty[c]), 1);
         for (int b = 0; b < 2; ++b) {
-            mbar_init(smem_u32(&t_ready[b]), 8);
+            mbar_init(smem_u32(&t_ready[b]), 5);   // 4 local converter warps + the odd CTA's forward
+            mbar_init(smem_u32(&t_local[b]), 4);
             mbar_init(smem_u32(&acc_full[b]), 1);
             mbar_init(smem_u32(&acc_empty[b]), kEpiWarps);
         }
@@ -492,34 +502,51 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 issued = true;
             }
             if (issued) mma_commit_pair(smem_u32(drain), 0x3);
+        } else if (lane == 0) {
+            // odd CTA: forward each tile's readiness (A rows in shared memory,
+            // accumulator initialized in TMEM) to the even CTA.  One
+            // cluster-scope release per tile, off the converter warps' path
+            // (a release at cluster scope costs about a microsecond).
+            for (int i = 0; i < T; ++i) {
+                const int b = i & 1;
+                if (!mbar_wait(smem_u32(&t_local[b]), (i >> 1) & 1, abort_flag, p.err, kErrTimeoutMma)) break;
+                tc_fence_after();
+                fence_proxy_async();
+                tc_fence_before();
+                mbar_arrive_cluster(mapa(smem_u32(&t_ready[b]), 0));
+            }
         }
         __syncwarp();
     } else if (warp >= kConvWarp0) {
         const int q = warp & 3;
         const int r = q * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        const uint32_t t_ready_leader0 = mapa(smem_u32(&t_ready[0]), 0);
-        const uint32_t t_ready_leader1 = mapa(smem_u32(&t_ready[1]), 0);
         uint32_t g = 0;
         bool ok = true;
+        // coefficients and classes fetched a tile ahead (see load_coef)
+        float4 cf_next = T > 0 ? load_coef(p.coef, my_tile(0) * kTileM + r, nsites) : float4{};
+        int cls_next = T > 0 ? pair_cls(0) : 0;
         for (int i = 0; i < T && ok; ++i) {
-            const int tile = my_tile(i);
+            const float4 cf = cf_next;
+            const int cls = cls_next;
             const int b = i & 1;
-            const int site = tile * kTileM + r;
+            if (i + 1 < T) {
+                cf_next = load_coef(p.coef, my_tile(i + 1) * kTileM + r, nsites);
+                cls_next = pair_cls(i + 1);
+            }
             ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_empty[b]), ((i >> 1) & 1) ^ 1, abort_flag, p.err,
                                                    kErrTimeoutConverter));
             if (!ok) break;
             tc_fence_after();
             const uint32_t acc = tmem + lane_base + (uint32_t)(b * N4);
-            ok = convert_tile<false>(p.coef + site, p.fwd + (size_t)pair_cls(i) * n, nsites, site, r, lane, n, groups,
-                                     stages, g, i, acc, sA, sA, sStage, st_full, st_empty, a_empty, a_chunk, abort_flag,
-                                     p.err);
+            ok = convert_tile<false>(cf, p.fwd + (size_t)cls * n, r, lane, n, groups, stages, g, i, acc, sA, sA, sStage,
+                                     st_full, st_empty, a_empty, a_chunk, abort_flag, p.err);
             if (!ok) break;
             tmem_wait_st();
             fence_proxy_async();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive_cluster(b ? t_ready_leader1 : t_ready_leader0);
+            if (lane == 0) mbar_arrive(smem_u32(leader ? &t_ready[b] : &t_local[b]));
         }
     } else {
         const int q = warp & 3;
@@ -651,7 +678,7 @@ size_t smem_bytes_pair(int N4, int stages)
 {
     const int C = (N4 + 63) / 64;
     size_t b = (size_t)C * (N4 / 2) * 128 * 2 + (size_t)C * kTileM * 128 + (size_t)stages * kStageBytes +
-               (size_t)(2 * stages + C + 9) * 8 + 16 + 2 * kMaxDirs;
+               (size_t)(2 * stages + C + 11) * 8 + 16 + 2 * kMaxDirs;
     return b + 1024;
 }
 
@@ -660,10 +687,14 @@ int mode_of(int precision)
     return precision == RTLB_PREC_BF16X3 ? 3 : (precision == RTLB_PREC_BF16X2 ? 2 : 1);
 }
 
+#ifndef RTLB_TC_MAX_STAGES
+#define RTLB_TC_MAX_STAGES 8
+#endif
+
 // Largest stage count that fits (0 = does not fit).
 int fit_stages(int N4, int mode, bool pair)
 {
-    for (int st = 8; st >= 2; --st)
+    for (int st = RTLB_TC_MAX_STAGES; st >= 2; --st)
         if ((pair ? smem_bytes_pair(N4, st) : smem_bytes(N4, mode, st)) <= (size_t)kSmemLimit) return st;
     return 0;
 }

@@ -25,6 +25,14 @@ constexpr int kSmemLimit = 232448;                  // max dynamic smem per bloc
 enum ErrCode { kErrTimeoutProducer = 1, kErrTimeoutConverter = 2, kErrTimeoutMma = 4, kErrTimeoutEpilogue = 8 };
 
 
+// Per-site coefficients {alpha_hi, alpha_lo, beta, e} of one tile row (zero
+// past the end of the lattice).  Converters fetch them a tile ahead so the
+// global-memory latency overlaps the previous tile's conversion.
+__device__ __forceinline__ float4 load_coef(const float4 *coef, int site, int nsites)
+{
+    return site < nsites ? __ldg(coef + site) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // Converter work for one tile (one site row per thread, TMEM lane r).  For
 // each 64-wide K chunk of the A operand (16 directions = two staging slots)
 // it first drains both slots into registers -- writing the float32 part
@@ -33,13 +41,11 @@ enum ErrCode { kErrTimeoutProducer = 1, kErrTimeoutConverter = 2, kErrTimeoutMma
 // the converter then waits for the MMA to free that A chunk.  Returns false
 // when a bounded wait gave up.
 template <bool ALO>
-__device__ __forceinline__ bool convert_tile(const float4 *coef_site, const float *fwd, int nsites, int site, int r,
-                                             int lane, int n, int groups, int stages, uint32_t &g, int i,
-                                             uint32_t acc, uint8_t *sA, uint8_t *sAlo, const uint8_t *sStage,
-                                             uint64_t *st_full, uint64_t *st_empty, uint64_t *a_empty,
-                                             uint32_t a_chunk, volatile int *abort_flag, int *err)
+__device__ __forceinline__ bool convert_tile(const float4 cf, const float *fwd, int r, int lane, int n, int groups,
+                                             int stages, uint32_t &g, int i, uint32_t acc, uint8_t *sA, uint8_t *sAlo,
+                                             const uint8_t *sStage, uint64_t *st_full, uint64_t *st_empty,
+                                             uint64_t *a_empty, uint32_t a_chunk, volatile int *abort_flag, int *err)
 {
-    const float4 cf = site < nsites ? *coef_site : make_float4(0.f, 0.f, 0.f, 0.f);
     const int half = r / kHalfSites, hr = r % kHalfSites;
     const int C = (4 * n + 63) / 64;
     for (int c = 0; c < C; ++c) {

@@ -69,10 +69,12 @@ __device__ __forceinline__ unsigned long long global_ns()
 
 // Bounded wait on one mbarrier phase.  Returns false (after raising the CTA's
 // abort flag and recording `code`) when the wait times out or another role
-// has already aborted.
-static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err, int code)
+// has already aborted.  Inlined entirely: a function call makes the warp
+// wait for all of its outstanding loads, which would expose the latency of
+// loads issued ahead on purpose (the converters' coefficient prefetch).
+__device__ __forceinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err,
+                                                   int code)
 {
-    if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (unsigned it = 1;; ++it) {
         if (mbar_try(bar, parity)) return true;
@@ -85,6 +87,11 @@ static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, vol
             }
         }
     }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err, int code)
+{
+    return mbar_try(bar, parity) || mbar_wait_slow(bar, parity, abort_flag, err, code);
 }
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1, int c2)
