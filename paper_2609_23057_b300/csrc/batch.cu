@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int c = 0; c < kMaxC; ++c) mbar_init(smem_u32(&a_empty[c]), 1);
         for (int b = 0; b < 2; ++b) {
-            mbar_init(smem_u32(&t_ready[b]), 4);
+            mbar_init(smem_u32(&t_ready[b]), kConvWarps);
             mbar_init(smem_u32(&acc_full[b]), 1);
             mbar_init(smem_u32(&acc_empty[b]), kEpiWarps);
         }
@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
     } else if (warp >= kConvWarp0) {
         const int q = warp & 3;
+        const int grp = (warp - kConvWarp0) >> 2;
         const int r = q * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         uint32_t g = 0;
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!ok) break;
             tc_fence_after();
             const uint32_t acc = tmem + lane_base + (uint32_t)(b * kMaxN4);
-            ok = convert_tile<false>(cf, d->fwd + (size_t)cls * n, r, lane, n, n / kDirsPerStage, stages, g, i, acc, sA,
+            ok = convert_tile<false>(cf, d->fwd + (size_t)cls * n, r, lane, grp, n, n / kDirsPerStage, stages, g, i, acc, sA,
                                      sA, sStage, st_full, st_empty, a_empty, a_chunk, abort_flag, err);
             if (!ok) break;
             tmem_wait_st();

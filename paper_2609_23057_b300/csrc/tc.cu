@@ -16,11 +16,11 @@
 // Persistent kernel, one CTA per SM, warp roles:
 //   warps 0-7   epilogue   (TMEM lane quadrant = warp % 4, one site per thread,
 //                           warps 4-7 take the second half of the directions)
-//   warps 8-11  converter  (FP32 staging -> bf16 A operand in the 128-byte
-//                           swizzled K-major layout, alpha * S~ -> TMEM)
-//   warp  12    producer   (TMA loads of state chunks and of Z, L2 prefetch
-//                           two tiles ahead)
-//   warp  13    MMA issuer (one thread; also allocates TMEM)
+//   warps 8-15  converter  (FP32 staging -> bf16 A operand in the 128-byte
+//                           swizzled K-major layout, alpha * S~ -> TMEM; two
+//                           groups of four take alternate staging slots)
+//   warp  16    producer   (TMA loads of state chunks and of Z)
+//   warp  17    MMA issuer (one thread; also allocates TMEM)
 // Z (one phase class at a time) and the whole A operand of the current tile
 // stay in shared memory; TMEM holds two accumulators so the epilogue of one
 // tile overlaps the next tile's conversion and MMAs.  Tiles whose sites mix
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int c = 0; c < C; ++c) mbar_init(smem_u32(&a_empty[c]), 1);
         for (int b = 0; b < 2; ++b) {
-            mbar_init(smem_u32(&t_ready[b]), 4);
+            mbar_init(smem_u32(&t_ready[b]), kConvWarps);
             mbar_init(smem_u32(&acc_full[b]), 1);
             mbar_init(smem_u32(&acc_empty[b]), kEpiWarps);
         }
@@ -254,6 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp >= kConvWarp0) {
         // ----------------------------------------------------------- converter
         const int q = warp & 3;
+        const int grp = (warp - kConvWarp0) >> 2;  // staging-slot group
         const int r = q * 32 + lane;               // site row = TMEM lane
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         uint32_t g = 0;
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!ok) break;
             tc_fence_after();
             const uint32_t acc = tmem + lane_base + (uint32_t)(b * N4);
-            ok = convert_tile<ALO>(cf, p.fwd + (size_t)(entry >> 24) * n, r, lane, n, groups, stages, g, i, acc, sA,
+            ok = convert_tile<ALO>(cf, p.fwd + (size_t)(entry >> 24) * n, r, lane, grp, n, groups, stages, g, i, acc, sA,
                                    sAlo, sStage, st_full, st_empty, a_empty, a_chunk, abort_flag, p.err);
             if (!ok) break;
             tmem_wait_st();
@@ -395,8 +396,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         }
         for (int c = 0; c < C; ++c) mbar_init(smem_u32(&a_empty[c]), 1);
         for (int b = 0; b < 2; ++b) {
-            mbar_init(smem_u32(&t_ready[b]), 5);   // 4 local converter warps + the odd CTA's forward
-            mbar_init(smem_u32(&t_local[b]), 4);
+            mbar_init(smem_u32(&t_ready[b]), kConvWarps + 1);   // local converter warps + the odd CTA's forward
+            mbar_init(smem_u32(&t_local[b]), kConvWarps);
             mbar_init(smem_u32(&acc_full[b]), 1);
             mbar_init(smem_u32(&acc_empty[b]), kEpiWarps);
         }
@@ -519,6 +520,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         __syncwarp();
     } else if (warp >= kConvWarp0) {
         const int q = warp & 3;
+        const int grp = (warp - kConvWarp0) >> 2;
         const int r = q * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         uint32_t g = 0;
@@ -539,7 +541,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             if (!ok) break;
             tc_fence_after();
             const uint32_t acc = tmem + lane_base + (uint32_t)(b * N4);
-            ok = convert_tile<false>(cf, p.fwd + (size_t)cls * n, r, lane, n, groups, stages, g, i, acc, sA, sA, sStage,
+            ok = convert_tile<false>(cf, p.fwd + (size_t)cls * n, r, lane, grp, n, groups, stages, g, i, acc, sA, sA, sStage,
                                      st_full, st_empty, a_empty, a_chunk, abort_flag, p.err);
             if (!ok) break;
             tmem_wait_st();

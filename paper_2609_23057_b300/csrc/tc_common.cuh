@@ -10,11 +10,12 @@ namespace tccommon {
 using namespace tcptx;
 
 constexpr int kTileM = 128;
-constexpr int kWarps = 14;
+constexpr int kWarps = 18;
 constexpr int kEpiWarps = 8;
 constexpr int kConvWarp0 = 8;
-constexpr int kProdWarp = 12;
-constexpr int kMmaWarp = 13;
+constexpr int kConvWarps = 8;                       // two groups of four (one TMEM lane quadrant each)
+constexpr int kProdWarp = 16;
+constexpr int kMmaWarp = 17;
 constexpr int kThreads = kWarps * 32;
 constexpr int kDirsPerStage = 8;                    // directions per state chunk
 constexpr int kStageBytes = kDirsPerStage * kTileM * 16;
@@ -33,53 +34,54 @@ __device__ __forceinline__ float4 load_coef(const float4 *coef, int site, int ns
     return site < nsites ? __ldg(coef + site) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// Converter work for one tile (one site row per thread, TMEM lane r).  For
-// each 64-wide K chunk of the A operand (16 directions = two staging slots)
-// it first drains both slots into registers -- writing the float32 part
-// (alpha_hi + alpha_lo + beta c_d) S~ into the TMEM accumulator and packing
-// beta S~ to bf16 -- and releases them, so the producer keeps loading while
-// the converter then waits for the MMA to free that A chunk.  Returns false
-// when a bounded wait gave up.
+// Converter work for one tile (one site row per thread, TMEM lane r).  The
+// converter warps form two groups; each 64-wide K chunk of the A operand (16
+// directions) comes in two staging slots of 8 directions, and group `grp`
+// takes slot 2c + grp: it writes the float32 part (alpha_hi + alpha_lo +
+// beta c_d) S~ of its directions into the TMEM accumulator, packs beta S~ to
+// bf16 in registers and releases the slot, then waits for the MMA to free A
+// chunk c and stores its half of the chunk's 128-byte rows.  Both groups
+// count every slot of the tile in `g`.  Returns false when a bounded wait
+// gave up.
 template <bool ALO>
-__device__ __forceinline__ bool convert_tile(const float4 cf, const float *fwd, int r, int lane, int n, int groups,
-                                             int stages, uint32_t &g, int i, uint32_t acc, uint8_t *sA, uint8_t *sAlo,
-                                             const uint8_t *sStage, uint64_t *st_full, uint64_t *st_empty,
-                                             uint64_t *a_empty, uint32_t a_chunk, volatile int *abort_flag, int *err)
+__device__ __forceinline__ bool convert_tile(const float4 cf, const float *fwd, int r, int lane, int grp, int n,
+                                             int groups, int stages, uint32_t &g, int i, uint32_t acc, uint8_t *sA,
+                                             uint8_t *sAlo, const uint8_t *sStage, uint64_t *st_full,
+                                             uint64_t *st_empty, uint64_t *a_empty, uint32_t a_chunk,
+                                             volatile int *abort_flag, int *err)
 {
     const int half = r / kHalfSites, hr = r % kHalfSites;
     const int C = (4 * n + 63) / 64;
     for (int c = 0; c < C; ++c) {
-        const int d_beg = 16 * c, d_end = min(n, 16 * c + 16);
-        float fw[16];
+        const int j = 2 * c + grp;                   // this group's slot of chunk c
+        const int d_beg = 8 * j;                     // its 8 directions (all < n when j < groups)
+        const bool mine = j < groups;
+        uint4 packed[4], packed_lo[4];
+        if (mine) {
+            float fw[8];
 #pragma unroll
-        for (int k = 0; k < 16; k += 4) {
-            const float4 f = (d_beg + k < d_end) ? __ldg(reinterpret_cast<const float4 *>(fwd + d_beg + k))
-                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-            fw[k] = f.x;
-            fw[k + 1] = f.y;
-            fw[k + 2] = f.z;
-            fw[k + 3] = f.w;
-        }
-        uint4 packed[8], packed_lo[8];
-#pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-            const int j = 2 * c + jj;
-            if (j >= groups) break;
-            const int s = g % stages;
-            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&st_full[s]), (g / stages) & 1, abort_flag, err,
+            for (int k = 0; k < 8; k += 4) {
+                const float4 f = __ldg(reinterpret_cast<const float4 *>(fwd + d_beg + k));
+                fw[k] = f.x;
+                fw[k + 1] = f.y;
+                fw[k + 2] = f.z;
+                fw[k + 3] = f.w;
+            }
+            const uint32_t seq = g + (uint32_t)j;
+            const int s = seq % stages;
+            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&st_full[s]), (seq / stages) & 1, abort_flag, err,
                                                    kErrTimeoutConverter)))
                 return false;
             const float4 *stg = reinterpret_cast<const float4 *>(sStage + (size_t)s * kStageBytes) +
                                 half * (kDirsPerStage * kHalfSites) + hr;
 #pragma unroll
             for (int dl = 0; dl < kDirsPerStage; dl += 2) {
-                const int d = j * kDirsPerStage + dl;
+                const int d = d_beg + dl;
                 float4 v0 = stg[dl * kHalfSites], v1 = stg[(dl + 1) * kHalfSites];
                 v0.x += cf.w;                               // emission (I only)
                 v1.x += cf.w;
                 const float sv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-                const int fi = jj * kDirsPerStage + dl;
-                const float g0 = fmaf(cf.z, fw[fi], cf.y), g1 = fmaf(cf.z, fw[fi + 1], cf.y);
+                const float g0 = fmaf(cf.z, fw[dl], cf.y), g1 = fmaf(cf.z, fw[dl + 1], cf.y);
                 float init[8], bs[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
@@ -92,10 +94,10 @@ __device__ __forceinline__ bool convert_tile(const float4 cf, const float *fwd, 
                 hi.y = pack_bf16(bs[2], bs[3]);
                 hi.z = pack_bf16(bs[4], bs[5]);
                 hi.w = pack_bf16(bs[6], bs[7]);
-                packed[fi >> 1] = hi;
+                packed[dl >> 1] = hi;
                 if (ALO) {
                     const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&hi);
-                    uint32_t *lw = reinterpret_cast<uint32_t *>(&packed_lo[fi >> 1]);
+                    uint32_t *lw = reinterpret_cast<uint32_t *>(&packed_lo[dl >> 1]);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const float2 f = __bfloat1622float2(h2[k]);
@@ -105,22 +107,23 @@ __device__ __forceinline__ bool convert_tile(const float4 cf, const float *fwd, 
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&st_empty[s]));
-            ++g;
         }
         // A chunk c is free once the previous tile's MMAs on it completed
         if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&a_empty[c]), (i & 1) ^ 1, abort_flag, err, kErrTimeoutConverter)))
             return false;
+        if (mine) {
 #pragma unroll
-        for (int gi = 0; gi < 8; ++gi) {
-            if (d_beg + 2 * gi >= d_end) break;
-            const uint32_t off = c * a_chunk + r * 128u + (((uint32_t)gi ^ (uint32_t)(r & 7)) << 4);
-            *reinterpret_cast<uint4 *>(sA + off) = packed[gi];
-            if (ALO) *reinterpret_cast<uint4 *>(sAlo + off) = packed_lo[gi];
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t gi = 4u * (uint32_t)grp + (uint32_t)k;
+                const uint32_t off = c * a_chunk + r * 128u + ((gi ^ (uint32_t)(r & 7)) << 4);
+                *reinterpret_cast<uint4 *>(sA + off) = packed[k];
+                if (ALO) *reinterpret_cast<uint4 *>(sAlo + off) = packed_lo[k];
+            }
         }
     }
+    g += (uint32_t)groups;
     return true;
 }
-
 
 }  // namespace tccommon
 }  // namespace rtlb
