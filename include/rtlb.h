@@ -220,8 +220,9 @@ void rtlb_destroy(rtlb_ctx *ctx);
 typedef struct rtlb_batch rtlb_batch;
 rtlb_status rtlb_batch_create(int32_t count, rtlb_ctx *const *channels, rtlb_batch **out);
 
-/* Shared-memory pipeline depth of the batch kernel (16-KB state stages, 2..8;
- * default 4).  Results do not depend on it. */
+/* Shared-memory pipeline depth of the batch kernel: 2, 4, 6 or 8 16-KB state
+ * stages (even: the two converter groups own half each; default 4; other
+ * values give RTLB_E_RANGE).  Results do not depend on it. */
 rtlb_status rtlb_batch_configure(rtlb_batch *batch, int32_t stages);
 
 /* Advance every channel nsteps steps on `stream`; pairs of steps replay a

@@ -27,7 +27,10 @@ def _sources():
 
 
 def _headers_mtime():
-    hs = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    # every header a translation unit may include: C/C++ headers and the
+    # device-code headers (*.cuh) shared by the kernels
+    hs = (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+          glob.glob(os.path.join(INCLUDE, "*.h")))
     return max(os.path.getmtime(h) for h in hs)
 
 

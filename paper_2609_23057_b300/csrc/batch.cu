@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == kProdWarp) {
         if (lane == 0) {
             int prev = -1;
-            uint32_t g = 0, zr = 0;
+            uint32_t gq[2] = {0, 0}, zr = 0;
             bool ok = true;
             for (int i = 0; i < T && ok; ++i) {
                 const int2 it = items[t_begin + i];
@@ -128,9 +128,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     prev = key;
                 }
-                for (int j = 0; j < groups && ok; ++j, ++g) {
-                    const int s = g % stages;
-                    ok = mbar_wait(smem_u32(&st_empty[s]), ((g / stages) & 1) ^ 1, abort_flag, err, kErrTimeoutProducer);
+                for (int j = 0; j < groups && ok; ++j) {
+                    const int gr = j & 1;
+                    const uint32_t local = gq[gr]++;
+                    const int s = ring_slot(gr, local, stages / 2);
+                    ok = mbar_wait(smem_u32(&st_empty[s]), ((local / (uint32_t)(stages / 2)) & 1) ^ 1, abort_flag, err,
+                                   kErrTimeoutProducer);
                     if (!ok) break;
                     const uint32_t fb = smem_u32(&st_full[s]);
                     mbar_expect_tx(fb, kStageBytes);
@@ -139,13 +142,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                                     4 * (tile * kTileM + h * kHalfSites), j * kDirsPerStage);
                 }
             }
-            for (uint32_t k = 0; k < (uint32_t)stages && k < g; ++k) {
-                const uint32_t gg = g - 1 - k;
-                const int s = gg % stages;
-                unsigned long long t0 = global_ns();
-                while (!mbar_try(smem_u32(&st_full[s]), (gg / stages) & 1) && global_ns() - t0 < kTimeoutNs) {
+            for (int gr = 0; gr < 2; ++gr)
+                for (uint32_t k = 0; k < (uint32_t)(stages / 2) && k < gq[gr]; ++k) {
+                    const uint32_t local = gq[gr] - 1 - k;
+                    const int s = ring_slot(gr, local, stages / 2);
+                    unsigned long long t0 = global_ns();
+                    while (!mbar_try(smem_u32(&st_full[s]), (local / (uint32_t)(stages / 2)) & 1) &&
+                           global_ns() - t0 < kTimeoutNs) {
+                    }
                 }
-            }
         }
     } else if (warp == kMmaWarp) {
         if (lane == 0) {
@@ -197,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int grp = (warp - kConvWarp0) >> 2;
         const int r = q * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        uint32_t g = 0;
+        uint32_t gq = 0;
         bool ok = true;
         // the next item's coefficients are fetched a tile ahead (see load_coef)
         auto coef_of = [&](int k) {
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!ok) break;
             tc_fence_after();
             const uint32_t acc = tmem + lane_base + (uint32_t)(b * kMaxN4);
-            ok = convert_tile<false>(cf, d->fwd + (size_t)cls * n, r, lane, grp, n, n / kDirsPerStage, stages, g, i, acc, sA,
+            ok = convert_tile<false>(cf, d->fwd + (size_t)cls * n, r, lane, grp, n, n / kDirsPerStage, stages, gq, i, acc, sA,
                                      sA, sStage, st_full, st_empty, a_empty, a_chunk, abort_flag, err);
             if (!ok) break;
             tmem_wait_st();
@@ -445,8 +450,8 @@ rtlb_status rtlb_batch_create(int32_t count, rtlb_ctx *const *channels, rtlb_bat
 rtlb_status rtlb_batch_configure(rtlb_batch *b, int32_t stages)
 {
     if (!b) return RTLB_E_ARG;
-    if (stages < 2 || stages > 8 || batch_smem(b->mode, stages) > 232448)
-        return batch_fail(b, RTLB_E_RANGE, "stages must be in [2, 8] and fit in shared memory");
+    if (stages < 2 || stages > 8 || stages % 2 != 0 || batch_smem(b->mode, stages) > 232448)
+        return batch_fail(b, RTLB_E_RANGE, "stages must be 2, 4, 6 or 8 and fit in shared memory");
     if (stages != b->stages) drop_graph(b);
     b->stages = stages;
     return RTLB_OK;

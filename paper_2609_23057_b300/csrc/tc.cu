@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             int prev_cls = -1;
-            uint32_t g = 0, zr = 0;
+            uint32_t gq[2] = {0, 0}, zr = 0;
             bool ok = true;
             for (int i = 0; i < T && ok; ++i) {
                 const int e = p.tiles[t_begin + i];
@@ -187,9 +187,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int h = 0; h < kTileM / kHalfSites; ++h)
                             tma_prefetch_2d(&tmS, 4 * (nt * kTileM + h * kHalfSites), j * kDirsPerStage);
                 }
-                for (int j = 0; j < groups && ok; ++j, ++g) {
-                    const int s = g % stages;
-                    ok = mbar_wait(smem_u32(&st_empty[s]), ((g / stages) & 1) ^ 1, abort_flag, p.err, kErrTimeoutProducer);
+                for (int j = 0; j < groups && ok; ++j) {
+                    const int gr = j & 1;
+                    const uint32_t local = gq[gr]++;
+                    const int s = ring_slot(gr, local, stages / 2);
+                    ok = mbar_wait(smem_u32(&st_empty[s]), ((local / (uint32_t)(stages / 2)) & 1) ^ 1, abort_flag, p.err,
+                                   kErrTimeoutProducer);
                     if (!ok) break;
                     const uint32_t fb = smem_u32(&st_full[s]);
                     mbar_expect_tx(fb, kStageBytes);
@@ -199,13 +202,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             // drain: wait (bounded) for the loads this thread issued into each stage
-            for (uint32_t k = 0; k < (uint32_t)stages && k < g; ++k) {
-                const uint32_t gg = g - 1 - k;
-                const int s = gg % stages;
-                unsigned long long t0 = global_ns();
-                while (!mbar_try(smem_u32(&st_full[s]), (gg / stages) & 1) && global_ns() - t0 < kTimeoutNs) {
+            for (int gr = 0; gr < 2; ++gr)
+                for (uint32_t k = 0; k < (uint32_t)(stages / 2) && k < gq[gr]; ++k) {
+                    const uint32_t local = gq[gr] - 1 - k;
+                    const int s = ring_slot(gr, local, stages / 2);
+                    unsigned long long t0 = global_ns();
+                    while (!mbar_try(smem_u32(&st_full[s]), (local / (uint32_t)(stages / 2)) & 1) &&
+                           global_ns() - t0 < kTimeoutNs) {
+                    }
                 }
-            }
         }
     } else if (warp == kMmaWarp) {
         // ---------------------------------------------------------- MMA issuer
@@ -257,7 +262,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int grp = (warp - kConvWarp0) >> 2;  // staging-slot group
         const int r = q * 32 + lane;               // site row = TMEM lane
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        uint32_t g = 0;
+        uint32_t gq = 0;
         bool ok = true;
         // tile entries two ahead, coefficients one ahead (see load_coef)
         int e_next = T > 0 ? p.tiles[t_begin] : 0, e_after = T > 1 ? p.tiles[t_begin + 1] : 0;
@@ -276,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!ok) break;
             tc_fence_after();
             const uint32_t acc = tmem + lane_base + (uint32_t)(b * N4);
-            ok = convert_tile<ALO>(cf, p.fwd + (size_t)(entry >> 24) * n, r, lane, grp, n, groups, stages, g, i, acc, sA,
+            ok = convert_tile<ALO>(cf, p.fwd + (size_t)(entry >> 24) * n, r, lane, grp, n, groups, stages, gq, i, acc, sA,
                                    sAlo, sStage, st_full, st_empty, a_empty, a_chunk, abort_flag, p.err);
             if (!ok) break;
             tmem_wait_st();
@@ -429,7 +434,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     if (warp == kProdWarp) {
         if (lane == 0) {
             int prev_cls = -1;
-            uint32_t g = 0, zl = 0, zr = 0;
+            uint32_t gq[2] = {0, 0}, zl = 0, zr = 0;
             bool ok = true;
             for (int i = 0; i < T && ok; ++i) {
                 const int tile = my_tile(i), cls = pair_cls(i);
@@ -451,9 +456,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     ++zl;
                     prev_cls = cls;
                 }
-                for (int j = 0; j < groups && ok; ++j, ++g) {
-                    const int s = g % stages;
-                    ok = mbar_wait(smem_u32(&st_empty[s]), ((g / stages) & 1) ^ 1, abort_flag, p.err, kErrTimeoutProducer);
+                for (int j = 0; j < groups && ok; ++j) {
+                    const int gr = j & 1;
+                    const uint32_t local = gq[gr]++;
+                    const int s = ring_slot(gr, local, stages / 2);
+                    ok = mbar_wait(smem_u32(&st_empty[s]), ((local / (uint32_t)(stages / 2)) & 1) ^ 1, abort_flag, p.err,
+                                   kErrTimeoutProducer);
                     if (!ok) break;
                     const uint32_t fb = smem_u32(&st_full[s]);
                     mbar_expect_tx(fb, kStageBytes);
@@ -462,13 +470,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                                     4 * (tile * kTileM + h * kHalfSites), j * kDirsPerStage);
                 }
             }
-            for (uint32_t k = 0; k < (uint32_t)stages && k < g; ++k) {
-                const uint32_t gg = g - 1 - k;
-                const int s = gg % stages;
-                unsigned long long t0 = global_ns();
-                while (!mbar_try(smem_u32(&st_full[s]), (gg / stages) & 1) && global_ns() - t0 < kTimeoutNs) {
+            for (int gr = 0; gr < 2; ++gr)
+                for (uint32_t k = 0; k < (uint32_t)(stages / 2) && k < gq[gr]; ++k) {
+                    const uint32_t local = gq[gr] - 1 - k;
+                    const int s = ring_slot(gr, local, stages / 2);
+                    unsigned long long t0 = global_ns();
+                    while (!mbar_try(smem_u32(&st_full[s]), (local / (uint32_t)(stages / 2)) & 1) &&
+                           global_ns() - t0 < kTimeoutNs) {
+                    }
                 }
-            }
         }
     } else if (warp == kMmaWarp) {
         if (lane == 0 && leader) {
@@ -523,7 +533,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         const int grp = (warp - kConvWarp0) >> 2;
         const int r = q * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        uint32_t g = 0;
+        uint32_t gq = 0;
         bool ok = true;
         // coefficients and classes fetched a tile ahead (see load_coef)
         float4 cf_next = T > 0 ? load_coef(p.coef, my_tile(0) * kTileM + r, nsites) : float4{};
@@ -541,7 +551,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             if (!ok) break;
             tc_fence_after();
             const uint32_t acc = tmem + lane_base + (uint32_t)(b * N4);
-            ok = convert_tile<false>(cf, p.fwd + (size_t)cls * n, r, lane, grp, n, groups, stages, g, i, acc, sA, sA, sStage,
+            ok = convert_tile<false>(cf, p.fwd + (size_t)cls * n, r, lane, grp, n, groups, stages, gq, i, acc, sA, sA, sStage,
                                      st_full, st_empty, a_empty, a_chunk, abort_flag, p.err);
             if (!ok) break;
             tmem_wait_st();
@@ -693,10 +703,11 @@ int mode_of(int precision)
 #define RTLB_TC_MAX_STAGES 8
 #endif
 
-// Largest stage count that fits (0 = does not fit).
+// Largest even stage count that fits (0 = does not fit); even because each
+// of the two converter groups owns half of the staging slots.
 int fit_stages(int N4, int mode, bool pair)
 {
-    for (int st = RTLB_TC_MAX_STAGES; st >= 2; --st)
+    for (int st = RTLB_TC_MAX_STAGES & ~1; st >= 2; st -= 2)
         if ((pair ? smem_bytes_pair(N4, st) : smem_bytes(N4, mode, st)) <= (size_t)kSmemLimit) return st;
     return 0;
 }

@@ -34,18 +34,25 @@ __device__ __forceinline__ float4 load_coef(const float4 *coef, int site, int ns
     return site < nsites ? __ldg(coef + site) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// Staging slots: each converter group owns a ring of its own, stages / 2
+// slots (stages is even), and the producer fills group (j & 1)'s ring with
+// slot j of every tile.  A slot therefore always has the same consumer, so a
+// consumer never waits on a slot more than one phase ahead of what it has
+// itself released (a shared ring fed to two groups could let one group pass a
+// parity test a full phase early when the other group lags).
+__device__ __forceinline__ int ring_slot(int grp, uint32_t local, int ring) { return grp * ring + (int)(local % (uint32_t)ring); }
+
 // Converter work for one tile (one site row per thread, TMEM lane r).  The
 // converter warps form two groups; each 64-wide K chunk of the A operand (16
 // directions) comes in two staging slots of 8 directions, and group `grp`
-// takes slot 2c + grp: it writes the float32 part (alpha_hi + alpha_lo +
-// beta c_d) S~ of its directions into the TMEM accumulator, packs beta S~ to
-// bf16 in registers and releases the slot, then waits for the MMA to free A
-// chunk c and stores its half of the chunk's 128-byte rows.  Both groups
-// count every slot of the tile in `g`.  Returns false when a bounded wait
-// gave up.
+// takes slot j = 2c + grp (its ring's next entry, counted in `gq`): it writes
+// the float32 part (alpha_hi + alpha_lo + beta c_d) S~ of its directions into
+// the TMEM accumulator, packs beta S~ to bf16 in registers and releases the
+// slot, then waits for the MMA to free A chunk c and stores its half of the
+// chunk's 128-byte rows.  Returns false when a bounded wait gave up.
 template <bool ALO>
 __device__ __forceinline__ bool convert_tile(const float4 cf, const float *fwd, int r, int lane, int grp, int n,
-                                             int groups, int stages, uint32_t &g, int i, uint32_t acc, uint8_t *sA,
+                                             int groups, int stages, uint32_t &gq, int i, uint32_t acc, uint8_t *sA,
                                              uint8_t *sAlo, const uint8_t *sStage, uint64_t *st_full,
                                              uint64_t *st_empty, uint64_t *a_empty, uint32_t a_chunk,
                                              volatile int *abort_flag, int *err)
@@ -67,9 +74,10 @@ __device__ __forceinline__ bool convert_tile(const float4 cf, const float *fwd, 
                 fw[k + 2] = f.z;
                 fw[k + 3] = f.w;
             }
-            const uint32_t seq = g + (uint32_t)j;
-            const int s = seq % stages;
-            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&st_full[s]), (seq / stages) & 1, abort_flag, err,
+            const int ring = stages / 2;
+            const uint32_t local = gq++;
+            const int s = ring_slot(grp, local, ring);
+            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&st_full[s]), (local / (uint32_t)ring) & 1, abort_flag, err,
                                                    kErrTimeoutConverter)))
                 return false;
             const float4 *stg = reinterpret_cast<const float4 *>(sStage + (size_t)s * kStageBytes) +
@@ -121,7 +129,6 @@ __device__ __forceinline__ bool convert_tile(const float4 cf, const float *fwd, 
             }
         }
     }
-    g += (uint32_t)groups;
     return true;
 }
 

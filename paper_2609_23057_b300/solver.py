@@ -369,7 +369,7 @@ def _tune_cache_path():
     return os.environ.get("RTLB_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "rtlb_tune.json")
 
 
-def autotune_batch(batch: Batch, candidates=(2, 3, 4, 6, 8), trial_steps: int = 4, cache_path=None) -> int:
+def autotune_batch(batch: Batch, candidates=(2, 4, 6, 8), trial_steps: int = 4, cache_path=None) -> int:
     """Pick the batch kernel's pipeline depth by timing `trial_steps` real
     steps per candidate (every candidate computes the same result, so the
     channels simply advance), remember the choice in a JSON cache keyed by

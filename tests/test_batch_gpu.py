@@ -29,6 +29,59 @@ def _channels():
     return ws
 
 
+def _mixed_n_channels():
+    """Lattices at n = 8 (only one converter group has staging work for
+    them), then n = 16 and n = 32: 313 tiles at n = 8 (odd), 154 at n = 16,
+    153 at n = 32, about four items per CTA, so CTA slices straddle both
+    direction-count changes; some lattices are ragged."""
+    ws = []
+    for k, (nx, nz, nzen, naz) in enumerate([(1024, 37, 2, 4), (64, 3, 2, 4), (320, 6, 2, 4), (1200, 16, 4, 4),
+                                             (130, 3, 4, 4), (596, 32, 4, 8), (100, 5, 4, 8)]):
+        ws.append(W.random_medium(nx, nz, nzen, naz, seed=200 + k, n_phase=1, steps=6))
+    return ws
+
+
+@pytest.mark.parametrize("stages", [2, 4, 6, 8])
+def test_batch_mixed_direction_counts_every_depth(torch_cuda, stages):
+    """Bitwise equality with single stepping at every pipeline depth on a
+    batch whose CTA slices mix n = 8, 16 and 32."""
+    from paper_2609_23057_b300.solver import Batch, solver_for
+    ws = _mixed_n_channels()
+    states = [W.random_state(w.nz, w.nx, w.n, seed=300 + k, dtype=np.float32) for k, w in enumerate(ws)]
+    bs, single = [], []
+    for w, S0 in zip(ws, states):
+        for lst in (bs, single):
+            s = solver_for(w, "bf16")
+            s.set_state(torch_cuda.from_numpy(S0).cuda())
+            lst.append(s)
+    b = Batch(bs)
+    b.configure(stages)
+    b.step(6)
+    b.check()
+    for s in single:
+        s.step(6)
+        s.total_intensity()
+    for k, (sb, ss) in enumerate(zip(bs, single)):
+        assert np.array_equal(sb.get_state().cpu().numpy(), ss.get_state().cpu().numpy()), k
+    b.close()
+    for s in bs + single:
+        s.close()
+
+
+def test_batch_rejects_odd_depth(torch_cuda):
+    from paper_2609_23057_b300 import _lib
+    from paper_2609_23057_b300.solver import Batch, solver_for
+    ss = [solver_for(w, "bf16") for w in _channels()[:2]]
+    b = Batch(ss)
+    for st in (1, 3, 5, 10):
+        with pytest.raises(_lib.RtlbError) as ei:
+            b.configure(st)
+        assert ei.value.status == 3
+    b.close()
+    for s in ss:
+        s.close()
+
+
 @pytest.mark.parametrize("prec", ["bf16", "bf16x2"])
 def test_batch_equals_individual_steps(torch_cuda, orc, prec):
     from paper_2609_23057_b300.solver import Batch, solver_for
