@@ -197,7 +197,7 @@ def _measured_traffic(kernel, sites):
     except (OSError, KeyError, ValueError):
         return None
     src = b"".join(open(os.path.join(HERE, "paper_2609_23057_b300", "csrc", fn), "rb").read()
-                   for fn in ("tc.cu", "step_common.cuh"))
+                   for fn in ("tc.cu", "step_common.cuh", "tc_common.cuh", "tc_ptx.cuh"))
     if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"]:
         return None
     return (rec["dram_bytes_read"] + rec["dram_bytes_write"]) * sites / rec["captured_sites"]
