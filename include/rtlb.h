@@ -185,9 +185,10 @@ rtlb_status rtlb_radiance_out(rtlb_ctx *ctx, int32_t side, float *out, void *str
  * rtlb_phase_hg's dZdg for dL/dg); grad_S0 [nz][nx][n][4] float32 (host or
  * device) -- dL/dS^0.  With BILINEAR streaming the reversed streaming
  * gathers each entry from its four streaming targets with the same weights.
- * Device memory: (ceil(nsteps/checkpoint_every) + checkpoint_every + 3)
- * states (one more for BILINEAR) plus the table-gradient accumulators.  n must
- * be in {8, 16, 32, 64}.  Synchronizes. */
+ * Device memory: ceil(nsteps/checkpoint_every) + max(checkpoint_every - 1, 2)
+ * + 3 states (checkpoint_every = 1: nsteps + 3, and no step is recomputed;
+ * one more for BILINEAR) plus the table-gradient accumulators.  n must be in
+ * {8, 16, 32, 64}.  Synchronizes. */
 rtlb_status rtlb_adjoint(rtlb_ctx *ctx, int32_t nsteps, int32_t checkpoint_every, const float *dL_dout,
                          float *grad_tau, float *grad_albedo, double *grad_Z, float *grad_S0,
                          void *stream);

@@ -568,7 +568,7 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
         }                                             \
     } while (0)
     AK(cudaMalloc(&ck, (size_t)nseg * bytes), "adjoint checkpoints");
-    AK(cudaMalloc(&seg, (size_t)K * bytes), "adjoint segment states");
+    if (K > 1) AK(cudaMalloc(&seg, (size_t)std::max(K - 1, 2) * bytes), "adjoint segment states");
     AK(cudaMalloc(&lam, 2 * bytes), "adjoint lambda");
     AK(cudaMalloc(&bm, bytes), "adjoint beta mu");
     AK(cudaMalloc(&ga, ns * sizeof(double)), "adjoint g_alpha");
@@ -595,15 +595,22 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
         AK(cudaMemcpyAsync(dl, dL_dout, dl_bytes, cudaMemcpyHostToDevice, s), "adjoint seed upload");
         dl_dev = dl;
     }
-    // forward in float32 with a checkpoint at the start of every segment
+    // forward in float32, stepping from checkpoint to checkpoint: segment g
+    // starts at ck[g] and ends in ck[g + 1] (the last one in the state buffer
+    // the context's step count points at), through at most two scratch
+    // states in between; no state is copied except S^0.
+    const int fin = c->cur ^ (nsteps & 1);
+    AK(cudaMemcpyAsync(ck, c->S[c->cur], bytes, cudaMemcpyDeviceToDevice, s), "checkpoint");
     for (int g = 0; g < nseg; ++g) {
-        AK(cudaMemcpyAsync(ck + (size_t)g * L, c->S[c->cur], bytes, cudaMemcpyDeviceToDevice, s), "checkpoint");
         const int len = std::min(K, nsteps - g * K);
         for (int j = 0; j < len; ++j) {
-            AK(fp32_step_into(c, c->S[c->cur], c->S[c->cur ^ 1], s), "adjoint forward");
-            c->cur ^= 1;
+            const float *in = j == 0 ? ck + (size_t)g * L : seg + (size_t)((j - 1) & 1) * L;
+            float *out = j + 1 < len ? seg + (size_t)(j & 1) * L
+                                     : (g + 1 < nseg ? ck + (size_t)(g + 1) * L : c->S[fin]);
+            AK(fp32_step_into(c, in, out, s), "adjoint forward");
         }
     }
+    c->cur = fin;
     c->steps += nsteps;
     c->has_prev = true;
     // reverse sweep
@@ -615,9 +622,10 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
     int lc = 0;
     for (int g = nseg - 1; g >= 0; --g) {
         const int len = std::min(K, nsteps - g * K);
-        AK(cudaMemcpyAsync(seg, ck + (size_t)g * L, bytes, cudaMemcpyDeviceToDevice, s), "segment start");
-        for (int j = 0; j + 1 < len; ++j)
-            AK(fp32_step_into(c, seg + (size_t)j * L, seg + (size_t)(j + 1) * L, s), "adjoint recompute");
+        // state j of the segment: the checkpoint for j = 0, recomputed into
+        // seg[j - 1] otherwise (a checkpoint every step means no replay)
+        auto state = [&](int j) -> float * { return j == 0 ? ck + (size_t)g * L : seg + (size_t)(j - 1) * L; };
+        for (int j = 0; j + 1 < len; ++j) AK(fp32_step_into(c, state(j), state(j + 1), s), "adjoint recompute");
         for (int j = len - 1; j >= 0; --j) {
             AdjointParams ap;
             ap.lam_next = lam + (size_t)lc * L;
@@ -632,7 +640,7 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
             }
             ap.lam_out = lam + (size_t)(lc ^ 1) * L;
             ap.beta_mu = bm;
-            ap.S = seg + (size_t)j * L;
+            ap.S = state(j);
             ap.coef = c->d_coef;
             ap.cls = c->d_cls;
             ap.Z = c->d_Z;

@@ -21,6 +21,8 @@ directions = n_zen x n_az, four Stokes components per direction):
 - ``channels``:   256 independent spectral channels with mixed lattice sizes and
                   direction counts (seeded).
 - ``adjoint``:    1024x256, n=32, medium seed 2, 1000 steps, loss on top I,Q,U.
+- ``paper_2d``:   the paper's 16x16 horizontal-lattice runs (n=8, central source,
+                  recycling or absorbing boundaries, 64 steps).
 """
 from __future__ import annotations
 
@@ -195,6 +197,23 @@ def channels(count: int = 256, seed: int = 3, steps: int = 500) -> List[Workload
                             bc=(BC_INFLOW, BC_VACUUM, BC_VACUUM, BC_VACUUM),
                             surv_mode=SURV_EXP, steps=steps, seed=seed))
     return out
+
+
+def paper_2d(bc: str = "recycle", scheme: str = "nearest", steps: int = 64) -> Workload:
+    """The paper's 2D runs (Sec. 3.2.1, Figs. 10-12): a horizontal 16x16
+    lattice, 2 zenith x 4 azimuth directions, Rayleigh scattering, Beer-Lambert
+    absorption, k_ext = 2.5 and k_scat = 0.5 with dt = 1/16 (tau = 2.5/16,
+    albedo 0.2), an unpolarized source J = 1 shared equally by the directions
+    on the four central sites (e = dt J / 8 per direction and step), recycling
+    ("recycle") or absorbing ("absorb") boundaries, 64 steps."""
+    N = 16
+    em = np.zeros((N, N))
+    em[7:9, 7:9] = 1.0 / 16 / 8
+    kind = BC_PERIODIC if bc == "recycle" else BC_VACUUM
+    return Workload(f"paper2d_{bc}_{scheme}", N, N, 2, 4, tau=_f32(np.full((N, N), 2.5 / 16)),
+                    albedo=_f32(np.full((N, N), 0.2)), emission=_f32(em), phase_index=None,
+                    phase_specs=[("rayleigh",)], inflow=None, bc=(kind,) * 4, surv_mode=SURV_LINEAR,
+                    steps=steps, seed=0, scheme=scheme, plane="xy")
 
 
 def random_medium(nx: int, nz: int, n_zen: int, n_az: int, seed: int, n_phase: int = 2,

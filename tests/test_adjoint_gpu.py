@@ -36,13 +36,16 @@ def _gpu_adjoint(torch, w, S0, nsteps, seed, K):
     return out
 
 
+@pytest.mark.parametrize("K", [1, 5, 12])
 @pytest.mark.parametrize("nx,nz,nzen,naz,bc,surv,absm,nph", [
     (13, 9, 2, 4, (2, 0, 0, 0), 1, 0, 2),
     (20, 7, 4, 4, (2, 0, 1, 1), 0, 0, 3),
     (17, 11, 4, 8, (1, 1, 2, 0), 1, 1, 2),
     (9, 6, 8, 8, (2, 2, 0, 0), 1, 0, 2),
 ])
-def test_adjoint_matches_oracle(torch_cuda, orc, nx, nz, nzen, naz, bc, surv, absm, nph):
+def test_adjoint_matches_oracle(torch_cuda, orc, nx, nz, nzen, naz, bc, surv, absm, nph, K):
+    """K = 1 keeps every state (no recomputation), K = 5 three segments of
+    5, 5 and 2 steps, K = 12 one segment."""
     w = W.random_medium(nx, nz, nzen, naz, seed=nx * nz, bc=bc, n_phase=nph, steps=12, surv_mode=surv)
     w.tau = np.minimum(w.tau, 0.9)
     w.abs_mode = absm
@@ -50,7 +53,7 @@ def test_adjoint_matches_oracle(torch_cuda, orc, nx, nz, nzen, naz, bc, surv, ab
     S0 = W.random_state(nz, nx, w.n, seed=4)
     seed = np.random.default_rng(5).standard_normal((nx, w.n, 4)).astype(np.float32).astype(np.float64)
     rt, ra, rZ, rS = P.adjoint(S0, w.steps, seed, want_S0=True)
-    gt, ga, gZ, gS, SN = _gpu_adjoint(torch_cuda, w, S0, w.steps, seed, K=5)
+    gt, ga, gZ, gS, SN = _gpu_adjoint(torch_cuda, w, S0, w.steps, seed, K=K)
     assert _rel(gt, rt) < TOL
     assert _rel(ga, ra) < TOL
     assert _rel(gZ, rZ) < TOL
