@@ -188,10 +188,18 @@ rtlb_status rtlb_radiance_out(rtlb_ctx *ctx, int32_t side, float *out, void *str
  * Device memory: ceil(nsteps/checkpoint_every) + max(checkpoint_every - 1, 2)
  * + 3 states (checkpoint_every = 1: nsteps + 3, and no step is recomputed;
  * one more for BILINEAR) plus the table-gradient accumulators.  n must be in
- * {8, 16, 32, 64}.  Synchronizes. */
+ * {8, 16, 32, 64}.  The workspace stays allocated after the call (see
+ * rtlb_release_workspace).  Synchronizes. */
 rtlb_status rtlb_adjoint(rtlb_ctx *ctx, int32_t nsteps, int32_t checkpoint_every, const float *dL_dout,
                          float *grad_tau, float *grad_albedo, double *grad_Z, float *grad_S0,
                          void *stream);
+
+/* rtlb_adjoint keeps its device workspace (the checkpoints, scratch and
+ * adjoint states, accumulators and staging listed above) in the context
+ * between calls and grows it only when a call needs more, so repeated calls
+ * of the same size allocate nothing.  This frees it (rtlb_destroy does too);
+ * the next rtlb_adjoint allocates again.  Synchronizes the device. */
+rtlb_status rtlb_release_workspace(rtlb_ctx *ctx);
 
 /* Total I over the lattice and directions, accumulated in float64 on the
  * device.  Synchronizes. */

@@ -29,7 +29,7 @@ EXPORTS = [
     "rtlb_stream_offsets", "rtlb_phase_rayleigh", "rtlb_phase_hg", "rtlb_phase_mix",
     "rtlb_residual_noalloc", "rtlb_adjoint", "rtlb_phase_conserve_intensity",
     "rtlb_batch_create", "rtlb_batch_configure", "rtlb_batch_step", "rtlb_batch_check",
-    "rtlb_batch_last_error", "rtlb_batch_destroy", "rtlb_stream_taps",
+    "rtlb_batch_last_error", "rtlb_batch_destroy", "rtlb_stream_taps", "rtlb_release_workspace",
 ]
 
 
@@ -89,6 +89,7 @@ def lib() -> C.CDLL:
     L.rtlb_phase_mix.argtypes = [C.POINTER(Directions), C.c_double, C.c_double, C.c_double, vp]
     L.rtlb_residual_noalloc.argtypes = [vp, vp, C.c_size_t, vp, vp]
     L.rtlb_adjoint.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
+    L.rtlb_release_workspace.argtypes = [vp]
     L.rtlb_batch_create.argtypes = [i32, C.POINTER(vp), C.POINTER(vp)]
     L.rtlb_batch_configure.argtypes = [vp, i32]
     L.rtlb_batch_step.argtypes = [vp, i32, vp]

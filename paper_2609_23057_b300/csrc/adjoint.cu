@@ -30,24 +30,29 @@ struct AdjCfg {
     static constexpr int SG = 256 / CG;
     static constexpr int SITES = SG * TS;
     static constexpr int KC = 16;
-    static constexpr size_t SMEM = 2 * (size_t)N4 * SITES * 4 + (size_t)KC * N4 * 4 + (size_t)SITES * 24;
+    // mu tile, table chunk, five per-site words and the per-site dot-product
+    // partials of each column group (summed in a fixed order, so the
+    // gradients are deterministic); S~ is read from global memory where it is
+    // used, which keeps two CTAs resident per SM
+    static constexpr size_t SMEM =
+        (size_t)N4 * SITES * 4 + (size_t)KC * N4 * 4 + (size_t)SITES * 20 + (size_t)2 * CG * SITES * 4;
 };
 
 template <int N4>
-__global__ void __launch_bounds__(256, 1) k_adj_step(AdjointParams p)
+__global__ void __launch_bounds__(256, 2) k_adj_step(AdjointParams p)
 {
     using Cf = AdjCfg<N4>;
     constexpr int TS = Cf::TS, SG = Cf::SG, SITES = Cf::SITES, KC = Cf::KC;
     extern __shared__ __align__(16) float smem[];
     float *Ms = smem;                          // [N4][SITES]  mu (k-major)
-    float *Ss = Ms + N4 * SITES;               // [N4][SITES]  S~
-    float *Bs = Ss + N4 * SITES;               // [KC][N4]     table chunk
+    float *Bs = Ms + N4 * SITES;               // [KC][N4]     table chunk
     float *s_ahi = Bs + KC * N4;
     float *s_alo = s_ahi + SITES;
     float *s_beta = s_alo + SITES;
-    float *s_ga = s_beta + SITES;
-    float *s_gb = s_ga + SITES;
-    int *s_cls = reinterpret_cast<int *>(s_gb + SITES);
+    float *s_e = s_beta + SITES;
+    int *s_cls = reinterpret_cast<int *>(s_e + SITES);
+    float *s_pa = reinterpret_cast<float *>(s_cls + SITES);   // [CG][TS][SG] partials of <mu, S~>
+    float *s_pb = s_pa + Cf::CG * SITES;                      // [CG][TS][SG] partials of <Y, S~>
     __shared__ unsigned s_mask;
 
     const int n = p.n;
@@ -69,37 +74,30 @@ __global__ void __launch_bounds__(256, 1) k_adj_step(AdjointParams p)
         s_ahi[s] = c.x;
         s_alo[s] = c.y;
         s_beta[s] = c.z;
+        s_e[s] = c.w;
         s_cls[s] = cl;
-        s_ga[s] = 0.f;
-        s_gb[s] = 0.f;
     }
     if (my_mask) atomicOr(&s_mask, my_mask);
 
-    // mu = T^T lambda (pull from the push target) and S~ = S^t + e
+    // mu = T^T lambda (pull from the push target)
     const float4 *L4 = reinterpret_cast<const float4 *>(p.lam_next);
     const float4 *S4 = reinterpret_cast<const float4 *>(p.S);
     const bool per_x = p.bc[RTLB_SIDE_LEFT] == RTLB_BC_PERIODIC, per_z = p.bc[RTLB_SIDE_TOP] == RTLB_BC_PERIODIC;
     for (int idx = tid; idx < n * SITES; idx += 256) {
         const int d = idx / SITES, s = idx - d * SITES;
         const int site = site0 + s;
-        float4 m = make_float4(0.f, 0.f, 0.f, 0.f), v = m;
+        float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
         if (site < nsites) {
             const int z = site / p.nx, x = site - z * p.nx;
             int xt = x + p.dir[d], zt = z + p.dir[n + d];
             if (per_x) xt = wrap_coord(xt, p.nx);
             if (per_z) zt = wrap_coord(zt, p.nz);
             if (xt >= 0 && xt < p.nx && zt >= 0 && zt < p.nz) m = L4[(size_t)d * nsites + (size_t)zt * p.nx + xt];
-            v = S4[(size_t)d * nsites + site];
-            v.x += p.coef[site].w;
         }
         Ms[(4 * d + 0) * SITES + s] = m.x;
         Ms[(4 * d + 1) * SITES + s] = m.y;
         Ms[(4 * d + 2) * SITES + s] = m.z;
         Ms[(4 * d + 3) * SITES + s] = m.w;
-        Ss[(4 * d + 0) * SITES + s] = v.x;
-        Ss[(4 * d + 1) * SITES + s] = v.y;
-        Ss[(4 * d + 2) * SITES + s] = v.z;
-        Ss[(4 * d + 3) * SITES + s] = v.w;
     }
     __syncthreads();
 
@@ -151,16 +149,23 @@ __global__ void __launch_bounds__(256, 1) k_adj_step(AdjointParams p)
 #pragma unroll
     for (int i = 0; i < TS; ++i) {
         const int s = sl + i, site = site0 + s;
-        if (site >= nsites) continue;
+        if (site >= nsites) {
+            s_pa[(cg * TS + i) * SG + sg] = 0.f;
+            s_pb[(cg * TS + i) * SG + sg] = 0.f;
+            continue;
+        }
         const float ah = s_ahi[s], al = s_alo[s], be = s_beta[s];
         float pa = 0.f, pb = 0.f;
 #pragma unroll
         for (int jd = 0; jd < 2; ++jd) {
             const int d = (c0 >> 2) + jd;
             float o[4], bm[4];
+            float4 sv4 = __ldg(S4 + (size_t)d * nsites + site);
+            sv4.x += s_e[s];
+            const float svk[4] = {sv4.x, sv4.y, sv4.z, sv4.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float m = Ms[(4 * d + k) * SITES + s], sv = Ss[(4 * d + k) * SITES + s];
+                const float m = Ms[(4 * d + k) * SITES + s], sv = svk[k];
                 const float y = acc[i][4 * jd + k];
                 o[k] = fmaf(ah, m, fmaf(al, m, be * y));
                 bm[k] = be * m;
@@ -170,15 +175,21 @@ __global__ void __launch_bounds__(256, 1) k_adj_step(AdjointParams p)
             Lo[(size_t)d * nsites + site] = make_float4(o[0], o[1], o[2], o[3]);
             Mo[(size_t)d * nsites + site] = make_float4(bm[0], bm[1], bm[2], bm[3]);
         }
-        atomicAdd(&s_ga[s], pa);
-        atomicAdd(&s_gb[s], pb);
+        s_pa[(cg * TS + i) * SG + sg] = pa;
+        s_pb[(cg * TS + i) * SG + sg] = pb;
     }
     __syncthreads();
     for (int s = tid; s < SITES; s += 256) {
         const int site = site0 + s;
         if (site < nsites) {
-            p.g_alpha[site] += (double)s_ga[s];
-            p.g_beta[site] += (double)s_gb[s];
+            const int i = s % TS, g = s / TS;
+            float a = 0.f, b = 0.f;
+            for (int c = 0; c < Cf::CG; ++c) {
+                a += s_pa[(c * TS + i) * SG + g];
+                b += s_pb[(c * TS + i) * SG + g];
+            }
+            p.g_alpha[site] += (double)a;
+            p.g_beta[site] += (double)b;
         }
     }
 }
@@ -189,7 +200,7 @@ __global__ void __launch_bounds__(256, 1) k_adj_step(AdjointParams p)
 // reduces a strided set of 32-site chunks in registers and adds its sum into
 // its own slot of `slots` (no atomics).
 template <int N4>
-__global__ void __launch_bounds__(256) k_adj_table(AdjointParams p, double *__restrict__ slots)
+__global__ void __launch_bounds__(256, 2) k_adj_table(AdjointParams p, double *__restrict__ slots)
 {
     constexpr int TT = N4 < 128 ? N4 : 128;    // tile edge
     constexpr int TPR = TT / 8;                // threads per tile row (8 outputs each)
@@ -212,15 +223,10 @@ __global__ void __launch_bounds__(256) k_adj_table(AdjointParams p, double *__re
         for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
     const float4 *M4 = reinterpret_cast<const float4 *>(p.beta_mu);
     const float4 *S4 = reinterpret_cast<const float4 *>(p.S);
-    __shared__ int s_any;
     for (int base = blockIdx.x * CH; base < nsites; base += gridDim.x * CH) {
-        // skip chunks without a site of this class (single-class layers)
-        __syncthreads();
-        if (tid == 0) s_any = 0;
-        __syncthreads();
-        if (tid < CH && base + tid < nsites && p.cls[base + tid] == cl) s_any = 1;
-        __syncthreads();
-        if (!s_any) continue;
+        // skip chunks without a site of this class (single-class layers); the
+        // vote is also the barrier before the tiles are overwritten
+        if (!__syncthreads_or(tid < CH && base + tid < nsites && p.cls[base + tid] == cl)) continue;
         for (int idx = tid; idx < CH * (TT / 4); idx += 256) {
             const int s = idx % CH, dd = idx / CH;      // dd: direction within the tile edge
             const int site = base + s;
@@ -334,12 +340,16 @@ int adjoint_table_slots() { return 148; }
 
 cudaError_t launch_adjoint_step(const AdjointParams &p, double *slots, cudaStream_t s)
 {
+    // the table gradient runs on the tensor cores where its accumulators fit
+    // in TMEM, on the CUDA cores otherwise
+    const bool tc = adjoint_table_tc_supported(p.n, p.n_phase);
+    const int ns = adjoint_table_slots();
     cudaError_t e;
     switch (4 * p.n) {
-    case 32: e = launch_adj<32>(p, s); if (e == cudaSuccess) e = launch_table<32>(p, slots, adjoint_table_slots(), s); break;
-    case 64: e = launch_adj<64>(p, s); if (e == cudaSuccess) e = launch_table<64>(p, slots, adjoint_table_slots(), s); break;
-    case 128: e = launch_adj<128>(p, s); if (e == cudaSuccess) e = launch_table<128>(p, slots, adjoint_table_slots(), s); break;
-    case 256: e = launch_adj<256>(p, s); if (e == cudaSuccess) e = launch_table<256>(p, slots, adjoint_table_slots(), s); break;
+    case 32: e = launch_adj<32>(p, s); if (e == cudaSuccess) e = tc ? launch_adjoint_table_tc(p, slots, ns, s) : launch_table<32>(p, slots, ns, s); break;
+    case 64: e = launch_adj<64>(p, s); if (e == cudaSuccess) e = tc ? launch_adjoint_table_tc(p, slots, ns, s) : launch_table<64>(p, slots, ns, s); break;
+    case 128: e = launch_adj<128>(p, s); if (e == cudaSuccess) e = tc ? launch_adjoint_table_tc(p, slots, ns, s) : launch_table<128>(p, slots, ns, s); break;
+    case 256: e = launch_adj<256>(p, s); if (e == cudaSuccess) e = launch_table<256>(p, slots, ns, s); break;
     default: e = cudaErrorInvalidValue;
     }
     return e;

@@ -17,6 +17,30 @@
 
 using namespace rtlb;
 
+namespace rtlb {
+
+cudaError_t DevBuf::ensure(size_t bytes)
+{
+    if (bytes <= cap) return cudaSuccess;
+    release();
+    const cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        return e;
+    }
+    cap = bytes;
+    return cudaSuccess;
+}
+
+void DevBuf::release()
+{
+    cudaFree(p);
+    p = nullptr;
+    cap = 0;
+}
+
+}  // namespace rtlb
+
 namespace {
 
 rtlb_status fail(rtlb_ctx *ctx, rtlb_status st, const char *fmt, ...)
@@ -131,8 +155,10 @@ void free_ctx_buffers(rtlb_ctx *c)
     cudaFree(c->d_rad);
     cudaFreeHost(c->h_out);
     cudaFreeHost(c->h_flags);
+    c->adj.release();
     tc_release(c);
 }
+
 
 rtlb_status require_boundary_pairs(rtlb_ctx *c)
 {
@@ -551,49 +577,67 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
     const int K = checkpoint_every, nseg = (nsteps + K - 1) / K, N4 = 4 * c->n;
     const int nslots = adjoint_table_slots();
     const size_t glen = (size_t)c->n_phase * N4 * N4;
-    float *ck = nullptr, *seg = nullptr, *lam = nullptr, *bm = nullptr, *dl = nullptr, *gtd = nullptr, *gad = nullptr;
-    float *gS = nullptr;
-    double *ga = nullptr, *gb = nullptr, *slots = nullptr, *G = nullptr;
-    int *tapT = nullptr;
-    auto release = [&]() {
-        cudaFree(ck); cudaFree(seg); cudaFree(lam); cudaFree(bm); cudaFree(dl); cudaFree(gtd); cudaFree(gad);
-        cudaFree(gS); cudaFree(ga); cudaFree(gb); cudaFree(slots); cudaFree(G); cudaFree(tapT);
+    // workspace: grown to this call's sizes (a call that needs no more than
+    // the last one allocates nothing); on an allocation failure the whole
+    // workspace is released and allocated once more at these sizes
+    AdjWork &w = c->adj;
+    const size_t dl_bytes = (size_t)c->nx * c->n * 4 * sizeof(float);
+    const bool host_dl = !is_device_ptr(dL_dout);
+    const bool stage_t = grad_tau && !is_device_ptr(grad_tau), stage_a = grad_albedo && !is_device_ptr(grad_albedo);
+    const bool stage_S = grad_S0 && !is_device_ptr(grad_S0);
+    const std::pair<DevBuf *, size_t> need[] = {
+        {&w.ck, (size_t)nseg * bytes},
+        {&w.seg, K > 1 ? (size_t)std::max(K - 1, 2) * bytes : 0},
+        {&w.lam, 2 * bytes},
+        {&w.bm, bytes},
+        {&w.ga, ns * sizeof(double)},
+        {&w.gb, ns * sizeof(double)},
+        {&w.slots, (size_t)nslots * glen * sizeof(double)},
+        {&w.G, glen * sizeof(double)},
+        {&w.tapT, bilinear(c) ? c->tap_o.size() * sizeof(int) : 0},
+        {&w.dl, host_dl ? dl_bytes : 0},
+        {&w.gtd, stage_t ? ns * sizeof(float) : 0},
+        {&w.gad, stage_a ? ns * sizeof(float) : 0},
+        {&w.gS, stage_S ? bytes : 0},
     };
+    auto grow = [&]() -> cudaError_t {
+        for (const auto &b : need) {
+            const cudaError_t e = b.first->ensure(b.second);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    if (grow() != cudaSuccess) {
+        cudaGetLastError();
+        w.release();
+        const cudaError_t e = grow();
+        if (e != cudaSuccess) {
+            w.release();
+            return cuda_fail(c, e, "adjoint workspace");
+        }
+    }
+    float *ck = w.ck.as<float>(), *seg = w.seg.as<float>(), *lam = w.lam.as<float>(), *bm = w.bm.as<float>();
+    float *gtd = w.gtd.as<float>(), *gad = w.gad.as<float>(), *gS = w.gS.as<float>();
+    double *ga = w.ga.as<double>(), *gb = w.gb.as<double>(), *slots = w.slots.as<double>(), *G = w.G.as<double>();
+    int *tapT = w.tapT.as<int>();
 #define AK(call, what)                                \
     do {                                              \
         cudaError_t e_ = (call);                      \
-        if (e_ != cudaSuccess) {                      \
-            release();                                \
-            return cuda_fail(c, e_, (what));          \
-        }                                             \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, (what)); \
     } while (0)
-    AK(cudaMalloc(&ck, (size_t)nseg * bytes), "adjoint checkpoints");
-    if (K > 1) AK(cudaMalloc(&seg, (size_t)std::max(K - 1, 2) * bytes), "adjoint segment states");
-    AK(cudaMalloc(&lam, 2 * bytes), "adjoint lambda");
-    AK(cudaMalloc(&bm, bytes), "adjoint beta mu");
-    AK(cudaMalloc(&ga, ns * sizeof(double)), "adjoint g_alpha");
-    AK(cudaMalloc(&gb, ns * sizeof(double)), "adjoint g_beta");
-    AK(cudaMalloc(&slots, (size_t)nslots * glen * sizeof(double)), "adjoint table slots");
-    AK(cudaMalloc(&G, glen * sizeof(double)), "adjoint table gradient");
     int bcT[4];
     for (int k = 0; k < 4; ++k) bcT[k] = c->bc[k] == RTLB_BC_PERIODIC ? RTLB_BC_PERIODIC : RTLB_BC_VACUUM;
     if (bilinear(c)) {
         st = ensure_post(c);
-        if (st != RTLB_OK) {
-            release();
-            return st;
-        }
+        if (st != RTLB_OK) return st;
         std::vector<int> neg(c->tap_o.size());
         for (size_t k = 0; k < neg.size(); ++k) neg[k] = -c->tap_o[k];
-        AK(cudaMalloc(&tapT, neg.size() * sizeof(int)), "adjoint taps");
         AK(cudaMemcpy(tapT, neg.data(), neg.size() * sizeof(int), cudaMemcpyHostToDevice), "adjoint taps");
     }
     const float *dl_dev = dL_dout;
-    const size_t dl_bytes = (size_t)c->nx * c->n * 4 * sizeof(float);
-    if (!is_device_ptr(dL_dout)) {
-        AK(cudaMalloc(&dl, dl_bytes), "adjoint seed staging");
-        AK(cudaMemcpyAsync(dl, dL_dout, dl_bytes, cudaMemcpyHostToDevice, s), "adjoint seed upload");
-        dl_dev = dl;
+    if (host_dl) {
+        AK(cudaMemcpyAsync(w.dl.p, dL_dout, dl_bytes, cudaMemcpyHostToDevice, s), "adjoint seed upload");
+        dl_dev = w.dl.as<float>();
     }
     // forward in float32, stepping from checkpoint to checkpoint: segment g
     // starts at ck[g] and ends in ck[g + 1] (the last one in the state buffer
@@ -658,14 +702,20 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
     }
     // outputs
     if (grad_tau || grad_albedo) {
-        const bool dev_t = grad_tau && is_device_ptr(grad_tau), dev_a = grad_albedo && is_device_ptr(grad_albedo);
-        float *ot = dev_t ? grad_tau : nullptr, *oa = dev_a ? grad_albedo : nullptr;
-        if (!ot) { AK(cudaMalloc(&gtd, ns * sizeof(float)), "grad staging"); ot = gtd; }
-        if (!oa) { AK(cudaMalloc(&gad, ns * sizeof(float)), "grad staging"); oa = gad; }
+        // a missing output is computed into staging that is not read back
+        float *ot = grad_tau && !stage_t ? grad_tau : gtd, *oa = grad_albedo && !stage_a ? grad_albedo : gad;
+        if (!ot || !oa) {
+            AK(w.gtd.ensure(ns * sizeof(float)), "grad staging");
+            AK(w.gad.ensure(ns * sizeof(float)), "grad staging");
+            gtd = w.gtd.as<float>();
+            gad = w.gad.as<float>();
+            if (!ot) ot = gtd;
+            if (!oa) oa = gad;
+        }
         AK(launch_adjoint_chain(ga, gb, c->d_tau, c->d_alb, (int)ns, c->opt.survival, c->opt.absorption, ot, oa, s),
            "adjoint chain rule");
-        if (grad_tau && !dev_t) AK(cudaMemcpyAsync(grad_tau, gtd, ns * sizeof(float), cudaMemcpyDeviceToHost, s), "grad_tau");
-        if (grad_albedo && !dev_a)
+        if (stage_t) AK(cudaMemcpyAsync(grad_tau, gtd, ns * sizeof(float), cudaMemcpyDeviceToHost, s), "grad_tau");
+        if (stage_a)
             AK(cudaMemcpyAsync(grad_albedo, gad, ns * sizeof(float), cudaMemcpyDeviceToHost, s), "grad_albedo");
     }
     if (grad_Z) {
@@ -676,14 +726,21 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
         if (is_device_ptr(grad_S0)) {
             AK(launch_dm_to_user(lam + (size_t)lc * L, grad_S0, (int)ns, c->n, s), "grad_S0");
         } else {
-            AK(cudaMalloc(&gS, bytes), "grad_S0 staging");
             AK(launch_dm_to_user(lam + (size_t)lc * L, gS, (int)ns, c->n, s), "grad_S0");
             AK(cudaMemcpyAsync(grad_S0, gS, bytes, cudaMemcpyDeviceToHost, s), "grad_S0 download");
         }
     }
     AK(cudaStreamSynchronize(s), "adjoint sync");
 #undef AK
-    release();
+    if (adjoint_table_tc_take_error() > 0) return fail(c, RTLB_E_TIMEOUT, "the table-gradient kernel gave up waiting");
+    return RTLB_OK;
+}
+
+rtlb_status rtlb_release_workspace(rtlb_ctx *c)
+{
+    if (!c) return RTLB_E_ARG;
+    CK(c, cudaDeviceSynchronize(), "release workspace");
+    c->adj.release();
     return RTLB_OK;
 }
 

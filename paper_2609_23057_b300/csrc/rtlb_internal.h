@@ -62,6 +62,10 @@ cudaError_t launch_adjoint_seed(float *lam, const float *dL_dout, const int *dir
 cudaError_t launch_adjoint_chain(const double *ga, const double *gb, const float *tau, const float *alb, int nsites,
                                  int surv_mode, int abs_mode, float *g_tau, float *g_alb, cudaStream_t s);
 cudaError_t launch_adjoint_fold(const double *slots, int nslots, size_t len, double *out, cudaStream_t s);
+// tensor-core table gradient (adj_table_tc.cu): 4n <= 128, n_phase * 4n <= 512
+bool adjoint_table_tc_supported(int n, int n_phase);
+cudaError_t launch_adjoint_table_tc(const AdjointParams &p, double *slots, int nslots, cudaStream_t s);
+int adjoint_table_tc_take_error();
 
 // ---- kernels (launchers return the launch error) ----
 cudaError_t launch_user_to_dm(const float *user, float *dm, int nsites, int n, cudaStream_t s);
@@ -83,6 +87,29 @@ cudaError_t launch_fill(float *p, size_t count, float v, cudaStream_t s);
 cudaError_t launch_stream_bilinear(const float *P, float *S, const int *taps_o, const float *taps_w,
                                    const float *inflow, int nx, int nz, int n, int bcbits, cudaStream_t s);
 
+}  // namespace rtlb
+
+namespace rtlb {
+// Grow-only device buffer: kept between calls, reallocated only when a call
+// needs more than it holds.
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes);
+    void release();
+    template <class T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+// rtlb_adjoint's device workspace (checkpoints, scratch states, adjoint
+// states, accumulators and staging), kept in the context between calls.
+struct AdjWork {
+    DevBuf ck, seg, lam, bm, ga, gb, slots, G, tapT, dl, gtd, gad, gS;
+    void release()
+    {
+        for (DevBuf *b : {&ck, &seg, &lam, &bm, &ga, &gb, &slots, &G, &tapT, &dl, &gtd, &gad, &gS}) b->release();
+    }
+};
 }  // namespace rtlb
 
 struct rtlb_ctx {
@@ -122,6 +149,7 @@ struct rtlb_ctx {
     float *d_stage = nullptr;     // user-layout staging for host transfers
     float *d_rad = nullptr;       // radiance_out staging for host transfers
     void *tc = nullptr;           // tensor-core path state (tc.cu)
+    rtlb::AdjWork adj;            // rtlb_adjoint workspace (grow-only)
 
     int64_t steps = 0;
     bool has_prev = false;

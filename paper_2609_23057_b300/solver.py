@@ -240,6 +240,11 @@ class Solver:
                                        _ptr(gZ), _ptr(gS), _stream(stream)))
         return gt, ga, gZ, gS
 
+    def release_workspace(self):
+        """Free the device workspace adjoint() keeps between calls (its
+        checkpoints and adjoint states); the next adjoint() allocates again."""
+        self._check(lib().rtlb_release_workspace(self._ctx))
+
     @property
     def steps_done(self) -> int:
         return int(lib().rtlb_steps_done(self._ctx))

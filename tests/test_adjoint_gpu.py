@@ -62,6 +62,53 @@ def test_adjoint_matches_oracle(torch_cuda, orc, nx, nz, nzen, naz, bc, surv, ab
     assert _rel(SN, P.run(S0, w.steps)) < 1e-5
 
 
+@pytest.mark.parametrize("nzen,naz", [(2, 4), (4, 4), (4, 8)])
+def test_adjoint_many_chunks_per_block(torch_cuda, orc, nzen, naz):
+    """A lattice of 30,560 sites (477.5 chunks of 64 sites, so several chunks
+    per block of the table-gradient sweep and a ragged last chunk), classes
+    mixed inside chunks, n = 8, 16 and 32 directions."""
+    w = W.random_medium(191, 160, nzen, naz, seed=7, bc=(2, 0, 1, 1), n_phase=3, steps=4, surv_mode=1)
+    w.tau = np.minimum(w.tau, 0.9)
+    w.abs_mode = 0
+    P = oracle_problem(orc, w)
+    S0 = W.random_state(w.nz, w.nx, w.n, seed=4)
+    seed = np.random.default_rng(5).standard_normal((w.nx, w.n, 4)).astype(np.float32).astype(np.float64)
+    rt, ra, rZ, rS = P.adjoint(S0, w.steps, seed, want_S0=True)
+    gt, ga, gZ, gS, _ = _gpu_adjoint(torch_cuda, w, S0, w.steps, seed, K=2)
+    assert _rel(gt, rt) < TOL
+    assert _rel(ga, ra) < TOL
+    assert _rel(gZ, rZ) < TOL
+    assert _rel(gS, rS) < TOL
+
+
+def test_adjoint_workspace_reuse(torch_cuda, orc):
+    """Calls on one context reuse (and grow) the workspace: the same call
+    repeated gives the same bits, a larger call after a smaller one and a
+    call after rtlb_release_workspace still match the oracle."""
+    from paper_2609_23057_b300.solver import solver_for
+    w = W.random_medium(17, 11, 4, 4, seed=3, bc=(2, 0, 1, 1), n_phase=2, steps=12, surv_mode=1)
+    w.tau = np.minimum(w.tau, 0.9)
+    P = oracle_problem(orc, w)
+    S0 = W.random_state(w.nz, w.nx, w.n, seed=4)
+    seed = np.random.default_rng(5).standard_normal((w.nx, w.n, 4)).astype(np.float32).astype(np.float64)
+    rt, ra, rZ, rS = P.adjoint(S0, w.steps, seed, want_S0=True)
+    s = solver_for(w, "fp32")
+    S0d = torch_cuda.from_numpy(np.asarray(S0, np.float32)).cuda()
+    seedd = torch_cuda.from_numpy(np.asarray(seed, np.float32)).cuda()
+    outs = []
+    for K, release in ((12, False), (12, False), (1, False), (5, True), (1, False)):
+        if release:
+            s.release_workspace()
+        s.set_state(S0d)
+        gt, ga, gZ, gS = s.adjoint(w.steps, seedd, checkpoint_every=K, want_S0=True)
+        gt, ga, gS = gt.cpu().numpy(), ga.cpu().numpy(), gS.cpu().numpy()
+        assert _rel(gt, rt) < TOL and _rel(ga, ra) < TOL and _rel(gZ, rZ) < TOL and _rel(gS, rS) < TOL
+        outs.append((gt, ga, gZ, gS))
+    s.close()
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+
+
 def test_adjoint_crop_fd_and_g(torch_cuda, orc):
     """16x16 crop of the 1024x256, n = 32 adjoint medium, 100 steps, loss =
     squared error of the top I, Q, U against a seeded target: GPU adjoint vs
