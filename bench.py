@@ -217,6 +217,10 @@ def _roofline(precision, n, sdu_per_launch, avg_launch_s, peaks, src):
             "traffic": None, "peak_source": f"hbm_gbs of {src} MEASURED_PEAKS"}
 
 
+# tensor-core kernel of each precision at n = 64
+KERNEL = {"bf16": "k_step_tc", "bf16x2": "k_step_tc_pair", "bf16x3": "k_step_tc", "fp8": "k_step_tc_fp8"}
+
+
 def accuracy(precisions, steps):
     """Top-of-domain radiance error of each precision form against the FP64
     oracle on the 256x256 crop [896,1152)^2 of the same medium, run for
@@ -247,13 +251,14 @@ def accuracy(precisions, steps):
 
 def adjoint_ratio(steps: int, headline: str):
     """Time rtlb_adjoint on the 1024x256, n = 32 workload against the forward
-    of the same number of steps in float32 and in the headline precision.
-    Every state is kept (checkpoint_every = 1: 134 MB per step, 134 GB for
-    1000 steps, which HBM holds), so no step is recomputed."""
+    of the same number of steps in float32 and in the headline precision, with
+    a checkpoint every 50 steps (each segment replayed once) and with every
+    state kept (checkpoint_every = 1: 134 MB per step, 134 GB for 1000 steps,
+    which HBM holds; nothing replayed)."""
     import torch
     from paper_2609_23057_b300.solver import solver_for
     w = W.adjoint(steps=steps)
-    out = {"workload": w.name, "steps": steps, "checkpoint_every": 1}
+    out = {"workload": w.name, "steps": steps}
     fwd = {}
     for prec in ("fp32", headline):
         if prec in fwd:
@@ -268,21 +273,27 @@ def adjoint_ratio(steps: int, headline: str):
         torch.cuda.synchronize()
         fwd[prec] = a.elapsed_time(b)
         s.close()
-    s = solver_for(w, "fp32")
     seed = torch.randn((w.nx, w.n, 4), device="cuda")
-    # warm-up: the same call, which also sizes the workspace the context keeps
-    # between adjoint calls (the timed call allocates nothing)
-    s.adjoint(steps, seed, checkpoint_every=1)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    s.adjoint(steps, seed, checkpoint_every=1)
-    torch.cuda.synchronize()
-    adj_ms = (time.perf_counter() - t0) * 1e3
-    s.close()
-    out.update({"adjoint_ms": adj_ms, "forward_ms": fwd,
-                "adjoint_over_forward": {p: adj_ms / v for p, v in fwd.items()},
-                "note": "the adjoint call includes its own float32 forward pass; every state is kept, none "
-                        "recomputed; the workspace is the one the previous (warm-up) call left in the context"})
+    for K in (50, 1):
+        s = solver_for(w, "fp32")
+        # warm-up: the same call, which also sizes the workspace the context
+        # keeps between adjoint calls (the timed call allocates nothing)
+        s.adjoint(steps, seed, checkpoint_every=K)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.adjoint(steps, seed, checkpoint_every=K)
+        torch.cuda.synchronize()
+        adj_ms = (time.perf_counter() - t0) * 1e3
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+        out[f"checkpoint_every_{K}"] = {"adjoint_ms": adj_ms,
+                                        "adjoint_over_forward": {p: adj_ms / v for p, v in fwd.items()}}
+    out.update({"forward_ms": fwd, "adjoint_over_forward": out["checkpoint_every_50"]["adjoint_over_forward"],
+                "note": "each adjoint call includes its own float32 forward pass; checkpoint_every = 50 (the "
+                        "differentiation workload's setting) replays each segment once, checkpoint_every = 1 "
+                        "keeps every state (134 GB) and replays none; the workspace is the one the warm-up "
+                        "call left in the context"})
     return out
 
 
@@ -370,7 +381,7 @@ def run_ours(args):
 
     # comparison form first (float32 on the CUDA cores), then the headline form
     compare = {}
-    others = [] if args.no_compare else [p for p in ("fp32", "bf16") if p != args.precision]
+    others = [] if args.no_compare else [p for p in ("fp32", "bf16", "fp8") if p != args.precision]
     for prec in others:
         sc = SV.solver_for(w, prec)
         sc.step(3)
@@ -380,6 +391,8 @@ def run_ours(args):
         compare[prec] = {"value": ws * sdu_per_step * len(per) / (tot * 1e-3), "unit": UNIT,
                          "ms_per_step": tot / len(per),
                          "roofline": _roofline(prec, n, sdu_per_step, statistics.mean(per) * 1e-3, peaks, src)}
+        if prec != "fp32":
+            compare[prec]["roofline"]["kernel"] = KERNEL[prec]
         del sc
         torch.cuda.empty_cache()
 
@@ -417,7 +430,7 @@ def run_ours(args):
 
     roof = _roofline(args.precision, n, sdu_per_step, statistics.mean(per_launch) * 1e-3, peaks, src)
     if args.precision != "fp32":
-        kern = "k_step_tc_pair" if (args.precision == "bf16x2" and n == 64) else "k_step_tc"
+        kern = KERNEL[args.precision] if n == 64 else ("k_step_tc_fp8" if args.precision == "fp8" else "k_step_tc")
         roof["kernel"] = kern
         roof["traffic"] = _measured_traffic(kern, sites)
         roof["traffic_note"] = "DRAM bytes per launch from profiles/traffic.json, scaled by sites"
@@ -426,14 +439,17 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x2": "bf16x2", "bf16x3": "bf16x3"}[args.precision],
+            "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x2": "bf16x2", "bf16x3": "bf16x3",
+                      "fp8": "e4m3"}[args.precision],
             "data": "synthetic",
             "config": {"workload": w.name, "nx": w.nx, "nz": w.nz, "n_dirs": n,
                        "precision": args.precision,
                        "arithmetic": {"fp32": "float32 FMA",
                                       "bf16": "bf16 operands, float32 accumulate, float32 state",
                                       "bf16x2": "bf16 state operand, bf16 hi+lo table (2 MMAs), float32 accumulate",
-                                      "bf16x3": "bf16 hi+lo operands (3 MMAs), float32 accumulate"}[args.precision],
+                                      "bf16x3": "bf16 hi+lo operands (3 MMAs), float32 accumulate",
+                                      "fp8": "e4m3 operands with UE8M0 scales per 32-element block "
+                                             "(block-scaled MMA), float32 accumulate, float32 state"}[args.precision],
                        "sites": sites, "phase_classes": 2,
                        "l2": "inputs larger than L2 (4.3 GB state per buffer)",
                        "parallelism": f"replicas{ws}" if ws > 1 else "single"},
@@ -453,7 +469,7 @@ def run_ours(args):
             line["adjoint"] = adj
             line["adjoint_over_forward"] = adj["adjoint_over_forward"]["fp32"]
         if ws == 1 and args.accuracy_steps > 0:
-            precs = [args.precision] + [p for p in ("bf16", "fp32") if p != args.precision]
+            precs = [args.precision] + [p for p in ("bf16", "fp8", "fp32") if p != args.precision]
             line["accuracy"] = accuracy(precs, args.accuracy_steps)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.steps)
@@ -469,7 +485,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x2", "bf16x3"], default="bf16x2",
+    ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x2", "bf16x3", "fp8"], default="bf16x2",
                     help="headline form; bf16x2 is the tensor-core form that meets 1e-3 on the crop")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the FP32 comparison form")

@@ -60,9 +60,24 @@ typedef enum { RTLB_BC_VACUUM = 0, RTLB_BC_PERIODIC = 1, RTLB_BC_INFLOW = 2 } rt
  *              (n <= 32: the operands must fit one CTA's shared memory).
  *  BF16X2   -- tcgen05, bf16 state operand and the phase table as bf16 hi+lo,
  *              two MMAs (n = 64 runs on CTA pairs, each holding half the table).
+ *  FP8      -- tcgen05 block-scaled MMA (kind::mxf8f6f4): e4m3 operands with
+ *              one UE8M0 (power-of-two) scale per 32-element block -- per site
+ *              and 8 directions for the state operand beta S~, per table row
+ *              and 32 columns for the table -- float32 accumulation.  The
+ *              scale of a block is the smallest 2^e with max|block| / 2^e <=
+ *              448; values round to nearest even and saturate at +-448.  The
+ *              table scales of every phase class stay in tensor memory, which
+ *              bounds the classes (n = 64: 12); rtlb_set_medium returns
+ *              RTLB_E_UNSUPPORTED beyond that.
  * Tensor-core forms need n in {8, 16, 32, 64}; rtlb_create returns
  * RTLB_E_UNSUPPORTED otherwise. */
-typedef enum { RTLB_PREC_FP32 = 0, RTLB_PREC_BF16 = 1, RTLB_PREC_BF16X3 = 2, RTLB_PREC_BF16X2 = 3 } rtlb_precision;
+typedef enum {
+    RTLB_PREC_FP32 = 0,
+    RTLB_PREC_BF16 = 1,
+    RTLB_PREC_BF16X3 = 2,
+    RTLB_PREC_BF16X2 = 3,
+    RTLB_PREC_FP8 = 4
+} rtlb_precision;
 
 /* Survival of unscattered light over one step: LINEAR = 1 - k_scat dt (Eq. 11
  * as printed), EXP = exp(-k_scat dt).  Absorption: BEER_LAMBERT =

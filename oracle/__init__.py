@@ -53,6 +53,11 @@ def lib():
                      _dp, C.c_int, C.c_int, _ip, _dp]
         L.orc_step.argtypes = step_args + [_dp, _dp]
         L.orc_run.argtypes = step_args + [_dp, C.c_int]
+        L.orc_step_fp8.argtypes = step_args[:12] + [C.c_int] + step_args[12:] + [_dp, _dp]
+        L.orc_e4m3.argtypes = [C.c_double]
+        L.orc_e4m3.restype = C.c_double
+        L.orc_fp8_exponent.argtypes = [C.c_double, C.c_int]
+        L.orc_fp8_exponent.restype = C.c_int
         L.orc_run_to_steady.argtypes = step_args + [_dp, C.c_double, C.c_int, C.POINTER(C.c_double)]
         L.orc_run_to_steady.restype = C.c_int
         L.orc_residual.argtypes = [C.c_size_t, _dp, _dp]
@@ -257,6 +262,15 @@ class Problem:
         lib().orc_step(*self._args(), S, out)
         return out
 
+    def step_fp8(self, S: np.ndarray) -> np.ndarray:
+        """One step in the FP8 block-scaled form of the contraction (see
+        orc_step_fp8); S must hold float32 values."""
+        S = np.ascontiguousarray(S, np.float64)
+        out = np.empty_like(S)
+        a = self._args()
+        lib().orc_step_fp8(*a[:12], int(self.Z.shape[0]), *a[12:], S, out)
+        return out
+
     def run(self, S: np.ndarray, nsteps: int) -> np.ndarray:
         S = np.array(S, np.float64, order="C", copy=True)
         lib().orc_run(*self._args(), S, int(nsteps))
@@ -292,6 +306,16 @@ class Problem:
         out = np.zeros((ln, self.n, 4))
         lib().orc_radiance_out(self.nx, self.nz, self.n, self.cx, self.cz, int(side), S, out)
         return out
+
+
+def e4m3(x: float) -> float:
+    """Nearest e4m3 value (ties to even, saturating at +-448)."""
+    return float(lib().orc_e4m3(float(x)))
+
+
+def fp8_exponent(amax: float, fp32_floor: bool = False) -> int:
+    """UE8M0 block exponent: smallest e with amax / 2^e <= 448, in [-127, 127]."""
+    return int(lib().orc_fp8_exponent(float(amax), int(bool(fp32_floor))))
 
 
 def residual(S_old, S_new) -> float:

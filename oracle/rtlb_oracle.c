@@ -350,6 +350,26 @@ static const double *upstream(int nx, int nz, int n, int x, int z, int d, int cx
     return NULL;
 }
 
+/* Streaming of the post-collision field P into S_out (weighted taps, see
+ * orc_step). */
+static void stream_all(int nx, int nz, int n, int ntap, const int *tx, const int *tz, const double *tw,
+                       const int *bc, const double *inflow, const double *P, double *S_out)
+{
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; ++z)
+        for (int x = 0; x < nx; ++x)
+            for (int d = 0; d < n; ++d) {
+                double *dst = S_out + (((size_t)z * nx + x) * n + d) * 4;
+                for (int s = 0; s < 4; ++s) dst[s] = 0.0;
+                for (int k = 0; k < ntap; ++k) {
+                    int j = d * ntap + k;
+                    const double *src = upstream(nx, nz, n, x, z, d, tx[j], tz[j], bc, inflow, P);
+                    if (src)
+                        for (int s = 0; s < 4; ++s) dst[s] += tw[j] * src[s];
+                }
+            }
+}
+
 /* One full step S_in -> S_out (emission, absorption, scattering, streaming).
  * Streaming of direction d is the weighted sum of ntap translations: tap k
  * moves content by (tx, tz)[d * ntap + k] cells with weight tw[d * ntap + k]
@@ -378,19 +398,7 @@ void orc_step(int nx, int nz, int n, int ntap, const int *tx, const int *tz, con
             }
         free(Se);
     }
-#pragma omp parallel for schedule(static)
-    for (int z = 0; z < nz; ++z)
-        for (int x = 0; x < nx; ++x)
-            for (int d = 0; d < n; ++d) {
-                double *dst = S_out + (((size_t)z * nx + x) * n + d) * 4;
-                for (int s = 0; s < 4; ++s) dst[s] = 0.0;
-                for (int k = 0; k < ntap; ++k) {
-                    int j = d * ntap + k;
-                    const double *src = upstream(nx, nz, n, x, z, d, tx[j], tz[j], bc, inflow, P);
-                    if (src)
-                        for (int s = 0; s < 4; ++s) dst[s] += tw[j] * src[s];
-                }
-            }
+    stream_all(nx, nz, n, ntap, tx, tz, tw, bc, inflow, P, S_out);
     free(P);
 }
 
@@ -408,6 +416,142 @@ void orc_run(int nx, int nz, int n, int ntap, const int *tx, const int *tz, cons
         memcpy(S, T, len * sizeof(double));
     }
     free(T);
+}
+
+/* ------------------------------------------------- FP8 block-scaled form */
+
+/* Nearest e4m3 value of x (OCP 8-bit floating point, E4M3: 4 exponent bits
+ * with bias 7, 3 mantissa bits, subnormals spaced 2^-9, largest finite value
+ * 448), ties to even; larger magnitudes saturate to 448. */
+double orc_e4m3(double x)
+{
+    double a = fabs(x);
+    if (a == 0.0) return x;
+    int E;
+    frexp(a, &E);                       /* a in [2^(E-1), 2^E) */
+    int b = E - 1;
+    if (b < -6) b = -6;                 /* below the normal range the spacing stays 2^-9 */
+    double q = ldexp(1.0, b - 3);       /* spacing of 3 mantissa bits in binade b */
+    double r = nearbyint(a / q) * q;    /* default rounding: ties to even */
+    if (r > 448.0) r = 448.0;
+    return copysign(r, x);
+}
+
+/* Power-of-two block scale 2^e (UE8M0): the smallest e with amax / 2^e <= 448,
+ * clamped to [-127, 127]; -127 for amax = 0 and, when fp32_floor is set, for
+ * amax below the float32 normal range. */
+int orc_fp8_exponent(double amax, int fp32_floor)
+{
+    if (!(amax > 0.0)) return -127;
+    if (fp32_floor && amax < ldexp(1.0, -126)) return -127;
+    int E;
+    double f = frexp(amax, &E);         /* amax = (2 f) 2^(E - 1), 2 f in [1, 2) */
+    int e = (E - 1) - 8 + (2.0 * f > 1.75 ? 1 : 0);
+    if (e < -127) e = -127;
+    if (e > 127) e = 127;
+    return e;
+}
+
+/* One step in the FP8 block-scaled precision form of the contraction (the
+ * CUDA library's FP8 precision), written out in float64 from that form's
+ * definition.  The paper fixes no low-precision arithmetic; the form is:
+ *   - state operand: S~ = S + e rounded to float32 (S holds float32 values),
+ *     beta rounded to float32, b = beta S~ rounded to float32; per site and
+ *     block of 8 directions (32 values) the scale 2^ea from the block's
+ *     largest |b| (float32 floor), each value e4m3(b 2^-ea) 2^ea;
+ *   - table: for each class whose forward blocks Z(i, i) are c_i I (within
+ *     1e-14 |c_i|), the float32 c_i is taken out and applied exactly, the
+ *     remainder c_i - float32(c_i) staying on the diagonal; the rest of the
+ *     table is quantized per row and block of 32 columns the same way (scale
+ *     from the block's largest |value|, no float32 floor);
+ *   - P = alpha S~ + beta c_i S~ + sum of the quantized products (exact here;
+ *     the tensor core accumulates them in float32), then streaming as in
+ *     orc_step.  n must be a multiple of 8. */
+void orc_step_fp8(int nx, int nz, int n, int ntap, const int *tx, const int *tz, const double *tw,
+                  const double *tau, const double *albedo, const double *emis, const int *cls,
+                  const double *Z, int n_phase, int surv_mode, int abs_mode, const int *bc,
+                  const double *inflow, const double *S_in, double *S_out)
+{
+    int K = 4 * n;
+    size_t nsite = (size_t)nx * nz;
+    double *Bq = (double *)malloc((size_t)n_phase * K * K * sizeof(double));
+    double *fw = (double *)calloc((size_t)n_phase * n, sizeof(double));
+    for (int c = 0; c < n_phase; ++c) {
+        const double *Zc = Z + (size_t)c * K * K;
+        double *B = Bq + (size_t)c * K * K;
+        memcpy(B, Zc, (size_t)K * K * sizeof(double));
+        int diag = 1;
+        for (int i = 0; i < n && diag; ++i) {
+            double ci = Zc[(size_t)(4 * i) * K + 4 * i];
+            for (int a = 0; a < 4 && diag; ++a)
+                for (int b = 0; b < 4; ++b) {
+                    double want = (a == b) ? ci : 0.0;
+                    if (fabs(Zc[(size_t)(4 * i + a) * K + 4 * i + b] - want) > 1e-14 * fabs(ci)) {
+                        diag = 0;
+                        break;
+                    }
+                }
+        }
+        if (diag)
+            for (int i = 0; i < n; ++i) {
+                double ci = Zc[(size_t)(4 * i) * K + 4 * i];
+                fw[(size_t)c * n + i] = (double)(float)ci;
+                for (int a = 0; a < 4; ++a) B[(size_t)(4 * i + a) * K + 4 * i + a] = ci - (double)(float)ci;
+            }
+        for (int row = 0; row < K; ++row)
+            for (int blk = 0; blk < K / 32; ++blk) {
+                double *v = B + (size_t)row * K + 32 * blk;
+                double amax = 0.0;
+                for (int k = 0; k < 32; ++k) amax = fmax(amax, fabs(v[k]));
+                int e = orc_fp8_exponent(amax, 0);
+                for (int k = 0; k < 32; ++k) v[k] = ldexp(orc_e4m3(ldexp(v[k], -e)), e);
+            }
+    }
+    double *P = (double *)malloc(nsite * K * sizeof(double));
+#pragma omp parallel
+    {
+        float *st = (float *)malloc((size_t)K * sizeof(float));
+        double *aq = (double *)malloc((size_t)K * sizeof(double));
+#pragma omp for schedule(static)
+        for (int z = 0; z < nz; ++z)
+            for (int x = 0; x < nx; ++x) {
+                size_t site = (size_t)z * nx + x;
+                int c = cls ? cls[site] : 0;
+                const double *S = S_in + site * K;
+                float e = (float)(emis ? emis[site] : 0.0);
+                for (int k = 0; k < K; ++k) st[k] = (float)S[k];
+                for (int d = 0; d < n; ++d) st[4 * d] = st[4 * d] + e;
+                double t = tau[site], w = albedo[site];
+                double kabs = (1.0 - w) * t, ksca = w * t;
+                double A = (abs_mode == ORC_ABS_TAYLOR) ? 1.0 - kabs : exp(-kabs);
+                double s = (surv_mode == ORC_SURV_EXP) ? exp(-ksca) : 1.0 - ksca;
+                double alpha = A * s;
+                float beta = (float)(A * (1.0 - s));
+                for (int blk = 0; blk < n / 8; ++blk) {
+                    float amax = 0.0f;
+                    for (int k = 32 * blk; k < 32 * blk + 32; ++k) amax = fmaxf(amax, fabsf(beta * st[k]));
+                    int ea = orc_fp8_exponent((double)amax, 1);
+                    float inv = (float)ldexp(1.0, -ea);
+                    for (int k = 32 * blk; k < 32 * blk + 32; ++k) {
+                        float b = beta * st[k];
+                        aq[k] = ldexp(orc_e4m3((double)(b * inv)), ea);
+                    }
+                }
+                const double *B = Bq + (size_t)c * K * K;
+                double *out = P + site * K;
+                for (int row = 0; row < K; ++row) {
+                    double acc = 0.0;
+                    for (int k = 0; k < K; ++k) acc += B[(size_t)row * K + k] * aq[k];
+                    out[row] = alpha * st[row] + (double)beta * fw[(size_t)c * n + row / 4] * st[row] + acc;
+                }
+            }
+        free(st);
+        free(aq);
+    }
+    stream_all(nx, nz, n, ntap, tx, tz, tw, bc, inflow, P, S_out);
+    free(P);
+    free(Bq);
+    free(fw);
 }
 
 /* Steady-state residual: max |S_new - S_old| / max |S_new| over all entries. */

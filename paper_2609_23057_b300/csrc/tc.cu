@@ -31,6 +31,7 @@
 // frees its TMEM and returns; the host reports RTLB_E_TIMEOUT.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -52,10 +53,12 @@ using namespace tccommon;
 
 struct TcState {
     int N4 = 0, KP = 0, C = 0, n_phase = 0;
-    int mode = 1;                    // 1 bf16, 2 bf16 + table lo, 3 hi+lo both
+    int mode = 1;                    // 1 bf16, 2 bf16 + table lo, 3 hi+lo both, 4 e4m3 block-scaled
     bool pair = false;               // CTA-pair kernel (table rows split over two CTAs)
     __nv_bfloat16 *d_Zhi = nullptr;  // [n_phase][N4][KP]
     __nv_bfloat16 *d_Zlo = nullptr;
+    uint8_t *d_Z8 = nullptr;         // FP8: [n_phase][N4][KP8] e4m3
+    uint8_t *d_sfb = nullptr;        // FP8: [n_phase][N4][N4 / 32] UE8M0 block scales of the table
     int *d_pure = nullptr;           // tile | class << 24, sorted by class (pairs: 2 per entry)
     int n_pure = 0;
     int *d_mixed = nullptr;          // tile indices
@@ -69,19 +72,6 @@ struct TcState {
     int sm_count = 0;
     int stages = 0;
     size_t smem = 0;
-};
-
-struct TcParams {
-    const float4 *coef;  // {alpha_hi, alpha_lo, beta, emission}
-    const int *dir;
-    const float *inflow;
-    float *S_new;
-    const int *tiles;  // tile | class << 24
-    const float *fwd;  // [n_phase][n] forward-block factors
-    int n_tiles;
-    int nx, nz, n;
-    int bcbits;
-    int *err;
 };
 
 // MODE 1: bf16 operands; 2: bf16 state operand, table as bf16 hi + lo (two
@@ -663,12 +653,40 @@ bool encode_z_map(CUtensorMap *m, const __nv_bfloat16 *Z, int N4, int KP, int n_
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// e4m3 table [n_phase][N4][KP8] bytes, boxes of 128 bytes (one SW128 row) x N4 rows
+bool encode_z8_map(CUtensorMap *m, const uint8_t *Z8, int N4, int KP8, int n_phase)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)KP8, (cuuint64_t)N4, (cuuint64_t)n_phase};
+    cuuint64_t strides[2] = {(cuuint64_t)KP8, (cuuint64_t)N4 * KP8};
+    cuuint32_t box[3] = {128, (cuuint32_t)N4, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(Z8), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// UE8M0 exponent of a table block whose largest |value| is amax (float64):
+// the smallest e with amax / 2^e <= 448, within [-127, 127]; -127 for zero.
+int table_block_exponent(double amax)
+{
+    if (!(amax > 0.0)) return -127;
+    int E2;
+    const double f = std::frexp(amax, &E2);   // amax = f 2^E2, f in [0.5, 1)
+    const int e = (E2 - 1) - 8 + (2.0 * f > 1.75 ? 1 : 0);
+    return std::max(-127, std::min(127, e));
+}
+
 TcState *state_of(rtlb_ctx *c) { return static_cast<TcState *>(c->tc); }
 
 void free_tables(TcState *t)
 {
     cudaFree(t->d_Zhi);
     cudaFree(t->d_Zlo);
+    cudaFree(t->d_Z8);
+    cudaFree(t->d_sfb);
+    t->d_Z8 = t->d_sfb = nullptr;
     cudaFree(t->d_fwd);
     cudaFree(t->d_pure);
     cudaFree(t->d_mixed);
@@ -696,6 +714,7 @@ size_t smem_bytes_pair(int N4, int stages)
 
 int mode_of(int precision)
 {
+    if (precision == RTLB_PREC_FP8) return 4;
     return precision == RTLB_PREC_BF16X3 ? 3 : (precision == RTLB_PREC_BF16X2 ? 2 : 1);
 }
 
@@ -708,7 +727,9 @@ int mode_of(int precision)
 int fit_stages(int N4, int mode, bool pair)
 {
     for (int st = RTLB_TC_MAX_STAGES & ~1; st >= 2; st -= 2)
-        if ((pair ? smem_bytes_pair(N4, st) : smem_bytes(N4, mode, st)) <= (size_t)kSmemLimit) return st;
+        if ((pair ? smem_bytes_pair(N4, st) : (mode == 4 ? tc_fp8_smem_bytes(N4, st) : smem_bytes(N4, mode, st))) <=
+            (size_t)kSmemLimit)
+            return st;
     return 0;
 }
 
@@ -727,7 +748,7 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
 {
     if (c->opt.precision == RTLB_PREC_FP32) return RTLB_OK;
     const int mode = mode_of(c->opt.precision);
-    const bool split = mode >= 2;
+    const bool split = mode == 2 || mode == 3;
     if (!tc_supported(c->n)) {
         c->err = "tensor-core forms need n in {8, 16, 32, 64}";
         return RTLB_E_UNSUPPORTED;
@@ -770,7 +791,14 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
     const int n = c->n;
     std::vector<float> fwd((size_t)n_phase * n, 0.0f);
     std::vector<double> work(tsz);
-    std::vector<__nv_bfloat16> hi((size_t)n_phase * psz, __float2bfloat16(0.0f)), lo(hi.size(), __float2bfloat16(0.0f));
+    const bool fp8 = mode == 4;
+    const int KP8 = ((N4 + 127) / 128) * 128, ksteps = N4 / 32;
+    std::vector<__nv_bfloat16> hi(fp8 ? 0 : (size_t)n_phase * psz, __float2bfloat16(0.0f)), lo(hi.size(), __float2bfloat16(0.0f));
+    std::vector<uint8_t> z8(fp8 ? (size_t)n_phase * N4 * KP8 : 0, 0), sfb(fp8 ? (size_t)n_phase * N4 * ksteps : 0, 0);
+    if (fp8 && tc_fp8_tmem_columns(N4, n_phase) > 512) {
+        c->err = "the FP8 form keeps every class's table scales in tensor memory: too many phase classes for this n";
+        return RTLB_E_UNSUPPORTED;
+    }
     for (int ph = 0; ph < n_phase; ++ph) {
         const double *Zp = tables + (size_t)ph * tsz;
         std::copy(Zp, Zp + tsz, work.begin());
@@ -795,6 +823,21 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
                 for (int a = 0; a < 4; ++a)
                     work[(size_t)(4 * i + a) * N4 + 4 * i + a] = ci - (double)(float)ci;
             }
+        if (mode == 4) {
+            // e4m3 with one UE8M0 scale per table row and 32-element block
+            for (int row = 0; row < N4; ++row)
+                for (int ks = 0; ks < ksteps; ++ks) {
+                    const double *blk = &work[(size_t)row * N4 + 32 * ks];
+                    double amax = 0.0;
+                    for (int k = 0; k < 32; ++k) amax = std::max(amax, std::fabs(blk[k]));
+                    const int e = table_block_exponent(amax);
+                    sfb[((size_t)ph * N4 + row) * ksteps + ks] = (uint8_t)(e + 127);
+                    for (int k = 0; k < 32; ++k)
+                        z8[(size_t)ph * N4 * KP8 + (size_t)row * KP8 + 32 * ks + k] =
+                            (uint8_t)__nv_cvt_double_to_fp8(std::ldexp(blk[k], -e), __NV_SATFINITE, __NV_E4M3);
+                }
+            continue;
+        }
         for (int row = 0; row < N4; ++row)
             for (int col = 0; col < N4; ++col) {
                 const double v = work[(size_t)row * N4 + col];
@@ -843,13 +886,17 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
     }
 
     free_tables(t);
-    cudaError_t e = cudaMalloc(&t->d_Zhi, hi.size() * sizeof(__nv_bfloat16));
+    cudaError_t e = fp8 ? cudaMalloc(&t->d_Z8, z8.size()) : cudaMalloc(&t->d_Zhi, hi.size() * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess && fp8) e = cudaMalloc(&t->d_sfb, sfb.size());
+    if (e == cudaSuccess && fp8) e = cudaMemcpy(t->d_Z8, z8.data(), z8.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && fp8) e = cudaMemcpy(t->d_sfb, sfb.data(), sfb.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&t->d_fwd, fwd.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(t->d_fwd, fwd.data(), fwd.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && split) e = cudaMalloc(&t->d_Zlo, lo.size() * sizeof(__nv_bfloat16));
     if (e == cudaSuccess && !pure.empty()) e = cudaMalloc(&t->d_pure, pure.size() * sizeof(int));
     if (e == cudaSuccess && !mixed.empty()) e = cudaMalloc(&t->d_mixed, mixed.size() * sizeof(int));
-    if (e == cudaSuccess) e = cudaMemcpy(t->d_Zhi, hi.data(), hi.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !fp8)
+        e = cudaMemcpy(t->d_Zhi, hi.data(), hi.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && split)
         e = cudaMemcpy(t->d_Zlo, lo.data(), lo.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !pure.empty())
@@ -862,8 +909,9 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
         return e == cudaErrorMemoryAllocation ? RTLB_E_OOM : RTLB_E_CUDA;
     }
     const int box_rows = pair ? N4 / 2 : N4;
-    if (!encode_z_map(&t->tmZhi, t->d_Zhi, N4, KP, n_phase, box_rows) ||
-        (split && !encode_z_map(&t->tmZlo, t->d_Zlo, N4, KP, n_phase, box_rows))) {
+    if (fp8 ? !encode_z8_map(&t->tmZhi, t->d_Z8, N4, KP8, n_phase)
+            : (!encode_z_map(&t->tmZhi, t->d_Zhi, N4, KP, n_phase, box_rows) ||
+               (split && !encode_z_map(&t->tmZlo, t->d_Zlo, N4, KP, n_phase, box_rows)))) {
         free_tables(t);
         c->err = "tensor map encoding for the phase tables failed";
         return RTLB_E_CUDA;
@@ -878,14 +926,14 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
     t->n_pure = pair ? (int)pure.size() / 2 : (int)pure.size();
     t->n_mixed = (int)mixed.size();
     t->stages = stages;
-    t->smem = pair ? smem_bytes_pair(N4, stages) : smem_bytes(N4, mode, stages);
+    t->smem = pair ? smem_bytes_pair(N4, stages) : (fp8 ? tc_fp8_smem_bytes(N4, stages) : smem_bytes(N4, mode, stages));
     return RTLB_OK;
 }
 
 rtlb_status tc_step(rtlb_ctx *c, const StepParams &p, cudaStream_t s)
 {
     TcState *t = state_of(c);
-    if (!t || !t->d_Zhi) {
+    if (!t || (!t->d_Zhi && !t->d_Z8)) {
         c->err = "tensor-core tables are not prepared";
         return RTLB_E_STATE;
     }
@@ -913,7 +961,10 @@ rtlb_status tc_step(rtlb_ctx *c, const StepParams &p, cudaStream_t s)
         tp.bcbits = pack_bc(p.bc);
         tp.err = t->d_err;
         cudaError_t e = cudaSuccess;
-        if (t->pair) {
+        if (t->mode == 4) {
+            e = launch_step_tc_fp8(t->tmS[which], t->tmZhi, tp, t->d_sfb, t->N4, t->stages, t->n_phase,
+                                   std::min(t->sm_count, t->n_pure), s);
+        } else if (t->pair) {
             const int grid = 2 * std::min(t->sm_count / 2, t->n_pure);
             e = cudaFuncSetAttribute(k_step_tc_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem);
             if (e == cudaSuccess)
@@ -973,7 +1024,7 @@ bool tc_encode_state_map(CUtensorMap *m, const float *S, size_t nsites, int n) {
 bool tc_table_maps(const rtlb_ctx *c, CUtensorMap *zhi, CUtensorMap *zlo, const float **fwd)
 {
     const TcState *t = static_cast<const TcState *>(c->tc);
-    if (!t || !t->d_Zhi || t->pair) return false;
+    if (!t || !t->d_Zhi || t->pair || t->mode == 4) return false;
     *zhi = t->tmZhi;
     *zlo = t->tmZlo;
     *fwd = t->d_fwd;

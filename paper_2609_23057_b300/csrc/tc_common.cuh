@@ -23,6 +23,20 @@ constexpr int kHalfSites = 64;                      // sites per TMA box row (25
 constexpr int kSmemLimit = 232448;                  // max dynamic smem per block
 
 
+// Arguments of the tensor-core step kernels.
+struct TcParams {
+    const float4 *coef;  // {alpha_hi, alpha_lo, beta, emission}
+    const int *dir;
+    const float *inflow;
+    float *S_new;
+    const int *tiles;  // tile | class << 24
+    const float *fwd;  // [n_phase][n] forward-block factors
+    int n_tiles;
+    int nx, nz, n;
+    int bcbits;
+    int *err;
+};
+
 enum ErrCode { kErrTimeoutProducer = 1, kErrTimeoutConverter = 2, kErrTimeoutMma = 4, kErrTimeoutEpilogue = 8 };
 
 
@@ -133,4 +147,12 @@ __device__ __forceinline__ bool convert_tile(const float4 cf, const float *fwd, 
 }
 
 }  // namespace tccommon
+
+// FP8 block-scaled form (tc_fp8.cu): TMEM columns it needs (D, A scales, the
+// B scales of every class; must be <= 512), shared memory for a stage count,
+// and the launch (grid CTAs over p.tiles, one class-sorted slice each).
+int tc_fp8_tmem_columns(int N4, int n_phase);
+size_t tc_fp8_smem_bytes(int N4, int stages);
+cudaError_t launch_step_tc_fp8(const CUtensorMap &tmS, const CUtensorMap &tmZ, const tccommon::TcParams &p,
+                               const uint8_t *sfb, int N4, int stages, int n_phase, int grid, cudaStream_t s);
 }  // namespace rtlb

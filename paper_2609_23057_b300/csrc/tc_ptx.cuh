@@ -166,6 +166,37 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float v[8])
                  : "memory");
 }
 
+// One 32-bit TMEM column per lane of the warp's quadrant.
+__device__ __forceinline__ void tmem_st1(uint32_t taddr, uint32_t v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(v) : "memory");
+}
+
+// D[tmem] (+)= (A . B^T) with e4m3 operands and one UE8M0 scale per row and
+// 32-element K block (block_scale, scale_vec::1X), f32 accumulate.  The scale
+// of A row m is read from lane m, column sfa + m / 32; that of B row n from
+// column sfb + n / 32, lane n % 32 of the lane quadrant of the D row being
+// computed (so B's scales are replicated in all four quadrants); the byte of
+// the 32-bit cell is chosen by the descriptor's scale-ID fields.
+__device__ __forceinline__ void mma_mxf8(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc, uint32_t sfa,
+                                         uint32_t sfb, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::mxf8f6f4.block_scale.scale_vec::1X [%0], %1, %2, %3, [%4], [%5], p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+        : "memory");
+}
+
+// Instruction descriptor of the block-scaled e4m3 MMA: A and B e4m3 (format
+// 0), both K-major, UE8M0 scales (bit 23), M x N, scale bytes sfa_id / sfb_id.
+__host__ __device__ constexpr uint32_t idesc_mxf8(int m, int n, int sfa_id, int sfb_id)
+{
+    return ((uint32_t)sfb_id << 4) | ((uint32_t)(n >> 3) << 17) | (1u << 23) | ((uint32_t)(m >> 4) << 24) |
+           ((uint32_t)sfa_id << 29);
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
 {
     uint32_t r[16];
