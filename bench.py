@@ -196,8 +196,8 @@ def _measured_traffic(kernel, sites):
             rec = json.load(f)[kernel]
     except (OSError, KeyError, ValueError):
         return None
-    src = b"".join(open(os.path.join(HERE, "paper_2609_23057_b300", "csrc", fn), "rb").read()
-                   for fn in ("tc.cu", "step_common.cuh", "tc_common.cuh", "tc_ptx.cuh"))
+    files = ("tc_fp8.cu" if kernel == "k_step_tc_fp8" else "tc.cu", "step_common.cuh", "tc_common.cuh", "tc_ptx.cuh")
+    src = b"".join(open(os.path.join(HERE, "paper_2609_23057_b300", "csrc", fn), "rb").read() for fn in files)
     if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"]:
         return None
     return (rec["dram_bytes_read"] + rec["dram_bytes_write"]) * sites / rec["captured_sites"]
