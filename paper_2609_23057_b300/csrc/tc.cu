@@ -189,6 +189,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int h = 0; h < kTileM / kHalfSites; ++h)
                         tma_load_2d(smem_u32(sStage + (size_t)s * kStageBytes + h * (kStageBytes / 2)), &tmS, fb,
                                     4 * (tile * kTileM + h * kHalfSites), j * kDirsPerStage);
+                    if (RTLB_TC_PREFETCH_SLOTS > 0) {
+                        // the state chunk RTLB_TC_PREFETCH_SLOTS slots ahead, into L2
+                        const int ahead = i * groups + j + RTLB_TC_PREFETCH_SLOTS;
+                        const int ia = ahead / groups, ja = ahead - ia * groups;
+                        if (ia < T) {
+                            const int ta = p.tiles[t_begin + ia] & 0xFFFFFF;
+                            for (int h = 0; h < kTileM / kHalfSites; ++h)
+                                tma_prefetch_2d(&tmS, 4 * (ta * kTileM + h * kHalfSites), ja * kDirsPerStage);
+                        }
+                    }
                 }
             }
             // drain: wait (bounded) for the loads this thread issued into each stage
@@ -458,6 +468,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     for (int h = 0; h < kTileM / kHalfSites; ++h)
                         tma_load_2d(smem_u32(sStage + (size_t)s * kStageBytes + h * (kStageBytes / 2)), &tmS, fb,
                                     4 * (tile * kTileM + h * kHalfSites), j * kDirsPerStage);
+                    if (RTLB_TC_PAIR_PREFETCH_SLOTS > 0) {
+                        // two staging slots per CTA hold ~32 KB in flight: the
+                        // chunk a few slots ahead goes to L2 meanwhile
+                        const int ahead = i * groups + j + RTLB_TC_PAIR_PREFETCH_SLOTS;
+                        const int ia = ahead / groups, ja = ahead - ia * groups;
+                        if (ia < T) {
+                            const int ta = my_tile(ia);
+                            for (int h = 0; h < kTileM / kHalfSites; ++h)
+                                tma_prefetch_2d(&tmS, 4 * (ta * kTileM + h * kHalfSites), ja * kDirsPerStage);
+                        }
+                    }
                 }
             }
             for (int gr = 0; gr < 2; ++gr)
