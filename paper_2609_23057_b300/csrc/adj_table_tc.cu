@@ -80,8 +80,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// Staging slot of one chunk: beta mu and S as [direction][site] rows of 64
-// float4 (1 KB per direction), then the chunk's emission e[64] and classes.
+// Staging slot of one chunk: beta mu (or mu, scaled here by beta) and S as
+// [direction][site] rows of 64 float4 (1 KB per direction), then the chunk's
+// emission e[64], beta[64] and classes.
 // Within each 128-byte group of eight sites the 16-byte entries are permuted
 // (entry i of group g sits at position i ^ g), so that both the coalesced
 // copies (one group of eight sites per eight threads) and the conversion
@@ -89,23 +90,27 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 constexpr uint32_t kRowBytes = kChunk * 16;
 constexpr uint32_t kStageS = (kTT / 8) * kRowBytes;            // S rows follow the 32 beta mu rows
 constexpr uint32_t kStageData = 2 * kStageS;
-constexpr uint32_t kStage = kStageData + kChunk * 4 + kChunk;   // + e[64] floats + cls[64] bytes
+constexpr uint32_t kStageE = kStageData;                         // e[64] floats
+constexpr uint32_t kStageBeta = kStageE + kChunk * 4;             // beta[64] floats
+constexpr uint32_t kStageCls = kStageBeta + kChunk * 4;           // cls[64] bytes
+constexpr uint32_t kStage = kStageCls + kChunk;
 constexpr uint32_t kStageAligned = (kStage + 127) / 128 * 128;
 
 __device__ __forceinline__ uint32_t stage_pos(int site) { return (uint32_t)((site & ~7) | ((site ^ (site >> 3)) & 7)) * 16u; }
 
 // Writes rows 4d .. 4d + 3 (hi and lo tiles) from the staged row of direction
-// d, sites 8 sg .. 8 sg + 7; `e` (or null) is added to I; sites of classes
-// other than `only` are zeroed when only >= 0.
-__device__ __forceinline__ void put_rows(const uint8_t *row, const float *e, const uint8_t *cl, int only, int d,
-                                         int sg, uint8_t *hi_tile, uint8_t *lo_tile)
+// d, sites 8 sg .. 8 sg + 7; `e` (or null) is added to I, `scale` (or null)
+// multiplies every component; sites of classes other than `only` are zeroed
+// when only >= 0.
+__device__ __forceinline__ void put_rows(const uint8_t *row, const float *e, const float *scale, const uint8_t *cl,
+                                         int only, int d, int sg, uint8_t *hi_tile, uint8_t *lo_tile)
 {
     float v[4][8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         float4 x = *reinterpret_cast<const float4 *>(row + stage_pos(8 * sg + i));
         if (e) x.x += e[8 * sg + i];
-        const float keep = (only < 0 || cl[8 * sg + i] == only) ? 1.f : 0.f;
+        const float keep = ((only < 0 || cl[8 * sg + i] == only) ? 1.f : 0.f) * (scale ? scale[8 * sg + i] : 1.f);
         v[0][i] = x.x * keep;
         v[1][i] = x.y * keep;
         v[2][i] = x.z * keep;
@@ -125,7 +130,7 @@ __device__ int g_table_tc_err;
 __global__ void __launch_bounds__(kTT, 1)
     k_adj_table_tc(const float4 *__restrict__ beta_mu, const float4 *__restrict__ S, const float4 *__restrict__ coef,
                    const uint8_t *__restrict__ cls, double *__restrict__ slots, int nsites, int n, int n_phase,
-                   uint32_t tcols)
+                   uint32_t tcols, int beta_scale)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -181,11 +186,13 @@ __global__ void __launch_bounds__(kTT, 1)
                 for (int i = 0; i < 8; ++i) {
                     const int site = site0 + i;
                     const bool in = site < nsites;
-                    cp_async4(base + kStageData + (8 * sg + i) * 4, ew + 4 * (size_t)(in ? site : 0), in ? 4u : 0u);
+                    cp_async4(base + kStageE + (8 * sg + i) * 4, ew + 4 * (size_t)(in ? site : 0), in ? 4u : 0u);
+                    if (beta_scale)
+                        cp_async4(base + kStageBeta + (8 * sg + i) * 4, ew - 1 + 4 * (size_t)(in ? site : 0), in ? 4u : 0u);
                 }
                 const int left = nsites - site0;   // class bytes present in this group (rest zero-filled)
                 const uint32_t nb = left <= 0 ? 0u : (left >= 8 ? 8u : (uint32_t)left);
-                cp_async8(base + kStageData + kChunk * 4 + 8 * sg, cls + (nb ? site0 : 0), nb);
+                cp_async8(base + kStageCls + 8 * sg, cls + (nb ? site0 : 0), nb);
             }
         }
         cp_async_commit();
@@ -206,8 +213,9 @@ __global__ void __launch_bounds__(kTT, 1)
         const int slot = it & 1;
         uint8_t *st = stage + slot * kStageAligned;
         const uint8_t *mine = st + d * kRowBytes;
-        const float *e = reinterpret_cast<const float *>(st + kStageData);
-        const uint8_t *cl = st + kStageData + kChunk * 4;
+        const float *e = reinterpret_cast<const float *>(st + kStageE);
+        const float *bt = beta_scale ? reinterpret_cast<const float *>(st + kStageBeta) : nullptr;
+        const uint8_t *cl = st + kStageCls;
         const int site0 = ch * kChunk;
         cp_async_wait1();                          // own copies of this chunk (the next chunk's may be pending)
         unsigned mask = 0u;
@@ -219,8 +227,8 @@ __global__ void __launch_bounds__(kTT, 1)
             if (!(mask & (1u << c))) continue;
             if (!(ok = ops_free())) break;
             if (loader) {
-                if (first) put_rows(mine + kStageS, e, cl, -1, d, sg, Bhi, Blo);          // S~ = S + e
-                put_rows(mine, nullptr, cl, single ? -1 : c, d, sg, Ahi, Alo);     // beta mu (this class)
+                if (first) put_rows(mine + kStageS, e, nullptr, cl, -1, d, sg, Bhi, Blo);   // S~ = S + e
+                put_rows(mine, nullptr, bt, cl, single ? -1 : c, d, sg, Ahi, Alo);        // beta mu (this class)
             }
             fence_proxy_async();
             tc_fence_before();
@@ -307,7 +315,7 @@ cudaError_t launch_adjoint_table_tc(const AdjointParams &p, double *slots, int n
     const int grid = std::min(nslots, (nsites + kChunk - 1) / kChunk);
     k_adj_table_tc<<<grid, kTT, smem, s>>>(reinterpret_cast<const float4 *>(p.beta_mu),
                                           reinterpret_cast<const float4 *>(p.S), p.coef, p.cls, slots, nsites, p.n,
-                                          p.n_phase, tcols);
+                                          p.n_phase, tcols, p.beta_scale);
     return cudaGetLastError();
 }
 

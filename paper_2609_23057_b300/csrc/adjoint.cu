@@ -38,7 +38,13 @@ struct AdjCfg {
         (size_t)N4 * SITES * 4 + (size_t)KC * N4 * 4 + (size_t)SITES * 20 + (size_t)2 * CG * SITES * 4;
 };
 
-template <int N4>
+// NU = false: lambda form (mu = T^T lambda^{t+1} pulled here, lambda^t stored
+// in place, beta mu written for the table gradient); one block per SITES
+// consecutive sites.  NU = true (4n = 128, SITES = 128): transposed-stream
+// form for the tiles of p.tiles -- the input is nu^t = mu itself, lambda^t is
+// pushed along the negated offsets (or stored in place when !p.push), and the
+// table gradient reads nu^t directly.
+template <int N4, bool NU>
 __global__ void __launch_bounds__(256, 2) k_adj_step(AdjointParams p)
 {
     using Cf = AdjCfg<N4>;
@@ -57,7 +63,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_step(AdjointParams p)
 
     const int n = p.n;
     const int nsites = p.nx * p.nz;
-    const int site0 = blockIdx.x * SITES;
+    const int site0 = NU ? (p.tiles[blockIdx.x] & 0xFFFFFF) * SITES : blockIdx.x * SITES;
     const int tid = threadIdx.x;
     if (tid == 0) s_mask = 0u;
     __syncthreads();
@@ -88,11 +94,15 @@ __global__ void __launch_bounds__(256, 2) k_adj_step(AdjointParams p)
         const int site = site0 + s;
         float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
         if (site < nsites) {
-            const int z = site / p.nx, x = site - z * p.nx;
-            int xt = x + p.dir[d], zt = z + p.dir[n + d];
-            if (per_x) xt = wrap_coord(xt, p.nx);
-            if (per_z) zt = wrap_coord(zt, p.nz);
-            if (xt >= 0 && xt < p.nx && zt >= 0 && zt < p.nz) m = L4[(size_t)d * nsites + (size_t)zt * p.nx + xt];
+            if (NU) {
+                m = L4[(size_t)d * nsites + site];
+            } else {
+                const int z = site / p.nx, x = site - z * p.nx;
+                int xt = x + p.dir[d], zt = z + p.dir[n + d];
+                if (per_x) xt = wrap_coord(xt, p.nx);
+                if (per_z) zt = wrap_coord(zt, p.nz);
+                if (xt >= 0 && xt < p.nx && zt >= 0 && zt < p.nz) m = L4[(size_t)d * nsites + (size_t)zt * p.nx + xt];
+            }
         }
         Ms[(4 * d + 0) * SITES + s] = m.x;
         Ms[(4 * d + 1) * SITES + s] = m.y;
@@ -172,8 +182,15 @@ __global__ void __launch_bounds__(256, 2) k_adj_step(AdjointParams p)
                 pa = fmaf(m, sv, pa);
                 pb = fmaf(y, sv, pb);
             }
-            Lo[(size_t)d * nsites + site] = make_float4(o[0], o[1], o[2], o[3]);
-            Mo[(size_t)d * nsites + site] = make_float4(bm[0], bm[1], bm[2], bm[3]);
+            const float4 lv = make_float4(o[0], o[1], o[2], o[3]);
+            if (!NU) {
+                Lo[(size_t)d * nsites + site] = lv;
+                Mo[(size_t)d * nsites + site] = make_float4(bm[0], bm[1], bm[2], bm[3]);
+            } else if (p.push) {
+                push_store(p.dirT, nullptr, p.bcbitsT, p.lam_out, p.nx, p.nz, n, site, d, lv);
+            } else {
+                Lo[(size_t)d * nsites + site] = lv;
+            }
         }
         s_pa[(cg * TS + i) * SG + sg] = pa;
         s_pb[(cg * TS + i) * SG + sg] = pb;
@@ -233,6 +250,13 @@ __global__ void __launch_bounds__(256, 2) k_adj_table(AdjointParams p, double *_
             float4 m = make_float4(0.f, 0.f, 0.f, 0.f), v = m;
             if (site < nsites && p.cls[site] == cl) {
                 m = M4[(size_t)(r0 / 4 + dd) * nsites + site];
+                if (p.beta_scale) {
+                    const float be = p.coef[site].z;
+                    m.x *= be;
+                    m.y *= be;
+                    m.z *= be;
+                    m.w *= be;
+                }
                 v = S4[(size_t)(k0 / 4 + dd) * nsites + site];
                 if ((k0 / 4 + dd) < n) v.x += p.coef[site].w;
             }
@@ -294,8 +318,9 @@ __global__ void k_adj_chain(const double *__restrict__ ga, const double *__restr
         const double dAt = dA * (1.0 - w), dAw = -dA * t, dst = ds * w, dsw = ds * t;
         const double da_t = dAt * s + A * dst, da_w = dAw * s + A * dsw;
         const double db_t = dAt * (1.0 - s) - A * dst, db_w = dAw * (1.0 - s) - A * dsw;
-        g_tau[j] = (float)(ga[j] * da_t + gb[j] * db_t);
-        g_alb[j] = (float)(ga[j] * da_w + gb[j] * db_w);
+        const double a = ga[j] + ga[nsites + j], b = gb[j] + gb[nsites + j];   // the two halves, in order
+        g_tau[j] = (float)(a * da_t + b * db_t);
+        g_alb[j] = (float)(a * da_w + b * db_w);
     }
 }
 
@@ -308,19 +333,43 @@ __global__ void k_adj_fold_slots(const double *__restrict__ slots, int nslots, s
     }
 }
 
-template <int N4>
-cudaError_t launch_adj(const AdjointParams &p, cudaStream_t s)
+template <int N4, bool NU>
+cudaError_t launch_adj(const AdjointParams &p, int blocks, cudaStream_t s)
 {
     using Cf = AdjCfg<N4>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_adj_step<N4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cf::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(k_adj_step<N4, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cf::SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const int nsites = p.nx * p.nz;
-    k_adj_step<N4><<<(nsites + Cf::SITES - 1) / Cf::SITES, 256, Cf::SMEM, s>>>(p);
+    k_adj_step<N4, NU><<<blocks, 256, Cf::SMEM, s>>>(p);
     return cudaGetLastError();
+}
+
+template <int N4>
+cudaError_t launch_adj(const AdjointParams &p, cudaStream_t s)
+{
+    return launch_adj<N4, false>(p, (p.nx * p.nz + AdjCfg<N4>::SITES - 1) / AdjCfg<N4>::SITES, s);
+}
+
+// nu^{N-1} = T^T lambda^N: the loss gradient on the top row's outgoing
+// directions, pushed along the negated offsets (the rest of nu is zero).
+__global__ void k_adj_seed_nu(float *__restrict__ nu, const float4 *__restrict__ dL_dout, const int *__restrict__ dir,
+                              int nx, int nz, int n, int bcbits)
+{
+    const size_t nsites = (size_t)nx * nz;
+    const bool per_x = bc_of(bcbits, RTLB_SIDE_LEFT) == RTLB_BC_PERIODIC;
+    const bool per_z = bc_of(bcbits, RTLB_SIDE_TOP) == RTLB_BC_PERIODIC;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nx * n; j += gridDim.x * blockDim.x) {
+        const int x = j / n, d = j % n;
+        if (dir[n + d] != 1) continue;
+        int xt = x - dir[d], zt = nz - 1 - dir[n + d];
+        if (per_x) xt = wrap_coord(xt, nx);
+        if (per_z) zt = wrap_coord(zt, nz);
+        if (xt >= 0 && xt < nx && zt >= 0 && zt < nz)
+            reinterpret_cast<float4 *>(nu)[(size_t)d * nsites + (size_t)zt * nx + xt] = dL_dout[j];
+    }
 }
 
 template <int N4>
@@ -353,6 +402,33 @@ cudaError_t launch_adjoint_step(const AdjointParams &p, double *slots, cudaStrea
     default: e = cudaErrorInvalidValue;
     }
     return e;
+}
+
+cudaError_t launch_adjoint_step_nu_mixed(const AdjointParams &p, int n_tiles, cudaStream_t s)
+{
+    if (p.n != 32) return cudaErrorInvalidValue;
+    return n_tiles > 0 ? launch_adj<128, true>(p, n_tiles, s) : cudaSuccess;
+}
+
+cudaError_t launch_adjoint_table(const AdjointParams &p, double *slots, cudaStream_t s)
+{
+    const int ns = adjoint_table_slots();
+    if (adjoint_table_tc_supported(p.n, p.n_phase)) return launch_adjoint_table_tc(p, slots, ns, s);
+    switch (4 * p.n) {
+    case 32: return launch_table<32>(p, slots, ns, s);
+    case 64: return launch_table<64>(p, slots, ns, s);
+    case 128: return launch_table<128>(p, slots, ns, s);
+    case 256: return launch_table<256>(p, slots, ns, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_adjoint_seed_nu(float *nu, const float *dL_dout, const int *dir, int nx, int nz, int n, int bcbits,
+                                   cudaStream_t s)
+{
+    k_adj_seed_nu<<<(nx * n + 255) / 256, 256, 0, s>>>(nu, reinterpret_cast<const float4 *>(dL_dout), dir, nx, nz, n,
+                                                       bcbits);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_seed(float *lam, const float *dL_dout, const int *dir, int nx, int nz, int n, cudaStream_t s)

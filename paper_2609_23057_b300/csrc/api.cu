@@ -156,6 +156,7 @@ void free_ctx_buffers(rtlb_ctx *c)
     cudaFreeHost(c->h_out);
     cudaFreeHost(c->h_flags);
     c->adj.release();
+    c->adj_tc.release();
     tc_release(c);
 }
 
@@ -418,6 +419,7 @@ rtlb_status rtlb_set_medium(rtlb_ctx *c, const float *tau, const float *albedo, 
     c->d_alb = alb_keep;
     c->n_phase = n_phase;
     c->medium_set = true;
+    ++c->medium_gen;
     return RTLB_OK;
 }
 
@@ -563,6 +565,65 @@ rtlb_status rtlb_run_to_steady(rtlb_ctx *c, double tol, int32_t max_steps, int32
     return RTLB_OK;
 }
 
+// Tensor-core reverse-step state for the current medium (4n = 128): Z^T as
+// bf16 hi + lo from the float32 tables (B[c][k] = Z[k][c], K-major), the
+// single-class 128-site tiles sorted by class and the mixed ones, and the
+// negated streaming offsets.
+static rtlb_status prepare_adj_tc(rtlb_ctx *c)
+{
+    AdjTcState &a = c->adj_tc;
+    if (a.gen == c->medium_gen) return RTLB_OK;
+    a.release();
+    const int n = c->n, N4 = 4 * n, np = c->n_phase;
+    const size_t ns = c->nsites(), tsz = (size_t)N4 * N4;
+    std::vector<float> Z((size_t)np * tsz);
+    CK(c, cudaMemcpy(Z.data(), c->d_Z, Z.size() * sizeof(float), cudaMemcpyDeviceToHost), "adjoint tables");
+    std::vector<__nv_bfloat16> hi(Z.size()), lo(Z.size());
+    for (int ph = 0; ph < np; ++ph)
+        for (int col = 0; col < N4; ++col)
+            for (int k = 0; k < N4; ++k) {
+                const float v = Z[(size_t)ph * tsz + (size_t)k * N4 + col];
+                const __nv_bfloat16 h = __float2bfloat16(v);
+                hi[(size_t)ph * tsz + (size_t)col * N4 + k] = h;
+                lo[(size_t)ph * tsz + (size_t)col * N4 + k] = __float2bfloat16(v - __bfloat162float(h));
+            }
+    std::vector<uint8_t> cls(ns);
+    CK(c, cudaMemcpy(cls.data(), c->d_cls, ns, cudaMemcpyDeviceToHost), "adjoint classes");
+    const int ntiles = (int)((ns + 127) / 128);
+    std::vector<int> pure, mixed;
+    for (int t = 0; t < ntiles; ++t) {
+        const size_t b = (size_t)t * 128, e = std::min(ns, b + 128);
+        bool same = true;
+        for (size_t k = b + 1; k < e && same; ++k) same = cls[k] == cls[b];
+        if (same) pure.push_back(t | ((int)cls[b] << 24));
+        else mixed.push_back(t);
+    }
+    std::stable_sort(pure.begin(), pure.end(), [](int x, int y) { return (x >> 24) < (y >> 24); });
+    std::vector<int> dirT(2 * n);
+    for (int d = 0; d < n; ++d) {
+        dirT[d] = -c->cx[d];
+        dirT[n + d] = -c->cz[d];
+    }
+    CK(c, a.zhi.ensure(hi.size() * 2), "adjoint tables");
+    CK(c, a.zlo.ensure(lo.size() * 2), "adjoint tables");
+    CK(c, a.pure.ensure(std::max<size_t>(pure.size(), 1) * sizeof(int)), "adjoint tiles");
+    CK(c, a.mixed.ensure(std::max<size_t>(mixed.size(), 1) * sizeof(int)), "adjoint tiles");
+    CK(c, a.dirT.ensure(dirT.size() * sizeof(int)), "adjoint offsets");
+    CK(c, cudaMemcpy(a.zhi.p, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice), "adjoint tables");
+    CK(c, cudaMemcpy(a.zlo.p, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice), "adjoint tables");
+    if (!pure.empty()) CK(c, cudaMemcpy(a.pure.p, pure.data(), pure.size() * sizeof(int), cudaMemcpyHostToDevice), "adjoint tiles");
+    if (!mixed.empty())
+        CK(c, cudaMemcpy(a.mixed.p, mixed.data(), mixed.size() * sizeof(int), cudaMemcpyHostToDevice), "adjoint tiles");
+    CK(c, cudaMemcpy(a.dirT.p, dirT.data(), dirT.size() * sizeof(int), cudaMemcpyHostToDevice), "adjoint offsets");
+    if (!tc_encode_table_map(&a.tmZhi, a.zhi.as<__nv_bfloat16>(), N4, N4, np, N4) ||
+        !tc_encode_table_map(&a.tmZlo, a.zlo.as<__nv_bfloat16>(), N4, N4, np, N4))
+        return fail(c, RTLB_E_CUDA, "tensor map encoding for the adjoint tables failed");
+    a.n_pure = (int)pure.size();
+    a.n_mixed = (int)mixed.size();
+    a.gen = c->medium_gen;
+    return RTLB_OK;
+}
+
 rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, const float *dL_dout,
                          float *grad_tau, float *grad_albedo, double *grad_Z, float *grad_S0, void *stream)
 {
@@ -590,8 +651,8 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
         {&w.seg, K > 1 ? (size_t)std::max(K - 1, 2) * bytes : 0},
         {&w.lam, 2 * bytes},
         {&w.bm, bytes},
-        {&w.ga, ns * sizeof(double)},
-        {&w.gb, ns * sizeof(double)},
+        {&w.ga, 2 * ns * sizeof(double)},
+        {&w.gb, 2 * ns * sizeof(double)},
         {&w.slots, (size_t)nslots * glen * sizeof(double)},
         {&w.G, glen * sizeof(double)},
         {&w.tapT, bilinear(c) ? c->tap_o.size() * sizeof(int) : 0},
@@ -627,6 +688,13 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
     } while (0)
     int bcT[4];
     for (int k = 0; k < 4; ++k) bcT[k] = c->bc[k] == RTLB_BC_PERIODIC ? RTLB_BC_PERIODIC : RTLB_BC_VACUUM;
+    // 4n = 128 with nearest-neighbour streaming: the reverse step runs on the
+    // tensor cores in the transposed-stream form
+    const bool nu_form = c->n == 32 && !bilinear(c) && adjoint_tc_stages() > 0;
+    if (nu_form) {
+        st = prepare_adj_tc(c);
+        if (st != RTLB_OK) return st;
+    }
     if (bilinear(c)) {
         st = ensure_post(c);
         if (st != RTLB_OK) return st;
@@ -659,11 +727,74 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
     c->has_prev = true;
     // reverse sweep
     AK(cudaMemsetAsync(lam, 0, 2 * bytes, s), "lambda init");
-    AK(cudaMemsetAsync(ga, 0, ns * sizeof(double), s), "g_alpha init");
-    AK(cudaMemsetAsync(gb, 0, ns * sizeof(double), s), "g_beta init");
+    AK(cudaMemsetAsync(ga, 0, 2 * ns * sizeof(double), s), "g_alpha init");
+    AK(cudaMemsetAsync(gb, 0, 2 * ns * sizeof(double), s), "g_beta init");
     AK(cudaMemsetAsync(slots, 0, (size_t)nslots * glen * sizeof(double), s), "slots init");
-    AK(launch_adjoint_seed(lam, dl_dev, c->d_dir, c->nx, c->nz, c->n, s), "adjoint seed");
     int lc = 0;
+    if (nu_form) {
+        // transposed-stream form: lam[lc] holds nu^t = T^T lambda^{t+1}; each
+        // reverse step writes nu^{t-1} (lambda^0 at t = 0) into lam[lc ^ 1]
+        AdjTcState &a = c->adj_tc;
+        CUtensorMap tmNu[2];
+        for (int k = 0; k < 2; ++k)
+            if (!tc_encode_state_map(&tmNu[k], lam + (size_t)k * L, ns, c->n))
+                return fail(c, RTLB_E_CUDA, "tensor map encoding for the adjoint state failed");
+        const int bcbitsT = pack_bc(bcT);
+        int sm_count = 148;
+        cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, c->dev);
+        AK(launch_adjoint_seed_nu(lam, dl_dev, c->d_dir, c->nx, c->nz, c->n, bcbitsT, s), "adjoint seed");
+        for (int g = nseg - 1; g >= 0; --g) {
+            const int len = std::min(K, nsteps - g * K);
+            auto state = [&](int j) -> float * { return j == 0 ? ck + (size_t)g * L : seg + (size_t)(j - 1) * L; };
+            for (int j = 0; j + 1 < len; ++j) AK(fp32_step_into(c, state(j), state(j + 1), s), "adjoint recompute");
+            for (int j = len - 1; j >= 0; --j) {
+                const bool push = g * K + j > 0;
+                if (a.n_pure > 0) {
+                    AdjTcLaunch tl;
+                    tl.S = state(j);
+                    tl.coef = c->d_coef;
+                    tl.dirT = a.dirT.as<int>();
+                    tl.bcbitsT = bcbitsT;
+                    tl.nu_out = lam + (size_t)(lc ^ 1) * L;
+                    tl.g_alpha = ga;
+                    tl.g_beta = gb;
+                    tl.tiles = a.pure.as<int>();
+                    tl.n_tiles = a.n_pure;
+                    tl.nx = c->nx;
+                    tl.nz = c->nz;
+                    tl.n = c->n;
+                    tl.push = push ? 1 : 0;
+                    tl.sm_count = sm_count;
+                    AK(launch_adjoint_step_tc(tmNu[lc], a.tmZhi, a.tmZlo, tl, s), "adjoint step (tensor cores)");
+                }
+                AdjointParams ap;
+                ap.lam_next = lam + (size_t)lc * L;
+                ap.lam_out = lam + (size_t)(lc ^ 1) * L;
+                ap.beta_mu = lam + (size_t)lc * L;     // nu^t, scaled by beta in the table gradient
+                ap.beta_scale = 1;
+                ap.S = state(j);
+                ap.coef = c->d_coef;
+                ap.cls = c->d_cls;
+                ap.Z = c->d_Z;
+                ap.dir = c->d_dir;
+                ap.nx = c->nx;
+                ap.nz = c->nz;
+                ap.n = c->n;
+                ap.n_phase = c->n_phase;
+                for (int k = 0; k < 4; ++k) ap.bc[k] = c->bc[k];
+                ap.g_alpha = ga;
+                ap.g_beta = gb;
+                ap.tiles = a.mixed.as<int>();
+                ap.dirT = a.dirT.as<int>();
+                ap.bcbitsT = bcbitsT;
+                ap.push = push ? 1 : 0;
+                AK(launch_adjoint_step_nu_mixed(ap, a.n_mixed, s), "adjoint step (mixed tiles)");
+                AK(launch_adjoint_table(ap, slots, s), "adjoint table gradient");
+                lc ^= 1;
+            }
+        }
+    } else {
+    AK(launch_adjoint_seed(lam, dl_dev, c->d_dir, c->nx, c->nz, c->n, s), "adjoint seed");
     for (int g = nseg - 1; g >= 0; --g) {
         const int len = std::min(K, nsteps - g * K);
         // state j of the segment: the checkpoint for j = 0, recomputed into
@@ -700,6 +831,7 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
             lc ^= 1;
         }
     }
+    }
     // outputs
     if (grad_tau || grad_albedo) {
         // a missing output is computed into staging that is not read back
@@ -733,6 +865,7 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
     AK(cudaStreamSynchronize(s), "adjoint sync");
 #undef AK
     if (adjoint_table_tc_take_error() > 0) return fail(c, RTLB_E_TIMEOUT, "the table-gradient kernel gave up waiting");
+    if (adjoint_step_tc_take_error() > 0) return fail(c, RTLB_E_TIMEOUT, "the tensor-core reverse step gave up waiting");
     return RTLB_OK;
 }
 
@@ -741,6 +874,7 @@ rtlb_status rtlb_release_workspace(rtlb_ctx *c)
     if (!c) return RTLB_E_ARG;
     CK(c, cudaDeviceSynchronize(), "release workspace");
     c->adj.release();
+    c->adj_tc.release();
     return RTLB_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/rtlb.h"
@@ -52,7 +53,15 @@ struct AdjointParams {
     const int *dir;
     int nx, nz, n, n_phase;
     int bc[4];
-    double *g_alpha, *g_beta;  // [nsites] accumulated over the steps
+    double *g_alpha, *g_beta;  // [2][nsites] accumulated over the steps (two halves, summed by the chain rule)
+    // transposed-stream form (4n = 128): tile list of the CUDA-core kernel,
+    // negated offsets and boundary kinds of the push of T^T, push or store in
+    // place; the table gradient multiplies its input by beta when beta_scale
+    const int *tiles = nullptr;
+    const int *dirT = nullptr;
+    int bcbitsT = 0;
+    int push = 1;
+    int beta_scale = 0;
 };
 
 bool adjoint_supported(int n);
@@ -62,6 +71,13 @@ cudaError_t launch_adjoint_seed(float *lam, const float *dL_dout, const int *dir
 cudaError_t launch_adjoint_chain(const double *ga, const double *gb, const float *tau, const float *alb, int nsites,
                                  int surv_mode, int abs_mode, float *g_tau, float *g_alb, cudaStream_t s);
 cudaError_t launch_adjoint_fold(const double *slots, int nslots, size_t len, double *out, cudaStream_t s);
+// transposed-stream form (4n = 128): CUDA-core reverse step over the listed
+// tiles (p.tiles, n_tiles of them), the table gradient alone, and the seed
+// nu^{N-1} = T^T lambda^N
+cudaError_t launch_adjoint_step_nu_mixed(const AdjointParams &p, int n_tiles, cudaStream_t s);
+cudaError_t launch_adjoint_table(const AdjointParams &p, double *slots, cudaStream_t s);
+cudaError_t launch_adjoint_seed_nu(float *nu, const float *dL_dout, const int *dir, int nx, int nz, int n, int bcbits,
+                                   cudaStream_t s);
 // tensor-core table gradient (adj_table_tc.cu): 4n <= 128, n_phase * 4n <= 512
 bool adjoint_table_tc_supported(int n, int n_phase);
 cudaError_t launch_adjoint_table_tc(const AdjointParams &p, double *slots, int nslots, cudaStream_t s);
@@ -110,6 +126,22 @@ struct AdjWork {
         for (DevBuf *b : {&ck, &seg, &lam, &bm, &ga, &gb, &slots, &G, &tapT, &dl, &gtd, &gad, &gS}) b->release();
     }
 };
+
+// Tensor-core reverse step state (4n = 128), built from the medium on the
+// first rtlb_adjoint after each rtlb_set_medium: Z^T as bf16 hi and lo with
+// their tensor maps, single-class and mixed 128-site tile lists, and the
+// negated streaming offsets.
+struct AdjTcState {
+    DevBuf zhi, zlo, pure, mixed, dirT;
+    int n_pure = 0, n_mixed = 0;
+    CUtensorMap tmZhi{}, tmZlo{};
+    long long gen = -1;                    // medium generation it was built for
+    void release()
+    {
+        for (DevBuf *b : {&zhi, &zlo, &pure, &mixed, &dirT}) b->release();
+        gen = -1;
+    }
+};
 }  // namespace rtlb
 
 struct rtlb_ctx {
@@ -150,6 +182,8 @@ struct rtlb_ctx {
     float *d_rad = nullptr;       // radiance_out staging for host transfers
     void *tc = nullptr;           // tensor-core path state (tc.cu)
     rtlb::AdjWork adj;            // rtlb_adjoint workspace (grow-only)
+    rtlb::AdjTcState adj_tc;      // tensor-core reverse step tables and tile lists
+    long long medium_gen = 0;     // counts rtlb_set_medium calls
 
     int64_t steps = 0;
     bool has_prev = false;

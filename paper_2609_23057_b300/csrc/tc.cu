@@ -1042,6 +1042,11 @@ rtlb_status tc_check_error(rtlb_ctx *c, cudaStream_t s)
 
 bool tc_encode_state_map(CUtensorMap *m, const float *S, size_t nsites, int n) { return encode_state_map(m, S, nsites, n); }
 
+bool tc_encode_table_map(CUtensorMap *m, const __nv_bfloat16 *Z, int N4, int KP, int n_phase, int box_rows)
+{
+    return encode_z_map(m, Z, N4, KP, n_phase, box_rows);
+}
+
 bool tc_table_maps(const rtlb_ctx *c, CUtensorMap *zhi, CUtensorMap *zlo, const float **fwd)
 {
     const TcState *t = static_cast<const TcState *>(c->tc);

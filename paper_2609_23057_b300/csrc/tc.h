@@ -1,6 +1,7 @@
 // Tensor-core (tcgen05) forms of the fused step: operand tables and launch.
 #pragma once
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <vector>
 
 #include "rtlb_internal.h"
@@ -22,6 +23,33 @@ rtlb_status tc_step(rtlb_ctx *c, const StepParams &p, cudaStream_t s);
 rtlb_status tc_check_error(rtlb_ctx *c, cudaStream_t s);
 int tc_mixed_tiles(const rtlb_ctx *c);
 void tc_release(rtlb_ctx *c);
+
+// Tensor-core reverse step of the adjoint (adj_tc.cu), 4n = 128 only: reads
+// nu^t (tensor map tmNu, direction-major) and S^t, writes nu^{t-1} pushed
+// along the negated offsets (push = 1) or lambda^0 in place (push = 0), and
+// adds the per-site gradient sums into g_alpha / g_beta, each [2][nsites]
+// (one half per group of directions).  Tables: Z^T as bf16 hi and lo,
+// [n_phase][128][128], tensor maps with 128-row boxes.  `tiles` lists
+// single-class 128-site tiles sorted by class (tile | class << 24).
+struct AdjTcLaunch {
+    const float *S;
+    const float4 *coef;
+    const int *dirT;
+    int bcbitsT;
+    float *nu_out;
+    double *g_alpha, *g_beta;
+    const int *tiles;
+    int n_tiles;
+    int nx, nz, n;
+    int push;
+    int sm_count;
+};
+int adjoint_tc_stages();
+cudaError_t launch_adjoint_step_tc(const CUtensorMap &tmNu, const CUtensorMap &tmZhi, const CUtensorMap &tmZlo,
+                                   const AdjTcLaunch &a, cudaStream_t s);
+int adjoint_step_tc_take_error();
+// bf16 table [n_phase][N4][KP] tensor map with boxes of 64 columns x box_rows rows
+bool tc_encode_table_map(CUtensorMap *m, const __nv_bfloat16 *Z, int N4, int KP, int n_phase, int box_rows);
 
 // For the multi-channel batch (single-CTA layout only, n <= 32):
 bool tc_encode_state_map(CUtensorMap *m, const float *S, size_t nsites, int n);

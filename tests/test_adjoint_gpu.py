@@ -81,6 +81,31 @@ def test_adjoint_many_chunks_per_block(torch_cuda, orc, nzen, naz):
     assert _rel(gS, rS) < TOL
 
 
+@pytest.mark.parametrize("nx,nz,bc,nph,K", [
+    (256, 6, (2, 0, 1, 1), 2, 5),      # rows alternate class, 128 | nx: every tile single-class
+    (200, 7, (2, 0, 0, 0), 2, 1),      # tiles straddle rows: single-class and mixed tiles
+    (130, 3, (1, 1, 2, 0), 1, 4),      # one class, ragged last tile, periodic z
+    (384, 4, (2, 2, 1, 1), 3, 12),
+])
+def test_adjoint_tensor_core_reverse_step(torch_cuda, orc, nx, nz, bc, nph, K):
+    """n = 32: the reverse step runs on the tensor cores over single-class
+    128-site tiles (the rest on the CUDA cores), in the transposed-stream
+    form; gradients and dL/dS0 against the oracle adjoint."""
+    w = W.random_medium(nx, nz, 4, 8, seed=nx + nz, bc=bc, n_phase=nph, steps=9, surv_mode=1)
+    w.tau = np.minimum(w.tau, 0.9)
+    w.phase_index = (np.arange(nz)[:, None] % nph * np.ones((1, nx))).astype(np.uint8)
+    P = oracle_problem(orc, w)
+    S0 = W.random_state(nz, nx, w.n, seed=4)
+    seed = np.random.default_rng(5).standard_normal((nx, w.n, 4)).astype(np.float32).astype(np.float64)
+    rt, ra, rZ, rS = P.adjoint(S0, w.steps, seed, want_S0=True)
+    gt, ga, gZ, gS, SN = _gpu_adjoint(torch_cuda, w, S0, w.steps, seed, K=K)
+    assert _rel(gt, rt) < TOL
+    assert _rel(ga, ra) < TOL
+    assert _rel(gZ, rZ) < TOL
+    assert _rel(gS, rS) < TOL
+    assert _rel(SN, P.run(S0, w.steps)) < 1e-5
+
+
 def test_adjoint_workspace_reuse(torch_cuda, orc):
     """Calls on one context reuse (and grow) the workspace: the same call
     repeated gives the same bits, a larger call after a smaller one and a
