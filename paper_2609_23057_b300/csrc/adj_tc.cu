@@ -297,6 +297,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int z = site / p.nx, x = site - z * p.nx;
             const bool interior = valid && x > 0 && x < p.nx - 1 && z > 0 && z < p.nz - 1;
             const float4 cf = valid ? __ldg(p.coef + site) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const double ga0 = valid ? ga[site] : 0.0, gb0 = valid ? gb[site] : 0.0;
+            // the next tile's S (this thread's directions) on its way into L2
+            if (i + 1 < T) {
+                const int next = (p.tiles[t_begin + i + 1] & 0xFFFFFF) * kTileM + r;
+                if (next < nsites)
+                    for (int d = dbeg; d < dbeg + dn; ++d)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(p.S + (size_t)d * nsites + next));
+            }
             ok = __all_sync(0xffffffffu,
                             mbar_wait(smem_u32(&acc_full[b]), (i >> 1) & 1, abort_flag, p.err, kErrTimeoutEpilogue));
             if (!ok) break;
@@ -304,6 +312,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t yb = tmem + lane_base + (uint32_t)(b * 2 * kN4), nb = yb + (uint32_t)kN4;
             float pa = 0.f, pb = 0.f;
             for (int d0 = dbeg; d0 < dbeg + dn; d0 += 4) {
+                // S first, so its latency overlaps the tensor-memory loads
+                float4 sv4[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    sv4[k] = valid ? __ldg(p.S + (size_t)(d0 + k) * nsites + site) : make_float4(0.f, 0.f, 0.f, 0.f);
                 float y[16], nu[16];
                 tmem_ld16(yb + (uint32_t)(4 * d0), y);
                 tmem_ld16(nb + (uint32_t)(4 * d0), nu);
@@ -311,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int d = d0 + k;
-                    float4 sv = __ldg(p.S + (size_t)d * nsites + site);
+                    float4 sv = sv4[k];
                     sv.x += cf.w;
                     const float svk[4] = {sv.x, sv.y, sv.z, sv.w};
                     float o[4];
@@ -333,8 +346,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             if (valid) {
-                ga[site] += (double)pa;
-                gb[site] += (double)pb;
+                ga[site] = ga0 + (double)pa;
+                gb[site] = gb0 + (double)pb;
             }
             tc_fence_before();
             __syncwarp();
