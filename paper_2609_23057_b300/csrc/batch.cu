@@ -32,6 +32,14 @@ using namespace tcptx;
 using namespace tccommon;
 
 constexpr int kMaxN4 = 128;                 // n <= 32 in a batch
+
+// Fixed cost of a tile in the work balance, in directions' worth.  Measured
+// on the 256-channel workload (n in {8, 16, 32}), TB/s of algorithmic
+// traffic: 0 -> 3.67, 4 -> 4.40, 8 -> 4.11-4.20, 12 -> 4.05, 16 -> 3.90,
+// 24 -> 3.60; equal tile counts per CTA gave 3.05.
+#ifndef RTLB_BATCH_TILE_COST
+#define RTLB_BATCH_TILE_COST 4
+#endif
 constexpr int kMaxC = kMaxN4 / 64;
 
 struct ChanDesc {
@@ -47,7 +55,8 @@ struct ChanDesc {
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_step_tc_batch(const ChanDesc *__restrict__ descs, const int2 *__restrict__ items, int n_items, int parity,
+    k_step_tc_batch(const ChanDesc *__restrict__ descs, const int2 *__restrict__ items, const int *__restrict__ bounds,
+                    int parity,
                     int stages, int *err)
 {
     constexpr bool ZLO = MODE >= 2;
@@ -98,24 +107,33 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int t_begin = (int)((long long)n_items * blockIdx.x / gridDim.x);
-    const int t_end = (int)((long long)n_items * (blockIdx.x + 1) / gridDim.x);
+    // this CTA's slice of the item list, balanced by work on the host
+    const int t_begin = bounds[blockIdx.x];
+    const int t_end = bounds[blockIdx.x + 1];
     const int T = t_end - t_begin;
     // item key of the table that must be resident: channel and class
-    auto table_key = [&](int i) { const int2 it = items[t_begin + i]; return (it.x << 8) | (it.y >> 24); };
+    auto key_of = [](int2 it) { return (it.x << 8) | (it.y >> 24); };
 
     if (warp == kProdWarp) {
         if (lane == 0) {
             int prev = -1;
             uint32_t gq[2] = {0, 0}, zr = 0;
             bool ok = true;
+            // the next item and its direction count are fetched a tile ahead
+            int2 it_next = T > 0 ? items[t_begin] : make_int2(0, 0);
+            int n_next = T > 0 ? descs[it_next.x].n : 0;
             for (int i = 0; i < T && ok; ++i) {
-                const int2 it = items[t_begin + i];
+                const int2 it = it_next;
+                const int n = n_next;
+                if (i + 1 < T) {
+                    it_next = items[t_begin + i + 1];
+                    n_next = descs[it_next.x].n;
+                }
                 const ChanDesc *d = descs + it.x;
                 const int tile = it.y & 0xFFFFFF, cls = it.y >> 24;
-                const int n = d->n, N4 = 4 * n, C = (N4 + 63) / 64, groups = n / kDirsPerStage;
+                const int N4 = 4 * n, C = (N4 + 63) / 64, groups = n / kDirsPerStage;
                 const uint32_t z_chunk = (uint32_t)N4 * 128u;
-                const int key = table_key(i);
+                const int key = key_of(it);
                 if (key != prev) {
                     // one z_free phase per table switch (cannot alias)
                     if (i > 0) ok = mbar_wait(smem_u32(z_free), (zr++) & 1, abort_flag, err, kErrTimeoutProducer);
@@ -127,6 +145,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (ZLO) tma_load_3d(smem_u32(sZlo + c * z_chunk), &d->tmZlo, zb, 64 * c, 0, cls);
                     }
                     prev = key;
+                }
+                if (RTLB_BATCH_PREFETCH_NEXT && i + 1 < T) {
+                    // the next item's state chunks on their way into L2
+                    const CUtensorMap *tn = &descs[it_next.x].tmS[parity];
+                    const int tn_tile = it_next.y & 0xFFFFFF;
+                    for (int j = 0; j < n_next / kDirsPerStage; ++j)
+                        for (int h = 0; h < kTileM / kHalfSites; ++h)
+                            tma_prefetch_2d(tn, 4 * (tn_tile * kTileM + h * kHalfSites), j * kDirsPerStage);
                 }
                 for (int j = 0; j < groups && ok; ++j) {
                     const int gr = j & 1;
@@ -157,11 +183,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             int prev = -1;
             uint32_t zl = 0;
             bool ok = true, issued = false;
+            int2 it_next = T > 0 ? items[t_begin] : make_int2(0, 0);
+            int n_next = T > 0 ? descs[it_next.x].n : 0;
             for (int i = 0; i < T && ok; ++i) {
-                const int2 it = items[t_begin + i];
-                const int N4 = 4 * descs[it.x].n, C = (N4 + 63) / 64;
+                const int2 it = it_next;
+                const int N4 = 4 * n_next, C = (N4 + 63) / 64;
+                if (i + 1 < T) {
+                    it_next = items[t_begin + i + 1];
+                    n_next = descs[it_next.x].n;
+                }
                 const int b = i & 1;
-                const int key = table_key(i);
+                const int key = key_of(it);
                 if (key != prev) {
                     ok = mbar_wait(smem_u32(z_full), zl & 1, abort_flag, err, kErrTimeoutMma);
                     ++zl;
@@ -186,7 +218,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mma_commit(smem_u32(&a_empty[c]));     // one completion per item on every chunk barrier
                 }
                 mma_commit(smem_u32(&acc_full[b]));
-                if (i + 1 < T && table_key(i + 1) != key) mma_commit(smem_u32(z_free));
+                if (i + 1 < T && key_of(it_next) != key) mma_commit(smem_u32(z_free));
                 issued = true;
             }
             if (issued) {
@@ -211,20 +243,28 @@ __global__ void __launch_bounds__(kThreads, 1)
             return load_coef(d->coef, (it.y & 0xFFFFFF) * kTileM + r, d->nx * d->nz);
         };
         float4 cf_next = T > 0 ? coef_of(0) : float4{};
+        int2 it_next = T > 0 ? items[t_begin] : make_int2(0, 0);
+        int n_next = T > 0 ? descs[it_next.x].n : 0;
+        const float *fwd_next = T > 0 ? descs[it_next.x].fwd : nullptr;
         for (int i = 0; i < T && ok; ++i) {
-            const int2 it = items[t_begin + i];
-            const ChanDesc *d = descs + it.x;
+            const int2 it = it_next;
             const int cls = it.y >> 24;
-            const int n = d->n;
+            const int n = n_next;
+            const float *fwd = fwd_next;
             const int b = i & 1;
             const float4 cf = cf_next;
-            if (i + 1 < T) cf_next = coef_of(i + 1);
+            if (i + 1 < T) {
+                cf_next = coef_of(i + 1);
+                it_next = items[t_begin + i + 1];
+                n_next = descs[it_next.x].n;
+                fwd_next = descs[it_next.x].fwd;
+            }
             ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_empty[b]), ((i >> 1) & 1) ^ 1, abort_flag, err,
                                                    kErrTimeoutConverter));
             if (!ok) break;
             tc_fence_after();
             const uint32_t acc = tmem + lane_base + (uint32_t)(b * kMaxN4);
-            ok = convert_tile<false>(cf, d->fwd + (size_t)cls * n, r, lane, grp, n, n / kDirsPerStage, stages, gq, i, acc, sA,
+            ok = convert_tile<false>(cf, fwd + (size_t)cls * n, r, lane, grp, n, n / kDirsPerStage, stages, gq, i, acc, sA,
                                      sA, sStage, st_full, st_empty, a_empty, a_chunk, abort_flag, err);
             if (!ok) break;
             tmem_wait_st();
@@ -239,17 +279,30 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int r = q * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         bool ok = true;
-        for (int i = 0; i < T && ok; ++i) {
-            const int2 it = items[t_begin + i];
+        // the next item's channel fields are fetched a tile ahead
+        struct Fields {
+            int tile, n, nx, nz, bcbits;
+            float *S_new;
+            const int *dir;
+            const float *inflow;
+        };
+        auto fields_of = [&](int k) {
+            const int2 it = items[t_begin + k];
             const ChanDesc *d = descs + it.x;
-            const int tile = it.y & 0xFFFFFF;
-            const int n = d->n, nx = d->nx, nz = d->nz, nsites = nx * nz;
+            return Fields{it.y & 0xFFFFFF, d->n, d->nx, d->nz, d->bcbits, d->S[parity ^ 1], d->dir, d->inflow};
+        };
+        Fields f_next = T > 0 ? fields_of(0) : Fields{};
+        for (int i = 0; i < T && ok; ++i) {
+            const Fields f = f_next;
+            if (i + 1 < T) f_next = fields_of(i + 1);
+            const int tile = f.tile;
+            const int n = f.n, nx = f.nx, nz = f.nz, nsites = nx * nz;
             const int b = i & 1;
             const int site = tile * kTileM + r;
             const int z = site / nx, x = site - z * nx;
             const bool interior = site < nsites && x > 0 && x < nx - 1 && z > 0 && z < nz - 1;
-            float *S_new = d->S[parity ^ 1];
-            const int *dir = d->dir;
+            float *S_new = f.S_new;
+            const int *dir = f.dir;
             ok = __all_sync(0xffffffffu,
                             mbar_wait(smem_u32(&acc_full[b]), (i >> 1) & 1, abort_flag, err, kErrTimeoutEpilogue));
             if (!ok) break;
@@ -270,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 } else if (site < nsites) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        push_store(dir, d->inflow, d->bcbits, S_new, nx, nz, n, site, d0 + k,
+                        push_store(dir, f.inflow, f.bcbits, S_new, nx, nz, n, site, d0 + k,
                                    make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
                 }
             }
@@ -304,6 +357,8 @@ struct rtlb_batch {
     ChanDesc *d_desc = nullptr;
     int2 *d_items = nullptr;
     int n_items = 0;
+    int *d_bounds = nullptr;           // [grid + 1] item range of each CTA
+    int grid = 0;
     std::vector<int> mixed_channels;   // channels with tiles that mix classes
     int *d_err = nullptr, *h_err = nullptr;
     int sm_count = 148;
@@ -334,18 +389,18 @@ void drop_graph(rtlb_batch *b)
 // single-class tile, then the CUDA-core kernel on the channels' mixed tiles.
 cudaError_t batch_launch(rtlb_batch *b, int parity, cudaStream_t s)
 {
-    const int grid = std::min(b->sm_count, b->n_items);
+    const int grid = b->grid;
     const size_t smem = batch_smem(b->mode, b->stages);
     cudaError_t e = cudaSuccess;
     if (grid > 0) {
         if (b->mode == 2) {
             e = cudaFuncSetAttribute(k_step_tc_batch<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e == cudaSuccess)
-                k_step_tc_batch<2><<<grid, kThreads, smem, s>>>(b->d_desc, b->d_items, b->n_items, parity, b->stages, b->d_err);
+                k_step_tc_batch<2><<<grid, kThreads, smem, s>>>(b->d_desc, b->d_items, b->d_bounds, parity, b->stages, b->d_err);
         } else {
             e = cudaFuncSetAttribute(k_step_tc_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e == cudaSuccess)
-                k_step_tc_batch<1><<<grid, kThreads, smem, s>>>(b->d_desc, b->d_items, b->n_items, parity, b->stages, b->d_err);
+                k_step_tc_batch<1><<<grid, kThreads, smem, s>>>(b->d_desc, b->d_items, b->d_bounds, parity, b->stages, b->d_err);
         }
         if (e == cudaSuccess) e = cudaGetLastError();
     }
@@ -430,8 +485,27 @@ rtlb_status rtlb_batch_create(int32_t count, rtlb_ctx *const *channels, rtlb_bat
     });
     cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, channels[0]->dev);
     b->n_items = (int)items.size();
+    // one contiguous item range per CTA, of equal work: a tile moves 32 n
+    // bytes per site and carries a fixed cost besides (RTLB_BATCH_TILE_COST
+    // directions' worth), so equal tile counts would leave the CTAs holding
+    // n = 32 tiles with about twice the work of those holding n = 8
+    b->grid = std::min(b->sm_count, b->n_items);
+    std::vector<int> bounds(b->grid + 1, b->n_items);
+    {
+        std::vector<double> pre(items.size() + 1, 0.0);
+        for (size_t i = 0; i < items.size(); ++i) pre[i + 1] = pre[i] + channels[items[i].x]->n + RTLB_BATCH_TILE_COST;
+        size_t i = 0;
+        for (int g = 0; g < b->grid; ++g) {
+            const double target = pre.back() * g / b->grid;
+            while (i < items.size() && pre[i] < target) ++i;
+            bounds[g] = (int)i;
+        }
+        bounds[b->grid] = b->n_items;
+    }
     cudaError_t e = cudaMalloc(&b->d_desc, desc.size() * sizeof(ChanDesc));
     if (e == cudaSuccess && !items.empty()) e = cudaMalloc(&b->d_items, items.size() * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_bounds, bounds.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_bounds, bounds.data(), bounds.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(b->d_desc, desc.data(), desc.size() * sizeof(ChanDesc), cudaMemcpyHostToDevice);
@@ -532,6 +606,7 @@ void rtlb_batch_destroy(rtlb_batch *b)
     drop_graph(b);
     cudaFree(b->d_desc);
     cudaFree(b->d_items);
+    cudaFree(b->d_bounds);
     cudaFree(b->d_err);
     cudaFreeHost(b->h_err);
     delete b;
