@@ -37,6 +37,12 @@ constexpr int kMaxN4 = 128;                 // n <= 32 in a batch
 // on the 256-channel workload (n in {8, 16, 32}), TB/s of algorithmic
 // traffic: 0 -> 3.67, 4 -> 4.40, 8 -> 4.11-4.20, 12 -> 4.05, 16 -> 3.90,
 // 24 -> 3.60; equal tile counts per CTA gave 3.05.
+// L2 prefetch of the next item's state chunks (0 = none; measured 3.01
+// TB/s with it against 3.06 without on the 256-channel workload)
+#ifndef RTLB_BATCH_PREFETCH_NEXT
+#define RTLB_BATCH_PREFETCH_NEXT 0
+#endif
+
 #ifndef RTLB_BATCH_TILE_COST
 #define RTLB_BATCH_TILE_COST 4
 #endif

@@ -25,11 +25,6 @@
 #ifndef RTLB_TC_PAIR_PREFETCH_SLOTS
 #define RTLB_TC_PAIR_PREFETCH_SLOTS 4
 #endif
-// Batch kernel: L2 prefetch of the next item's state chunks (0 = none;
-// measured 3.01 TB/s with it against 3.06 without on the 256-channel workload)
-#ifndef RTLB_BATCH_PREFETCH_NEXT
-#define RTLB_BATCH_PREFETCH_NEXT 0
-#endif
 #ifndef RTLB_TC_STREAM_STORES
 #define RTLB_TC_STREAM_STORES 1
 #endif
