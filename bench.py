@@ -256,6 +256,43 @@ def accuracy(precisions, steps):
     return out
 
 
+def fp32_class(steps: int, peaks, src):
+    """The float32-accuracy forms on the 512x512, n = 32 steady-state medium:
+    BF16X3 (tensor cores, bf16 hi+lo operands, three MMAs) against FP32 (CUDA
+    cores): CUDA-event time per step over `steps` steps, and the error of each
+    against the FP64 oracle on the 128x128 centre crop run as its own problem
+    for 100 steps from zero."""
+    import torch
+    import oracle
+    from paper_2609_23057_b300.solver import solver_for
+    sys.path.insert(0, os.path.join(HERE, "tests"))
+    from _util import oracle_problem, rel_err_I
+    w = W.steady()
+    out = {"workload": w.name, "steps": steps}
+    for prec in ("bf16x3", "fp32"):
+        s = solver_for(w, prec)
+        s.step(3)
+        torch.cuda.synchronize()
+        per, tot = _time_steps(torch, s, torch.cuda.current_stream(), steps)
+        s.close()
+        ms = tot / len(per)
+        sdu = w.sites * w.n
+        entry = {"ms_per_step": ms, "value": sdu / (ms * 1e-3), "unit": UNIT}
+        if prec == "bf16x3":
+            entry["roofline"] = _roofline(prec, w.n, sdu, statistics.mean(per) * 1e-3, peaks, src)
+        out[prec] = entry
+    c = w.crop(192, 320, 192, 320, name="lattice512_n32_crop128")
+    P = oracle_problem(oracle, c)
+    ref = P.run(P.zero_state(), 100)
+    for prec in ("bf16x3", "fp32"):
+        s = solver_for(c, prec)
+        s.step(100)
+        got = s.get_state().cpu().numpy().astype(np.float64)
+        s.close()
+        out[prec]["rel_err_I_state_crop128_100steps"] = rel_err_I(got, ref, floor_frac=1e-3)
+    return out
+
+
 def adjoint_ratio(steps: int, headline: str):
     """Time rtlb_adjoint on the 1024x256, n = 32 workload against the forward
     of the same number of steps in float32 and in the headline precision, with
@@ -475,6 +512,8 @@ def run_ours(args):
             adj = adjoint_ratio(args.adjoint_steps, args.precision)
             line["adjoint"] = adj
             line["adjoint_over_forward"] = adj["adjoint_over_forward"]["fp32"]
+        if ws == 1 and args.fp32_class_steps > 0:
+            line["fp32_class"] = fp32_class(args.fp32_class_steps, peaks, src)
         if ws == 1 and args.accuracy_steps > 0:
             precs = [args.precision] + [p for p in ("bf16", "fp8", "fp32") if p != args.precision]
             line["accuracy"] = accuracy(precs, args.accuracy_steps)
@@ -500,6 +539,8 @@ def main():
                     help="steps of the bilinear-streaming timing (0 = skip)")
     ap.add_argument("--batch-steps", type=int, default=500,
                     help="steps of the 256-channel batch timing (0 = skip)")
+    ap.add_argument("--fp32-class-steps", type=int, default=100,
+                    help="steps of the 512x512 n=32 BF16X3 / FP32 timing (0 = skip)")
     ap.add_argument("--adjoint-steps", type=int, default=1000,
                     help="steps of the 1024x256 adjoint timing (0 = skip)")
     ap.add_argument("--nx", type=int, default=2048, help="lattice width (profiling of smaller cases)")

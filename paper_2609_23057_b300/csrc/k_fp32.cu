@@ -26,8 +26,19 @@ struct Cfg {
     static constexpr int SG = 256 / CG;                  // site groups
     static constexpr int SITES = SG * TS;                // sites per CTA
     static constexpr int KC = 16;                        // k rows per B chunk
-    static constexpr size_t SMEM = (size_t)N4 * SITES * 4 + (size_t)KC * N4 * 4 + (size_t)SITES * 16;
+    // S~ tile, two Z^T chunks (the next one is copied in while the current one
+    // is used), four per-site words
+    static constexpr size_t SMEM = (size_t)N4 * SITES * 4 + (size_t)2 * KC * N4 * 4 + (size_t)SITES * 16;
 };
+
+__device__ __forceinline__ void cp_async16(float *dst, const float *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ void store_out(const StepParams &p, int site, int d, float4 v)
 {
@@ -41,8 +52,8 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
     constexpr int TS = C::TS, SG = C::SG, SITES = C::SITES, KC = C::KC;
     extern __shared__ __align__(16) float smem[];
     float *As = smem;                        // [N4][SITES]   S~ (k-major)
-    float *Bs = As + N4 * SITES;             // [KC][N4]      Z^T chunk
-    float *s_alpha = Bs + KC * N4;           // [SITES]  alpha hi
+    float *Bs = As + N4 * SITES;             // [2][KC][N4]   Z^T chunks
+    float *s_alpha = Bs + 2 * KC * N4;       // [SITES]  alpha hi
     float *s_alo = s_alpha + SITES;          // [SITES]  alpha lo
     float *s_beta = s_alo + SITES;           // [SITES]
     int *s_cls = reinterpret_cast<int *>(s_beta + SITES);
@@ -112,24 +123,41 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
-    for (int cl = 0; cl < p.n_phase; ++cl) {
-        if (!(mask & (1u << cl))) continue;
-        const float *Zc = p.ZT + (size_t)cl * N4 * N4;
+    // the (class, chunk) sequence: every KC-row chunk of Z_c^T for each class
+    // present, the next chunk's copies in flight while the current one is used
+    constexpr int NCH = N4 / KC;
+    auto next_class = [&](int cl) {
+        const unsigned rest = cl < 31 ? mask & ~((2u << cl) - 1u) : 0u;
+        return rest ? __ffs(rest) - 1 : -1;
+    };
+    auto load_chunk = [&](int cl, int ch, int buf) {
+        const float *src = p.ZT + (size_t)cl * N4 * N4 + (size_t)ch * KC * N4;
+        float *dst = Bs + buf * KC * N4;
+        for (int idx = tid; idx < KC * N4 / 4; idx += 256) cp_async16(dst + 4 * idx, src + 4 * idx);
+        cp_async_commit();
+    };
+    int cl = mask ? __ffs(mask) - 1 : -1;
+    if (cl >= 0) load_chunk(cl, 0, 0);
+    int buf = 0;
+    while (cl >= 0) {
+        const int ncl = next_class(cl);
         float m[TS];
 #pragma unroll
         for (int i = 0; i < TS; ++i) m[i] = (!mixed || s_cls[sl + i] == cl) ? 1.f : 0.f;
-        for (int k0 = 0; k0 < N4; k0 += KC) {
-            __syncthreads();
-            for (int idx = tid; idx < KC * N4 / 4; idx += 256)
-                reinterpret_cast<float4 *>(Bs)[idx] =
-                    reinterpret_cast<const float4 *>(Zc + (size_t)k0 * N4)[idx];
-            __syncthreads();
+        for (int ch = 0; ch < NCH; ++ch) {
+            const int k0 = ch * KC;
+            if (ch + 1 < NCH) load_chunk(cl, ch + 1, buf ^ 1);
+            else if (ncl >= 0) load_chunk(ncl, 0, buf ^ 1);
+            else cp_async_commit();              // empty group: the wait below counts the same way
+            cp_async_wait1();                    // this thread's copies of the current chunk
+            __syncthreads();                     // everyone's
+            const float *Bc = Bs + buf * KC * N4;
 #pragma unroll 4
             for (int k = 0; k < KC; ++k) {
                 const float4 a0 = *reinterpret_cast<const float4 *>(&As[(k0 + k) * SITES + sl]);
                 const float4 a1 = *reinterpret_cast<const float4 *>(&As[(k0 + k) * SITES + sl + 4]);
-                const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[k * N4 + c0]);
-                const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[k * N4 + c0 + 4]);
+                const float4 b0 = *reinterpret_cast<const float4 *>(&Bc[k * N4 + c0]);
+                const float4 b1 = *reinterpret_cast<const float4 *>(&Bc[k * N4 + c0 + 4]);
                 float a[TS] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
                 const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
                 if (mixed) {
@@ -141,8 +169,12 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
             }
+            __syncthreads();                     // the buffer is free for the chunk after next
+            buf ^= 1;
         }
+        cl = ncl;
     }
+    cp_async_wait0();
 
     // epilogue: P = alpha S~ + beta Y, pushed to the neighbour
 #pragma unroll
