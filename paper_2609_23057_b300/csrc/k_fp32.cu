@@ -111,8 +111,12 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
     }
     __syncthreads();
 
+    // this thread's eight sites: four at sg * 4 and four half a tile further,
+    // so that a warp's site groups read consecutive 16-byte chunks of a row
+    // of As (one wavefront per 128 bytes, no bank conflicts)
     const int sg = tid % SG, cg = tid / SG;
-    const int sl = sg * TS;       // first local site of this thread
+    const int sl0 = sg * 4, sl1 = SITES / 2 + sg * 4;
+    auto site_of = [&](int i) { return i < 4 ? sl0 + i : sl1 + i - 4; };
     const int c0 = cg * 8;        // first output column of this thread
     const unsigned mask = s_mask;
     const bool mixed = (mask & (mask - 1u)) != 0u;
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
         const int ncl = next_class(cl);
         float m[TS];
 #pragma unroll
-        for (int i = 0; i < TS; ++i) m[i] = (!mixed || s_cls[sl + i] == cl) ? 1.f : 0.f;
+        for (int i = 0; i < TS; ++i) m[i] = (!mixed || s_cls[site_of(i)] == cl) ? 1.f : 0.f;
         for (int ch = 0; ch < NCH; ++ch) {
             const int k0 = ch * KC;
             if (ch + 1 < NCH) load_chunk(cl, ch + 1, buf ^ 1);
@@ -154,8 +158,8 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
             const float *Bc = Bs + buf * KC * N4;
 #pragma unroll 4
             for (int k = 0; k < KC; ++k) {
-                const float4 a0 = *reinterpret_cast<const float4 *>(&As[(k0 + k) * SITES + sl]);
-                const float4 a1 = *reinterpret_cast<const float4 *>(&As[(k0 + k) * SITES + sl + 4]);
+                const float4 a0 = *reinterpret_cast<const float4 *>(&As[(k0 + k) * SITES + sl0]);
+                const float4 a1 = *reinterpret_cast<const float4 *>(&As[(k0 + k) * SITES + sl1]);
                 const float4 b0 = *reinterpret_cast<const float4 *>(&Bc[k * N4 + c0]);
                 const float4 b1 = *reinterpret_cast<const float4 *>(&Bc[k * N4 + c0 + 4]);
                 float a[TS] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
@@ -179,7 +183,7 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
     // epilogue: P = alpha S~ + beta Y, pushed to the neighbour
 #pragma unroll
     for (int i = 0; i < TS; ++i) {
-        const int s = sl + i, site = site0 + s;
+        const int s = site_of(i), site = site0 + s;
         if (site >= nsites) continue;
         const float al = s_alpha[s], alo = s_alo[s], be = s_beta[s];
 #pragma unroll
