@@ -143,9 +143,37 @@ def cpu_baseline(steps: int, seconds: float = 12.0):
             break
     dt = time.perf_counter() - t0
     sdu = w.sites * w.n * k
-    return {"value": sdu / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle, {k} steps of the 256x256 crop [896,1152)^2 of the same "
-                      f"medium (n=64), {dt:.1f} s"}
+    out = {"value": sdu / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"FP64 oracle, {k} steps of the 256x256 crop [896,1152)^2 of the same "
+                     f"medium (n=64), {dt:.1f} s"}
+    out["single_thread"] = _cpu_single_thread(seconds / 2)
+    return out
+
+
+def _cpu_single_thread(seconds: float):
+    """The same oracle loop on one host thread (a child process started with
+    OMP_NUM_THREADS=1, since the thread count is fixed when OpenMP starts)."""
+    code = ("import json, os, sys, time; sys.path.insert(0, {here!r}); sys.path.insert(0, {tests!r})\n"
+            "import oracle\n"
+            "from paper_2609_23057_b300 import workloads as W\n"
+            "from _util import oracle_problem\n"
+            "w = W.precision_crop(steps=1); P = oracle_problem(oracle, w); S = P.step(P.zero_state())\n"
+            "t0 = time.perf_counter(); k = 0\n"
+            "while True:\n"
+            "    S = P.step(S); k += 1\n"
+            "    if time.perf_counter() - t0 >= {sec}: break\n"
+            "dt = time.perf_counter() - t0\n"
+            "print(json.dumps({{'value': w.sites * w.n * k / dt, 'cores': oracle.num_threads(), 'steps': k, 'seconds': dt}}))\n"
+            ).format(here=HERE, tests=os.path.join(HERE, "tests"), sec=float(seconds))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=seconds * 4 + 120)
+        d = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    except (subprocess.SubprocessError, IndexError, ValueError) as e:
+        return {"unavailable": f"single-thread run failed: {type(e).__name__}"}
+    return {"value": d["value"], "unit": UNIT, "cores": d["cores"],
+            "sample": f"FP64 oracle on one thread, {d['steps']} steps of the same crop, {d['seconds']:.1f} s"}
 
 
 def run_reference(args):
