@@ -21,25 +21,46 @@ inline int grid_for(size_t work, int per_block = kThreads)
 }
 
 // user [site][d][4]  ->  direction-major [d][site][4]
-__global__ void k_user_to_dm(const float4 *__restrict__ user, float4 *__restrict__ dm,
-                             size_t nsites, int n)
+// Layout conversion between the user's [site][d] and the direction-major
+// [d][site] state (float4 entries): a transpose through shared memory in
+// tiles of kXS sites x kXD directions, so that both the reads and the writes
+// of global memory are contiguous runs.  The tile rows are padded by one
+// float4 so that neither shared-memory phase has bank conflicts.
+constexpr int kXS = 32, kXD = 64;
+
+__global__ void __launch_bounds__(256) k_user_to_dm(const float4 *__restrict__ user, float4 *__restrict__ dm,
+                                                    int nsites, int n)
 {
-    const size_t total = nsites * n;
-    for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < total;
-         j += (size_t)gridDim.x * blockDim.x) {
-        const size_t d = j / nsites, site = j % nsites;  // consecutive j -> consecutive sites
-        dm[j] = user[site * n + d];
+    __shared__ float4 t[kXD][kXS + 1];
+    const int s0 = blockIdx.x * kXS, d0 = blockIdx.y * kXD;
+    const int ns = min(kXS, nsites - s0), nd = min(kXD, n - d0);
+    // read: for each site, its nd directions are contiguous in the user layout
+    for (int k = threadIdx.x; k < kXS * kXD; k += blockDim.x) {
+        const int s = k / kXD, dd = k - s * kXD;
+        if (s < ns && dd < nd) t[dd][s] = user[(size_t)(s0 + s) * n + d0 + dd];
+    }
+    __syncthreads();
+    // write: for each direction, the tile's sites are contiguous
+    for (int k = threadIdx.x; k < kXS * kXD; k += blockDim.x) {
+        const int dd = k / kXS, s = k - dd * kXS;
+        if (s < ns && dd < nd) dm[(size_t)(d0 + dd) * nsites + s0 + s] = t[dd][s];
     }
 }
 
-__global__ void k_dm_to_user(const float4 *__restrict__ dm, float4 *__restrict__ user,
-                             size_t nsites, int n)
+__global__ void __launch_bounds__(256) k_dm_to_user(const float4 *__restrict__ dm, float4 *__restrict__ user,
+                                                    int nsites, int n)
 {
-    const size_t total = nsites * n;
-    for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < total;
-         j += (size_t)gridDim.x * blockDim.x) {
-        const size_t site = j / n, d = j % n;  // consecutive j -> consecutive user entries
-        user[j] = dm[d * nsites + site];
+    __shared__ float4 t[kXD][kXS + 1];
+    const int s0 = blockIdx.x * kXS, d0 = blockIdx.y * kXD;
+    const int ns = min(kXS, nsites - s0), nd = min(kXD, n - d0);
+    for (int k = threadIdx.x; k < kXS * kXD; k += blockDim.x) {
+        const int dd = k / kXS, s = k - dd * kXS;
+        if (s < ns && dd < nd) t[dd][s] = dm[(size_t)(d0 + dd) * nsites + s0 + s];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kXS * kXD; k += blockDim.x) {
+        const int s = k / kXD, dd = k - s * kXD;
+        if (s < ns && dd < nd) user[(size_t)(s0 + s) * n + d0 + dd] = t[dd][s];
     }
 }
 
@@ -243,15 +264,15 @@ __global__ void k_fill(float *p, size_t count, float v)
 
 cudaError_t launch_user_to_dm(const float *user, float *dm, int nsites, int n, cudaStream_t s)
 {
-    k_user_to_dm<<<grid_for((size_t)nsites * n), kThreads, 0, s>>>(
-        reinterpret_cast<const float4 *>(user), reinterpret_cast<float4 *>(dm), (size_t)nsites, n);
+    const dim3 grid((nsites + kXS - 1) / kXS, (n + kXD - 1) / kXD);
+    k_user_to_dm<<<grid, 256, 0, s>>>(reinterpret_cast<const float4 *>(user), reinterpret_cast<float4 *>(dm), nsites, n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dm_to_user(const float *dm, float *user, int nsites, int n, cudaStream_t s)
 {
-    k_dm_to_user<<<grid_for((size_t)nsites * n), kThreads, 0, s>>>(
-        reinterpret_cast<const float4 *>(dm), reinterpret_cast<float4 *>(user), (size_t)nsites, n);
+    const dim3 grid((nsites + kXS - 1) / kXS, (n + kXD - 1) / kXD);
+    k_dm_to_user<<<grid, 256, 0, s>>>(reinterpret_cast<const float4 *>(dm), reinterpret_cast<float4 *>(user), nsites, n);
     return cudaGetLastError();
 }
 
