@@ -111,8 +111,12 @@ __global__ void __launch_bounds__(256, 2) k_adj_step(AdjointParams p)
     }
     __syncthreads();
 
+    // this thread's eight sites: four at sg * 4 and four half a tile further,
+    // so that a warp's site groups read consecutive 16-byte chunks of a row of
+    // Ms (no shared-memory bank conflicts)
     const int sg = tid % SG, cg = tid / SG;
-    const int sl = sg * TS, c0 = cg * 8;
+    const int sl0 = sg * 4, sl1 = SITES / 2 + sg * 4, c0 = cg * 8;
+    auto site_of = [&](int i) { return i < 4 ? sl0 + i : sl1 + i - 4; };
     const unsigned mask = s_mask;
     const bool mixed = (mask & (mask - 1u)) != 0u;
     float acc[TS][8];
@@ -126,7 +130,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_step(AdjointParams p)
         const float *Zc = p.Z + (size_t)cl * N4 * N4;
         float msk[TS];
 #pragma unroll
-        for (int i = 0; i < TS; ++i) msk[i] = (!mixed || s_cls[sl + i] == cl) ? 1.f : 0.f;
+        for (int i = 0; i < TS; ++i) msk[i] = (!mixed || s_cls[site_of(i)] == cl) ? 1.f : 0.f;
         for (int k0 = 0; k0 < N4; k0 += KC) {
             __syncthreads();
             for (int idx = tid; idx < KC * N4 / 4; idx += 256)
@@ -134,8 +138,8 @@ __global__ void __launch_bounds__(256, 2) k_adj_step(AdjointParams p)
             __syncthreads();
 #pragma unroll 4
             for (int k = 0; k < KC; ++k) {
-                const float4 a0 = *reinterpret_cast<const float4 *>(&Ms[(k0 + k) * SITES + sl]);
-                const float4 a1 = *reinterpret_cast<const float4 *>(&Ms[(k0 + k) * SITES + sl + 4]);
+                const float4 a0 = *reinterpret_cast<const float4 *>(&Ms[(k0 + k) * SITES + sl0]);
+                const float4 a1 = *reinterpret_cast<const float4 *>(&Ms[(k0 + k) * SITES + sl1]);
                 const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[k * N4 + c0]);
                 const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[k * N4 + c0 + 4]);
                 float a[TS] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
@@ -158,7 +162,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_step(AdjointParams p)
     float4 *Mo = reinterpret_cast<float4 *>(p.beta_mu);
 #pragma unroll
     for (int i = 0; i < TS; ++i) {
-        const int s = sl + i, site = site0 + s;
+        const int s = site_of(i), site = site0 + s;
         if (site >= nsites) {
             s_pa[(cg * TS + i) * SG + sg] = 0.f;
             s_pb[(cg * TS + i) * SG + sg] = 0.f;
@@ -199,7 +203,9 @@ __global__ void __launch_bounds__(256, 2) k_adj_step(AdjointParams p)
     for (int s = tid; s < SITES; s += 256) {
         const int site = site0 + s;
         if (site < nsites) {
-            const int i = s % TS, g = s / TS;
+            // the (i, sg) that site_of maps to s
+            const int h = s >= SITES / 2, r = s - h * (SITES / 2);
+            const int i = 4 * h + (r & 3), g = r >> 2;
             float a = 0.f, b = 0.f;
             for (int c = 0; c < Cf::CG; ++c) {
                 a += s_pa[(c * TS + i) * SG + g];
