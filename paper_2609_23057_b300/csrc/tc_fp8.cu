@@ -328,6 +328,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             fence_proxy_async();
             tc_fence_before();
             __syncwarp();
+            // arrive for tile i only once t_ready's phase for tile i - 1 has
+            // completed: a warp with no slot in a tile (group 1 at n = 8) would
+            // otherwise run ahead and its arrivals for later tiles would
+            // complete tile i's phase before the other group wrote A
+            ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(t_ready), (i & 1) ^ 1, abort_flag, p.err,
+                                                   kErrTimeoutConverter));
+            if (!ok) break;
             if (lane == 0) mbar_arrive(smem_u32(t_ready));
         }
     } else {

@@ -1,0 +1,415 @@
+"""A randomized model of the tensor-core step kernels' warp roles and mbarrier
+protocol, for race checking on the CPU.
+
+Roles are generators that yield waits on mbarriers (with the phase index the
+role means to wait for) and perform actions (arrivals, TMA loads, MMAs and
+commits).  The scheduler interleaves runnable roles and completes outstanding
+asynchronous work (TMA loads in any order, MMAs in issue order, a commit once
+every MMA issued before it completed) at random.  mbarrier semantics are the
+hardware's: a phase completes when its pending arrival count and its
+transaction bytes reach zero; `wait(parity p)` passes when the number of
+completed phases has the other parity.  A wait meant for phase k that passes
+with fewer than k + 1 completed phases is a stale pass (the parity aliased); a
+state where nothing can move while roles still wait is a deadlock.  Every
+shared resource carries a data tag that readers check: staging slots (which
+tile and slot was loaded), A-operand chunks, tensor-memory accumulators and
+the resident table.
+"""
+import random
+
+
+class ProtocolError(AssertionError):
+    pass
+
+
+class Barrier:
+    def __init__(self, name, count):
+        self.name, self.count = name, count
+        self.pending, self.tx, self.completed = count, 0, 0
+
+    def arrive(self, n=1):
+        self.pending -= n
+        if self.pending < 0:
+            raise ProtocolError(f"{self.name}: more arrivals than expected in phase {self.completed}")
+        self._maybe_complete()
+
+    def expect_tx(self, nbytes):            # mbarrier.arrive.expect_tx: one arrival plus bytes
+        self.tx += nbytes
+        self.arrive()
+
+    def complete_tx(self, nbytes):
+        self.tx -= nbytes
+        self._maybe_complete()
+
+    def _maybe_complete(self):
+        if self.pending == 0 and self.tx == 0:
+            self.completed += 1
+            self.pending = self.count
+
+    def passes(self, parity):
+        return (self.completed & 1) != parity
+
+
+class Wait:
+    """Yielded by a role: wait on `bar` for the completion of phase `k`
+    (k = -1: the phase before the first, passes on a fresh barrier)."""
+
+    def __init__(self, bar, k, who):
+        self.bar, self.k, self.who = bar, k, who
+
+    def ready(self):
+        return self.bar.passes(self.k & 1)
+
+    def check_pass(self):
+        if self.bar.completed < self.k + 1:
+            raise ProtocolError(f"{self.who}: stale pass on {self.bar.name} waiting for phase {self.k} "
+                                f"with {self.bar.completed} completed")
+
+
+class Machine:
+    def __init__(self, seed):
+        self.rng = random.Random(seed)
+        self.roles = {}                 # name -> [generator, pending Wait or None]
+        self.tma = []                   # outstanding TMA loads: callables run on completion
+        self.mma = []                   # FIFO of ("mma", fn) / ("commit", barrier)
+        self.steps = 0
+
+    def add_role(self, name, gen):
+        self.roles[name] = [gen, None]
+
+    # actions used by roles -------------------------------------------------
+    def tma_load(self, on_land):
+        self.tma.append(on_land)
+
+    def issue_mma(self, on_complete):
+        self.mma.append(("mma", on_complete))
+
+    def commit(self, bar):
+        self.mma.append(("commit", bar))
+
+    # scheduler ---------------------------------------------------------------
+    def _advance(self, name):
+        gen, _ = self.roles[name]
+        try:
+            w = next(gen)
+        except StopIteration:
+            del self.roles[name]
+            return
+        self.roles[name][1] = w
+
+    def run(self, max_steps=2_000_000):
+        for name in list(self.roles):
+            self._advance(name)
+        while self.roles or self.tma or self.mma:
+            self.steps += 1
+            if self.steps > max_steps:
+                raise ProtocolError("model did not finish")
+            choices = [("role", n) for n, (g, w) in self.roles.items() if w is None or w.ready()]
+            if self.tma:
+                choices.append(("tma", None))
+            if self.mma:
+                choices.append(("mma", None))
+            if not choices:
+                waits = {n: f"{w.bar.name}[phase {w.k}, {w.bar.completed} done]" for n, (g, w) in self.roles.items()}
+                raise ProtocolError(f"deadlock: {waits}")
+            kind, name = self.rng.choice(choices)
+            if kind == "role":
+                w = self.roles[name][1]
+                if w is not None:
+                    w.check_pass()
+                self._advance(name)
+            elif kind == "tma":
+                self.tma.pop(self.rng.randrange(len(self.tma)))()
+            else:
+                what, obj = self.mma.pop(0)
+                if what == "mma":
+                    obj()
+                else:
+                    obj.arrive()
+
+
+def _groups(n):
+    return n // 8                        # 8-direction staging slots per tile
+
+
+def _chunks(n):
+    return (4 * n + 63) // 64            # 64-wide bf16 K chunks per tile
+
+
+def bf16_step(items, stages, seed, shared_ring=False):
+    """The single-CTA tensor-core step (and the batch kernel, whose items may
+    differ in n and table): `items` lists (n, table key) per tile in the order
+    a CTA processes them.  Roles as in the kernels: one producer thread (TMA of
+    the table on a key change, after `z_free`; one staging slot per 8
+    directions into its group's ring), eight converter warps (quadrant q,
+    group grp: slot j = 2c + grp of every 64-wide chunk c; TMEM init, then the
+    A chunk once the previous tile's MMAs released it), one MMA thread (a
+    commit per chunk barrier for every chunk the widest item has, then the
+    accumulator barrier, then `z_free` before a key change) and eight epilogue
+    warps (quadrant q, half of the directions).  shared_ring: the earlier form
+    in which both converter groups consumed one ring of `stages` slots."""
+    M = Machine(seed)
+    T = len(items)
+    ring = stages // 2
+    max_c = max(_chunks(n) for n, _ in items)
+    st_full = [Barrier(f"st_full[{s}]", 1) for s in range(stages)]
+    st_empty = [Barrier(f"st_empty[{s}]", 4) for s in range(stages)]
+    a_empty = [Barrier(f"a_empty[{c}]", 1) for c in range(max_c)]
+    t_ready = [Barrier(f"t_ready[{b}]", 8) for b in range(2)]
+    acc_full = [Barrier(f"acc_full[{b}]", 1) for b in range(2)]
+    acc_empty = [Barrier(f"acc_empty[{b}]", 8) for b in range(2)]
+    z_full, z_free = Barrier("z_full", 1), Barrier("z_free", 1)
+    stage = [None] * stages
+    A, acc, z = {}, {}, [None]
+    base = [0]
+    for n, _ in items:
+        base.append(base[-1] + _groups(n))
+
+    def slot_of(i, j, grp, local):
+        if shared_ring:
+            qg = base[i] + j
+            return qg % stages, qg // stages
+        return grp * ring + local % ring, local // ring
+
+    def producer():
+        prev, zr, gq = None, 0, [0, 0]
+        for i, (n, key) in enumerate(items):
+            if key != prev:
+                if i > 0:
+                    yield Wait(z_free, zr, "producer")
+                    zr += 1
+                z_full.expect_tx(1)
+
+                def land_z(key=key):
+                    z[0] = key
+                    z_full.complete_tx(1)
+                M.tma_load(land_z)
+                prev = key
+            for j in range(_groups(n)):
+                gr = j & 1
+                local = gq[gr]
+                gq[gr] += 1
+                s, k = slot_of(i, j, gr, local)
+                yield Wait(st_empty[s], k - 1, "producer")
+                st_full[s].expect_tx(1)
+
+                def land(s=s, tag=(i, j)):
+                    stage[s] = tag
+                    st_full[s].complete_tx(1)
+                M.tma_load(land)
+
+    def converter(q, grp):
+        who = f"converter(q{q},g{grp})"
+        gq = 0
+        for i, (n, key) in enumerate(items):
+            b = i & 1
+            yield Wait(acc_empty[b], (i >> 1) - 1, who)
+            for c in range(_chunks(n)):
+                j = 2 * c + grp
+                mine = j < _groups(n)
+                if mine:
+                    local = gq
+                    gq += 1
+                    s, k = slot_of(i, j, grp, local)
+                    yield Wait(st_full[s], k, who)
+                    if stage[s] != (i, j):
+                        raise ProtocolError(f"{who} tile {i} slot {j}: staging slot {s} holds {stage[s]}")
+                    cell = acc.get((b, j, q))
+                    if cell is not None and cell[0] != "free":
+                        raise ProtocolError(f"{who} tile {i}: accumulator {b} slot {j} still {cell[0]} for tile {cell[1]}")
+                    acc[(b, j, q)] = ["init", i, 0]
+                    st_empty[s].arrive()
+                yield Wait(a_empty[c], i - 1, who)
+                if mine:
+                    A[(c, grp, q)] = i
+            t_ready[b].arrive()
+
+    def mma():
+        prev, zl = None, 0
+        for i, (n, key) in enumerate(items):
+            b = i & 1
+            if key != prev:
+                yield Wait(z_full, zl, "mma")
+                zl += 1
+                prev = key
+            yield Wait(t_ready[b], i >> 1, "mma")
+            for c in range(max_c):
+                if c < _chunks(n):
+                    def done(i=i, b=b, c=c, n=n, key=key):
+                        for grp in (0, 1):
+                            if 2 * c + grp < _groups(n):
+                                for q in range(4):
+                                    if A.get((c, grp, q)) != i:
+                                        raise ProtocolError(f"MMA tile {i} chunk {c}: A part ({grp},{q}) holds "
+                                                            f"tile {A.get((c, grp, q))}")
+                        if z[0] != key:
+                            raise ProtocolError(f"MMA tile {i}: table {z[0]} resident, {key} needed")
+                        for j in range(_groups(n)):
+                            for q in range(4):
+                                cell = acc.get((b, j, q))
+                                if cell is None or cell[1] != i or cell[0] not in ("init", "partial"):
+                                    raise ProtocolError(f"MMA tile {i} chunk {c}: accumulator {b} slot {j} is {cell}")
+                                cell[0] = "done" if c == _chunks(n) - 1 else "partial"
+                    M.issue_mma(done)
+                M.commit(a_empty[c])
+            M.commit(acc_full[b])
+            if i + 1 < T and items[i + 1][1] != key:
+                M.commit(z_free)
+
+    def epilogue(q, dh):
+        who = f"epilogue(q{q},h{dh})"
+        for i, (n, key) in enumerate(items):
+            b = i & 1
+            yield Wait(acc_full[b], i >> 1, who)
+            dn = n // 2
+            readers = 2 if dn < 8 else 1
+            for j in sorted({d // 8 for d in range(dh * dn, dh * dn + dn)}):
+                cell = acc.get((b, j, q))
+                if cell is None or cell[0] != "done" or cell[1] != i:
+                    raise ProtocolError(f"{who} tile {i}: accumulator {b} slot {j} is {cell}")
+                cell[2] += 1
+                if cell[2] == readers:
+                    cell[0] = "free"
+            acc_empty[b].arrive()
+
+    M.add_role("producer", producer())
+    M.add_role("mma", mma())
+    for q in range(4):
+        for grp in range(2):
+            M.add_role(f"conv{q}{grp}", converter(q, grp))
+        for dh in range(2):
+            M.add_role(f"epi{q}{dh}", epilogue(q, dh))
+    M.run()
+    return M.steps
+
+
+def fp8_step(items, stages, seed, gate_t_ready=True):
+    """The FP8 kernel: one TMEM accumulator handed back by the epilogue one
+    8-direction slot at a time (`d_free[j]`, arrived by every epilogue warp
+    whose directions touch slot j), no A-chunk barriers (a converter past the
+    slot's hand-off knows the previous tile's MMAs completed), a single
+    `t_ready` and `acc_full`.  The converter reads a staging slot twice (block
+    maximum, then conversion), the second time after the hand-off, and arrives
+    on `t_ready` for tile i only after its phase for tile i - 1 completed
+    (gate_t_ready=False: the first form, without that wait, in which a warp
+    with no slot in a tile -- group 1 at n = 8 -- runs ahead)."""
+    M = Machine(seed)
+    T = len(items)
+    n = items[0][0]
+    assert all(it[0] == n for it in items)
+    G, ring = _groups(n), stages // 2
+    dfree_count = 4 if (n // 2) % 8 == 0 else 8
+    st_full = [Barrier(f"st_full[{s}]", 1) for s in range(stages)]
+    st_empty = [Barrier(f"st_empty[{s}]", 4) for s in range(stages)]
+    d_free = [Barrier(f"d_free[{j}]", dfree_count) for j in range(G)]
+    t_ready, acc_full = Barrier("t_ready", 8), Barrier("acc_full", 1)
+    z_full, z_free = Barrier("z_full", 1), Barrier("z_free", 1)
+    stage = [None] * stages
+    A, acc, z, mma_done = {}, {}, [None], [-1]
+
+    def producer():
+        prev, zr, gq = None, 0, [0, 0]
+        for i, (_, key) in enumerate(items):
+            if key != prev:
+                if i > 0:
+                    yield Wait(z_free, zr, "producer")
+                    zr += 1
+                z_full.expect_tx(1)
+
+                def land_z(key=key):
+                    z[0] = key
+                    z_full.complete_tx(1)
+                M.tma_load(land_z)
+                prev = key
+            for j in range(G):
+                gr = j & 1
+                local = gq[gr]
+                gq[gr] += 1
+                s = gr * ring + local % ring
+                yield Wait(st_empty[s], local // ring - 1, "producer")
+                st_full[s].expect_tx(1)
+
+                def land(s=s, tag=(i, j)):
+                    stage[s] = tag
+                    st_full[s].complete_tx(1)
+                M.tma_load(land)
+
+    def converter(q, grp):
+        who = f"converter(q{q},g{grp})"
+        gq = 0
+        for i, _ in enumerate(items):
+            for j in range(grp, G, 2):
+                local = gq
+                gq += 1
+                s = grp * ring + local % ring
+                yield Wait(st_full[s], local // ring, who)
+                if stage[s] != (i, j):                       # first pass: block maximum
+                    raise ProtocolError(f"{who} tile {i} slot {j}: staging slot {s} holds {stage[s]}")
+                yield Wait(d_free[j], i - 1, who)
+                if stage[s] != (i, j):                       # second pass: conversion
+                    raise ProtocolError(f"{who} tile {i} slot {j}: staging slot {s} changed to {stage[s]}")
+                cell = acc.get((j, q))
+                if cell is not None and cell[0] != "free":
+                    raise ProtocolError(f"{who} tile {i}: accumulator slot {j} still {cell[0]} for tile {cell[1]}")
+                acc[(j, q)] = ["init", i, 0]
+                st_empty[s].arrive()
+                if mma_done[0] < i - 1:
+                    raise ProtocolError(f"{who} tile {i}: A slot {j} rewritten before tile {i - 1}'s MMAs completed")
+                A[(j, q)] = i
+            if gate_t_ready:
+                yield Wait(t_ready, i - 1, who)
+            t_ready.arrive()
+
+    def mma():
+        prev, zl = None, 0
+        for i, (_, key) in enumerate(items):
+            if key != prev:
+                yield Wait(z_full, zl, "mma")
+                zl += 1
+                prev = key
+            yield Wait(t_ready, i, "mma")
+
+            def done(i=i, key=key):
+                for j in range(G):
+                    for q in range(4):
+                        if A.get((j, q)) != i:
+                            raise ProtocolError(f"MMA tile {i}: A slot ({j},{q}) holds tile {A.get((j, q))}")
+                        cell = acc.get((j, q))
+                        if cell is None or cell[0] != "init" or cell[1] != i:
+                            raise ProtocolError(f"MMA tile {i}: accumulator slot ({j},{q}) is {cell}")
+                        cell[0] = "done"
+                if z[0] != key:
+                    raise ProtocolError(f"MMA tile {i}: table {z[0]} resident, {key} needed")
+                mma_done[0] = i
+            M.issue_mma(done)
+            M.commit(acc_full)
+            if i + 1 < T and items[i + 1][1] != key:
+                M.commit(z_free)
+
+    def epilogue(q, dh):
+        who = f"epilogue(q{q},h{dh})"
+        dn = n // 2
+        for i, _ in enumerate(items):
+            yield Wait(acc_full, i, who)
+            for d0 in range(dh * dn, dh * dn + dn, 4):
+                j = d0 // 8
+                cell = acc.get((j, q))
+                if cell is None or cell[0] not in ("done", "read") or cell[1] != i:
+                    raise ProtocolError(f"{who} tile {i}: accumulator slot {j} is {cell}")
+                cell[0] = "read"
+                nxt = d0 + 4
+                if nxt % 8 == 0 or nxt == dh * dn + dn:
+                    cell[2] += 1
+                    if cell[2] == (2 if dn < 8 else 1):
+                        cell[0] = "free"
+                    d_free[j].arrive()
+
+    M.add_role("producer", producer())
+    M.add_role("mma", mma())
+    for q in range(4):
+        for grp in range(2):
+            M.add_role(f"conv{q}{grp}", converter(q, grp))
+        for dh in range(2):
+            M.add_role(f"epi{q}{dh}", epilogue(q, dh))
+    M.run()
+    return M.steps

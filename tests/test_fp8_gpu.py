@@ -47,11 +47,13 @@ def _rel(a, b):
 
 @pytest.mark.parametrize("nx,nz,nzen,naz,n_phase", [(256, 8, 2, 4, 2), (256, 8, 4, 4, 2), (384, 6, 4, 8, 2),
                                                     (256, 4, 8, 8, 2), (130, 3, 4, 8, 1), (200, 7, 8, 8, 1),
-                                                    (67, 5, 2, 4, 1)])
+                                                    (67, 5, 2, 4, 1), (512, 128, 2, 4, 2)])
 def test_fp8_one_step_matches_the_fp8_form(torch_cuda, orc, nx, nz, nzen, naz, n_phase):
     """Single-class 128-site tiles (rows of 128-multiple width alternate class,
     or one class with a ragged last tile), emission, polarized inflow on top,
-    periodic sides; a random state; one step."""
+    periodic sides; a random state; one step.  512x128 at n = 8 gives every
+    CTA several tiles, where a converter group without a slot (n = 8) must
+    not run ahead of the other."""
     w = W.random_medium(nx, nz, nzen, naz, seed=nx + nz + naz, bc=(2, 0, 1, 1), n_phase=n_phase, steps=1)
     w.phase_index = (np.arange(nz)[:, None] % n_phase * np.ones((1, nx))).astype(np.uint8)
     S0 = W.random_state(nz, nx, w.n, seed=9, dtype=np.float32)

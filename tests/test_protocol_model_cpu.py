@@ -1,0 +1,60 @@
+"""Race checking of the tensor-core kernels' warp-role protocols on the CPU
+(tests/_protocol_model.py: exact mbarrier parity semantics, TMA loads landing
+in any order, MMAs completing in issue order, a data tag on every staging
+slot, A chunk, accumulator and table).  The kernels' current protocols must
+run clean under many random interleavings; the two earlier forms that the
+model showed to be wrong must be caught."""
+import pytest
+
+import _protocol_model as P
+
+
+@pytest.mark.parametrize("n", [8, 16, 32, 64])
+@pytest.mark.parametrize("stages", [2, 4, 6, 8])
+def test_single_lattice_step_is_race_free(n, stages):
+    items = [(n, 0)] * 5 + [(n, 1)] * 3 + [(n, 0)] * 2          # class switches and back
+    for seed in range(8):
+        P.bf16_step(items, stages, seed)
+
+
+@pytest.mark.parametrize("stages", [2, 4, 6, 8])
+def test_batch_with_mixed_direction_counts_is_race_free(stages):
+    items = ([(8, (0, 0))] * 4 + [(16, (1, 0))] * 3 + [(16, (1, 1))] * 2 + [(32, (2, 0))] * 3 +
+             [(8, (3, 0))] * 2 + [(32, (4, 0))] * 2)
+    for seed in range(12):
+        P.bf16_step(items, stages, seed)
+
+
+def test_shared_staging_ring_is_caught():
+    """The earlier batch form in which both converter groups used one ring of
+    staging slots: a group could pass a slot's parity test a full phase early
+    when the other group lagged (seen on the GPU as faults)."""
+    items = [(8, (0, 0))] * 4 + [(16, (1, 0))] * 3 + [(32, (2, 0))] * 3
+    caught = 0
+    for stages in (2, 3, 4):
+        for seed in range(60):
+            try:
+                P.bf16_step(items, stages, seed, shared_ring=True)
+            except P.ProtocolError:
+                caught += 1
+    assert caught > 0
+
+
+@pytest.mark.parametrize("n", [8, 16, 32, 64])
+@pytest.mark.parametrize("stages", [2, 4, 8])
+def test_fp8_step_is_race_free(n, stages):
+    items = [(n, 0)] * 4 + [(n, 1)] * 3
+    for seed in range(8):
+        P.fp8_step(items, stages, seed)
+
+
+def test_fp8_without_the_t_ready_gate_is_caught():
+    """The first FP8 form let a converter warp with no slot in a tile (group 1
+    at n = 8) arrive on t_ready for later tiles at once, completing a tile's
+    phase before the other group wrote the A operand; it showed only with
+    several tiles per CTA."""
+    with pytest.raises(P.ProtocolError):
+        for seed in range(10):
+            P.fp8_step([(8, 0)] * 4, 4, seed, gate_t_ready=False)
+    for seed in range(10):                       # one tile per CTA hid it
+        P.fp8_step([(8, 0)], 4, seed, gate_t_ready=False)
