@@ -413,3 +413,152 @@ def fp8_step(items, stages, seed, gate_t_ready=True):
             M.add_role(f"epi{q}{dh}", epilogue(q, dh))
     M.run()
     return M.steps
+
+
+def pair_step(keys, stages, seed, n=64):
+    """The CTA-pair kernel (cta_group::2, bf16 state operand and split table):
+    each entry of `keys` is one pair of tiles (one per CTA) of the same table
+    key.  Per CTA: a producer (its half of the table and its own tile's
+    staging), eight converter warps and eight epilogue warps as in bf16_step.
+    The even CTA's MMA thread issues M = 256 MMAs reading both CTAs' A chunks
+    and table halves and writing both accumulators; its commits arrive on the
+    barriers of both CTAs.  The odd CTA's converters arrive on a local
+    barrier that one thread forwards to the even CTA's t_ready (count 9); the
+    odd producer forwards the completion of its table half to the even z_full
+    (count 2)."""
+    M = Machine(seed)
+    T = len(keys)
+    G, C, ring = _groups(n), _chunks(n), stages // 2
+    R = (0, 1)
+    st_full = {(r, s): Barrier(f"st_full[{r}][{s}]", 1) for r in R for s in range(stages)}
+    st_empty = {(r, s): Barrier(f"st_empty[{r}][{s}]", 4) for r in R for s in range(stages)}
+    a_empty = {(r, c): Barrier(f"a_empty[{r}][{c}]", 1) for r in R for c in range(C)}
+    acc_full = {(r, b): Barrier(f"acc_full[{r}][{b}]", 1) for r in R for b in range(2)}
+    acc_empty = {(r, b): Barrier(f"acc_empty[{r}][{b}]", 8) for r in R for b in range(2)}
+    z_free = {r: Barrier(f"z_free[{r}]", 1) for r in R}
+    t_ready = [Barrier(f"t_ready[{b}]", 9) for b in range(2)]          # even CTA
+    t_local = [Barrier(f"t_local[{b}]", 8) for b in range(2)]          # odd CTA
+    z_full = {0: Barrier("z_full[0]", 2), 1: Barrier("z_full[1]", 1)}
+    stage = {(r, s): None for r in R for s in range(stages)}
+    A, acc, z = {}, {}, {0: None, 1: None}
+
+    def mcast(bars):
+        for bar in bars:
+            M.commit(bar)
+
+    def producer(r):
+        who = f"producer{r}"
+        prev, zr, zl, gq = None, 0, 0, [0, 0]
+        for i, key in enumerate(keys):
+            if key != prev:
+                if i > 0:
+                    yield Wait(z_free[r], zr, who)
+                    zr += 1
+                z_full[r].expect_tx(1)
+
+                def land_z(key=key, r=r):
+                    z[r] = key
+                    z_full[r].complete_tx(1)
+                M.tma_load(land_z)
+                if r == 1:
+                    yield Wait(z_full[1], zl, who)
+                    z_full[0].arrive()                      # forward to the even CTA
+                zl += 1
+                prev = key
+            for j in range(G):
+                gr = j & 1
+                local = gq[gr]
+                gq[gr] += 1
+                s = gr * ring + local % ring
+                yield Wait(st_empty[(r, s)], local // ring - 1, who)
+                st_full[(r, s)].expect_tx(1)
+
+                def land(r=r, s=s, tag=(i, j)):
+                    stage[(r, s)] = tag
+                    st_full[(r, s)].complete_tx(1)
+                M.tma_load(land)
+
+    def converter(r, q, grp):
+        who = f"converter{r}(q{q},g{grp})"
+        gq = 0
+        for i, key in enumerate(keys):
+            b = i & 1
+            yield Wait(acc_empty[(r, b)], (i >> 1) - 1, who)
+            for c in range(C):
+                j = 2 * c + grp
+                local = gq
+                gq += 1
+                s = grp * ring + local % ring
+                yield Wait(st_full[(r, s)], local // ring, who)
+                if stage[(r, s)] != (i, j):
+                    raise ProtocolError(f"{who} tile {i} slot {j}: staging holds {stage[(r, s)]}")
+                cell = acc.get((r, b, j, q))
+                if cell is not None and cell[0] != "free":
+                    raise ProtocolError(f"{who} tile {i}: accumulator {b} slot {j} still {cell[0]}")
+                acc[(r, b, j, q)] = ["init", i, 0]
+                st_empty[(r, s)].arrive()
+                yield Wait(a_empty[(r, c)], i - 1, who)
+                A[(r, c, grp, q)] = i
+            (t_ready[b] if r == 0 else t_local[b]).arrive()
+
+    def forwarder():
+        for i, _ in enumerate(keys):
+            b = i & 1
+            yield Wait(t_local[b], i >> 1, "forwarder")
+            t_ready[b].arrive()
+
+    def mma():
+        prev, zl = None, 0
+        for i, key in enumerate(keys):
+            b = i & 1
+            if key != prev:
+                yield Wait(z_full[0], zl, "mma")
+                zl += 1
+                prev = key
+            yield Wait(t_ready[b], i >> 1, "mma")
+            for c in range(C):
+                def done(i=i, b=b, c=c, key=key):
+                    for r in R:
+                        if z[r] != key:
+                            raise ProtocolError(f"MMA pair {i}: CTA {r} holds table {z[r]}, {key} needed")
+                        for grp in (0, 1):
+                            for q in range(4):
+                                if A.get((r, c, grp, q)) != i:
+                                    raise ProtocolError(f"MMA pair {i} chunk {c}: CTA {r} A part ({grp},{q}) holds "
+                                                        f"{A.get((r, c, grp, q))}")
+                        for j in range(G):
+                            for q in range(4):
+                                cell = acc.get((r, b, j, q))
+                                if cell is None or cell[1] != i or cell[0] not in ("init", "partial"):
+                                    raise ProtocolError(f"MMA pair {i}: CTA {r} accumulator slot {j} is {cell}")
+                                cell[0] = "done" if c == C - 1 else "partial"
+                M.issue_mma(done)
+                mcast([a_empty[(0, c)], a_empty[(1, c)]])
+            mcast([acc_full[(0, b)], acc_full[(1, b)]])
+            if i + 1 < T and keys[i + 1] != key:
+                mcast([z_free[0], z_free[1]])
+
+    def epilogue(r, q, dh):
+        who = f"epilogue{r}(q{q},h{dh})"
+        dn = n // 2
+        for i, _ in enumerate(keys):
+            b = i & 1
+            yield Wait(acc_full[(r, b)], i >> 1, who)
+            for j in sorted({d // 8 for d in range(dh * dn, dh * dn + dn)}):
+                cell = acc.get((r, b, j, q))
+                if cell is None or cell[0] != "done" or cell[1] != i:
+                    raise ProtocolError(f"{who} tile {i}: accumulator {b} slot {j} is {cell}")
+                cell[0] = "free"
+            acc_empty[(r, b)].arrive()
+
+    M.add_role("mma", mma())
+    M.add_role("forwarder", forwarder())
+    for r in R:
+        M.add_role(f"producer{r}", producer(r))
+        for q in range(4):
+            for grp in range(2):
+                M.add_role(f"conv{r}{q}{grp}", converter(r, q, grp))
+            for dh in range(2):
+                M.add_role(f"epi{r}{q}{dh}", epilogue(r, q, dh))
+    M.run()
+    return M.steps

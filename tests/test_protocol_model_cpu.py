@@ -58,3 +58,12 @@ def test_fp8_without_the_t_ready_gate_is_caught():
             P.fp8_step([(8, 0)] * 4, 4, seed, gate_t_ready=False)
     for seed in range(10):                       # one tile per CTA hid it
         P.fp8_step([(8, 0)], 4, seed, gate_t_ready=False)
+
+
+@pytest.mark.parametrize("stages", [2, 4])
+def test_cta_pair_step_is_race_free(stages):
+    """The headline CTA-pair kernel: forwarded readiness of the odd CTA
+    (t_local -> t_ready, count 9), forwarded table half (z_full count 2),
+    multicast commits to both CTAs' barriers."""
+    for seed in range(10):
+        P.pair_step([0, 0, 0, 1, 1, 0, 0], stages, seed)
