@@ -211,6 +211,15 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _leg(fn, *args):
+    """A secondary measurement: its result, or {"error": ...} when it fails, so
+    that one failing leg does not cost the whole line."""
+    try:
+        return fn(*args)
+    except Exception as e:  # noqa: BLE001 -- recorded in the JSON line
+        return {"error": f"{type(e).__name__}: {e}"[:500]}
+
+
 def _time_steps(torch, s, stream, steps):
     """Per-launch CUDA-event times (ms) of `steps` single steps on `stream`."""
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
@@ -451,23 +460,6 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    # comparison form first (float32 on the CUDA cores), then the headline form
-    compare = {}
-    others = [] if args.no_compare else [p for p in ("fp32", "bf16", "fp8") if p != args.precision]
-    for prec in others:
-        sc = SV.solver_for(w, prec)
-        sc.step(3)
-        barrier()
-        per, tot = _time_steps(torch, sc, stream, max(3, args.steps // (5 if prec == "fp32" else 1)))
-        sc.close()
-        compare[prec] = {"value": ws * sdu_per_step * len(per) / (tot * 1e-3), "unit": UNIT,
-                         "ms_per_step": tot / len(per),
-                         "roofline": _roofline(prec, n, sdu_per_step, statistics.mean(per) * 1e-3, peaks, src)}
-        if prec != "fp32":
-            compare[prec]["roofline"]["kernel"] = KERNEL[prec]
-        del sc
-        torch.cuda.empty_cache()
-
     s = SV.solver_for(w, args.precision)
     s.step(args.warmup)
     barrier()
@@ -499,6 +491,29 @@ def run_ours(args):
     s.close()
     del s, host_state
     torch.cuda.empty_cache()
+
+    # comparison forms after the headline, each on its own context; a form
+    # that fails records its error instead of ending the run
+    compare = {}
+    others = [] if args.no_compare else [p for p in ("fp32", "bf16", "fp8") if p != args.precision]
+    for prec in others:
+        def one(prec=prec):
+            sc = SV.solver_for(w, prec)
+            try:
+                sc.step(3)
+                barrier()
+                per, tot = _time_steps(torch, sc, stream, max(3, args.steps // (5 if prec == "fp32" else 1)))
+                sc.total_intensity()                 # surfaces a device-side error of the form
+            finally:
+                sc.close()
+            out = {"value": ws * sdu_per_step * len(per) / (tot * 1e-3), "unit": UNIT,
+                   "ms_per_step": tot / len(per),
+                   "roofline": _roofline(prec, n, sdu_per_step, statistics.mean(per) * 1e-3, peaks, src)}
+            if prec != "fp32":
+                out["roofline"]["kernel"] = KERNEL[prec]
+            return out
+        compare[prec] = _leg(one)
+        torch.cuda.empty_cache()
 
     roof = _roofline(args.precision, n, sdu_per_step, statistics.mean(per_launch) * 1e-3, peaks, src)
     if args.precision != "fp32":
@@ -533,20 +548,21 @@ def run_ours(args):
             "adjoint_over_forward": None,
         }
         if ws == 1 and args.bilinear_steps > 0 and args.nx == 2048 and args.nz == 2048:
-            line["bilinear"] = bilinear_throughput(args.precision, args.bilinear_steps, t_max / args.steps, peaks, src)
+            line["bilinear"] = _leg(bilinear_throughput, args.precision, args.bilinear_steps, t_max / args.steps, peaks,
+                                    src)
         if ws == 1 and args.batch_steps > 0:
-            line["batch"] = batch_throughput(args.batch_steps)
+            line["batch"] = _leg(batch_throughput, args.batch_steps)
         if ws == 1 and args.adjoint_steps > 0:
-            adj = adjoint_ratio(args.adjoint_steps, args.precision)
+            adj = _leg(adjoint_ratio, args.adjoint_steps, args.precision)
             line["adjoint"] = adj
-            line["adjoint_over_forward"] = adj["adjoint_over_forward"]["fp32"]
+            line["adjoint_over_forward"] = adj["adjoint_over_forward"]["fp32"] if "error" not in adj else None
         if ws == 1 and args.fp32_class_steps > 0:
-            line["fp32_class"] = fp32_class(args.fp32_class_steps, peaks, src)
+            line["fp32_class"] = _leg(fp32_class, args.fp32_class_steps, peaks, src)
         if ws == 1 and args.accuracy_steps > 0:
             precs = [args.precision] + [p for p in ("bf16", "fp8", "fp32") if p != args.precision]
-            line["accuracy"] = accuracy(precs, args.accuracy_steps)
+            line["accuracy"] = _leg(accuracy, precs, args.accuracy_steps)
         if ws == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args.steps)
+            line["cpu_baseline"] = _leg(cpu_baseline, args.steps)
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

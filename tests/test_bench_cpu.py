@@ -60,3 +60,10 @@ def test_traffic_lookup():
     got = bench._measured_traffic("k_step_tc_pair", 2 * rec["captured_sites"])
     if got is not None:
         assert got == pytest.approx(2 * (rec["dram_bytes_read"] + rec["dram_bytes_write"]))
+
+
+def test_failing_leg_is_recorded_not_raised():
+    def boom(x):
+        raise RuntimeError(f"leg failed on {x}")
+    assert bench._leg(lambda a, b: a + b, 2, 3) == 5
+    assert bench._leg(boom, 7) == {"error": "RuntimeError: leg failed on 7"}
