@@ -143,7 +143,8 @@ def cpu_baseline(steps: int, seconds: float = 12.0):
             break
     dt = time.perf_counter() - t0
     sdu = w.sites * w.n * k
-    out = {"value": sdu / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    out = {"value": sdu / dt, "unit": UNIT, "cores": oracle.num_threads(), "cpu_model": _cpu_model(),
+           "kind": "oracle",
            "sample": f"FP64 oracle, {k} steps of the 256x256 crop [896,1152)^2 of the same "
                      f"medium (n=64), {dt:.1f} s"}
     out["single_thread"] = _cpu_single_thread(seconds / 2)
@@ -204,7 +205,7 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": "lattice2048_n64 (oracle on the 256x256 crop, same medium)",
                    "nx": 2048, "nz": 2048, "n_dirs": 64, "sample_sites": w.sites},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "cpu_model": _cpu_model(),
                          "kind": "oracle", "sample": f"{args.steps} steps of the 256x256 crop"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -213,11 +214,28 @@ def run_reference(args):
 
 def _leg(fn, *args):
     """A secondary measurement: its result, or {"error": ...} when it fails, so
-    that one failing leg does not cost the whole line."""
+    that one failing leg does not cost the whole line.  With several ranks a
+    failure is not swallowed: a leg that raised on one rank only would leave
+    the other ranks waiting in the leg's next collective, so the exception
+    ends the rank and the launcher ends the job."""
+    if _dist()[0] > 1:
+        return fn(*args)
     try:
         return fn(*args)
     except Exception as e:  # noqa: BLE001 -- recorded in the JSON line
         return {"error": f"{type(e).__name__}: {e}"[:500]}
+
+
+def _cpu_model() -> str:
+    """Host CPU model name (first 'model name' of /proc/cpuinfo)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def _time_steps(torch, s, stream, steps):
@@ -589,7 +607,7 @@ def main():
                     help="steps of the 1024x256 adjoint timing (0 = skip)")
     ap.add_argument("--nx", type=int, default=2048, help="lattice width (profiling of smaller cases)")
     ap.add_argument("--nz", type=int, default=2048, help="lattice height (profiling of smaller cases)")
-    ap.add_argument("--accuracy-steps", type=int, default=200,
+    ap.add_argument("--accuracy-steps", type=int, default=1000,
                     help="steps of the 256x256 crop compared with the oracle (0 = skip)")
     args = ap.parse_args()
     if args.warmup < 3:

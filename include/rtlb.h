@@ -69,14 +69,22 @@ typedef enum { RTLB_BC_VACUUM = 0, RTLB_BC_PERIODIC = 1, RTLB_BC_INFLOW = 2 } rt
  *              table scales of every phase class stay in tensor memory, which
  *              bounds the classes (n = 64: 12); rtlb_set_medium returns
  *              RTLB_E_UNSUPPORTED beyond that.
- * Tensor-core forms need n in {8, 16, 32, 64}; rtlb_create returns
- * RTLB_E_UNSUPPORTED otherwise. */
+ *  TF32X3   -- tcgen05 kind::tf32, both operands split into tf32 hi + lo
+ *              (round to nearest; about 22 significand bits each), three MMAs
+ *              (hi.hi + hi.lo + lo.hi), float32 accumulation: the accuracy of
+ *              the FP32 form on the tensor cores.  The split state operand is
+ *              kept in tensor memory.  n in {8, 16, 32} (the split tf32 table
+ *              of n = 64 is 512 KB, more than any CTA's shared memory).
+ * Tensor-core forms need n in {8, 16, 32, 64} (TF32X3: {8, 16, 32});
+ * rtlb_create returns RTLB_E_UNSUPPORTED otherwise.  Tiles of 128 sites that
+ * mix phase classes run on the FP32 CUDA-core kernel in every form. */
 typedef enum {
     RTLB_PREC_FP32 = 0,
     RTLB_PREC_BF16 = 1,
     RTLB_PREC_BF16X3 = 2,
     RTLB_PREC_BF16X2 = 3,
-    RTLB_PREC_FP8 = 4
+    RTLB_PREC_FP8 = 4,
+    RTLB_PREC_TF32X3 = 5
 } rtlb_precision;
 
 /* Survival of unscattered light over one step: LINEAR = 1 - k_scat dt (Eq. 11
@@ -187,6 +195,13 @@ rtlb_status rtlb_last_residual(rtlb_ctx *ctx, double *residual, void *stream);
  * across that side is nonzero and points out), zero for the others. */
 rtlb_status rtlb_radiance_out(rtlb_ctx *ctx, int32_t side, float *out, void *stream);
 
+/* Degree of polarization of the radiance leaving through one side (Sec. 3.2.1,
+ * Eq. 36): out[len][n] float32 (host or device) = sqrt(Q^2 + U^2 + V^2) / I of
+ * the entries rtlb_radiance_out returns, evaluated in float64 and rounded once;
+ * zero for the directions that do not leave through that side and where
+ * I <= 0.  Errors as rtlb_radiance_out. */
+rtlb_status rtlb_dop_out(rtlb_ctx *ctx, int32_t side, float *out, void *stream);
+
 /* Reverse-mode gradients (adjoint of Eq. 2's step: transposed phase-matrix
  * scattering and reversed streaming) of a loss L whose gradient with respect to
  * the top radiance radiance_out(TOP) after nsteps steps is dL_dout[nx][n][4]
@@ -279,16 +294,36 @@ void rtlb_batch_destroy(rtlb_batch *batch);
  * elementwise), 16-byte aligned, count a multiple of 4.  out: device, 3
  * doubles, 8-byte aligned: {max|S_new - S_old|, max|S_new|, number of
  * non-finite entries of S_new}; the residual is out[0] / out[1].
- * count > RTLB_NOALLOC_MAX_COUNT returns RTLB_E_SHAPE; bad pointers, alignment
- * or count % 4 != 0 return RTLB_E_ARG.  Never calls cudaMalloc / cudaFree.
- * The first call on a device (with that device current) looks up the array's
- * device address once; make that first call before any stream capture.  All
- * calls share the one array and each overwrites the slots it reads, so two
- * calls that overlap on the GPU (different streams, no ordering) race.
- * Stream-ordered on `stream`. */
+ * count > RTLB_NOALLOC_MAX_COUNT returns RTLB_E_SHAPE; null pointers, pointers
+ * that are not device (or managed) memory of the current device, bad
+ * alignment or count % 4 != 0 return RTLB_E_ARG.  Never calls cudaMalloc /
+ * cudaFree.  The first call in a CUDA context (normally: the first on each
+ * device, with that device current) looks up the array's device address and
+ * may make the driver load the library's device code, which can allocate
+ * inside the driver; make that first call before any stream capture and
+ * before any use from an allocator hook or host callback.  After a device
+ * reset the next call looks the address up again.  All calls share the one
+ * array and each overwrites the slots it reads, so two calls that overlap on
+ * the GPU (different streams, no ordering) race.  Stream-ordered on `stream`. */
 #define RTLB_NOALLOC_MAX_COUNT ((size_t)1 << 30)
 rtlb_status rtlb_residual_noalloc(const float *S_old, const float *S_new, size_t count,
                                   double *out, void *stream);
+
+/* ---- test hook of the bounded device waits (the paper has no counterpart) ----
+ *
+ * Every wait inside the tensor-core kernels gives up after about 2 s; the CTA
+ * then drains its in-flight loads and MMAs, frees its tensor memory and
+ * returns, and the next call that reads the device error flag
+ * (rtlb_get_state, rtlb_last_residual, rtlb_total_intensity, ...) returns
+ * RTLB_E_TIMEOUT and clears it.  This arms that path for a test: the next
+ * tensor-core step launch of this context leaves the load of one state chunk
+ * in its first CTA unissued, so that CTA's converter warps wait for data that
+ * never comes.  Nothing is in flight for the skipped chunk, so the launch ends
+ * normally after the wait runs out; the state after that step is undefined
+ * (set it again) and the context stays usable.  Covers the BF16, BF16X3 and
+ * BF16X2 kernels (single CTA and CTA pair); RTLB_E_UNSUPPORTED for FP32 and
+ * FP8, RTLB_E_STATE before rtlb_set_medium.  Disarmed after one launch. */
+rtlb_status rtlb_test_stall_next_step(rtlb_ctx *ctx);
 
 /* ---- host helpers (float64, no GPU needed) ---- */
 
@@ -325,6 +360,14 @@ rtlb_status rtlb_phase_conserve_intensity(int32_t n, double *Z_inout);
  * may be NULL) receives the derivative of the normalized table in g. */
 rtlb_status rtlb_phase_hg(const rtlb_directions *dirs, double g, double pol_amp,
                           double *Z_out, double *dZdg_out);
+
+/* Gradient of a loss with respect to the asymmetry g of the table above
+ * (Eq. 13-17 differentiated in g): dL_dg = sum over entries of
+ * grad_Z[4n][4n] * dZ/dg, where grad_Z (host float64) is dL/dZ of that class
+ * as rtlb_adjoint returns it; summed in entry order, so identical inputs give
+ * identical bits.  Errors as rtlb_phase_hg; grad_Z and dL_dg must be non-NULL. */
+rtlb_status rtlb_phase_hg_grad(const rtlb_directions *dirs, double g, double pol_amp,
+                               const double *grad_Z, double *dL_dg);
 
 /* Mixture table m * Rayleigh + (1 - m) * HG(g, pol_amp), both normalized as
  * above (so the mixture's weights also sum to one); 0 <= m <= 1. */

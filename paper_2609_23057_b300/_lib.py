@@ -30,6 +30,7 @@ EXPORTS = [
     "rtlb_residual_noalloc", "rtlb_adjoint", "rtlb_phase_conserve_intensity",
     "rtlb_batch_create", "rtlb_batch_configure", "rtlb_batch_step", "rtlb_batch_check",
     "rtlb_batch_last_error", "rtlb_batch_destroy", "rtlb_stream_taps", "rtlb_release_workspace",
+    "rtlb_dop_out", "rtlb_phase_hg_grad", "rtlb_test_stall_next_step",
 ]
 
 
@@ -98,6 +99,9 @@ def lib() -> C.CDLL:
     L.rtlb_batch_last_error.restype = C.c_char_p
     L.rtlb_batch_destroy.argtypes = [vp]
     L.rtlb_batch_destroy.restype = None
+    L.rtlb_dop_out.argtypes = [vp, i32, vp, vp]
+    L.rtlb_phase_hg_grad.argtypes = [C.POINTER(Directions), C.c_double, C.c_double, vp, dp]
+    L.rtlb_test_stall_next_step.argtypes = [vp]
     for name in EXPORTS:
         f = getattr(L, name)
         if f.restype is C.c_int:     # ctypes default: status codes are int32

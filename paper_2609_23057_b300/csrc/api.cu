@@ -228,7 +228,7 @@ rtlb_status rtlb_create(const rtlb_grid *grid, const rtlb_directions *dirs, cons
     if (grid->nx < 1 || grid->nz < 1 || grid->nx > 65535 || grid->nz > 65535) return RTLB_E_SHAPE;
     rtlb_options o{};
     if (opts) o = *opts;
-    if (o.precision < RTLB_PREC_FP32 || o.precision > RTLB_PREC_FP8 || o.survival < 0 || o.survival > 1 ||
+    if (o.precision < RTLB_PREC_FP32 || o.precision > RTLB_PREC_TF32X3 || o.survival < 0 || o.survival > 1 ||
         o.absorption < 0 || o.absorption > 1)
         return RTLB_E_ARG;
     std::vector<double> mu, phi, tap_w;
@@ -897,6 +897,33 @@ rtlb_status rtlb_radiance_out(rtlb_ctx *c, int32_t side, float *out, void *strea
     return RTLB_OK;
 }
 
+rtlb_status rtlb_dop_out(rtlb_ctx *c, int32_t side, float *out, void *stream)
+{
+    if (!c || !out) return fail(c, RTLB_E_ARG, "null argument");
+    if (side < 0 || side > 3) return fail(c, RTLB_E_ARG, "side must be 0..3");
+    cudaStream_t s = S(stream);
+    const int len = (side == RTLB_SIDE_TOP || side == RTLB_SIDE_BOTTOM) ? c->nx : c->nz;
+    const size_t bytes = (size_t)len * c->n * sizeof(float);
+    if (is_device_ptr(out)) {
+        CK(c, launch_dop_out(c->S[c->cur], out, c->nx, c->nz, c->n, c->d_dir, side, s), "dop_out");
+        return RTLB_OK;
+    }
+    const size_t need = (size_t)(c->nx > c->nz ? c->nx : c->nz) * c->n * 4;
+    if (!c->d_rad) CK(c, cudaMalloc(&c->d_rad, need * sizeof(float)), "radiance staging");
+    CK(c, launch_dop_out(c->S[c->cur], c->d_rad, c->nx, c->nz, c->n, c->d_dir, side, s), "dop_out");
+    CK(c, cudaMemcpyAsync(out, c->d_rad, bytes, cudaMemcpyDeviceToHost, s), "dop download");
+    CK(c, cudaStreamSynchronize(s), "dop sync");
+    return RTLB_OK;
+}
+
+rtlb_status rtlb_test_stall_next_step(rtlb_ctx *c)
+{
+    if (!c) return RTLB_E_ARG;
+    if (!c->medium_set) return fail(c, RTLB_E_STATE, "rtlb_set_medium must come before the stall hook");
+    if (c->opt.precision == RTLB_PREC_FP32) return fail(c, RTLB_E_UNSUPPORTED, "the stall hook needs a tensor-core precision");
+    return tc_arm_stall(c);
+}
+
 rtlb_status rtlb_total_intensity(rtlb_ctx *c, double *total, void *stream)
 {
     if (!c || !total) return fail(c, RTLB_E_ARG, "null argument");
@@ -972,6 +999,26 @@ rtlb_status rtlb_phase_hg(const rtlb_directions *dirs, double g, double pol_amp,
     rtlb_status st = build_dirs(dirs, RTLB_STREAM_BILINEAR, RTLB_PLANE_XZ, mu, phi, x, z, to, tw, nullptr);
     if (st != RTLB_OK) return st;
     phase_hg(mu, phi, g, pol_amp, Z_out, dZdg_out);
+    return RTLB_OK;
+}
+
+rtlb_status rtlb_phase_hg_grad(const rtlb_directions *dirs, double g, double pol_amp, const double *grad_Z,
+                               double *dL_dg)
+{
+    if (!grad_Z || !dL_dg) return RTLB_E_ARG;
+    if (!(g > -1.0 && g < 1.0) || !(std::fabs(pol_amp) <= 1.0)) return RTLB_E_RANGE;
+    std::vector<double> mu, phi, tw;
+    std::vector<int> x, z, to;
+    rtlb_status st = build_dirs(dirs, RTLB_STREAM_BILINEAR, RTLB_PLANE_XZ, mu, phi, x, z, to, tw, nullptr);
+    if (st != RTLB_OK) return st;
+    const size_t len = 16 * mu.size() * mu.size();
+    std::vector<double> Z(len), dZ(len);
+    phase_hg(mu, phi, g, pol_amp, Z.data(), dZ.data());
+    // chain rule through the table: dL/dg = sum over entries of dL/dZ * dZ/dg,
+    // summed in entry order (deterministic)
+    double acc = 0.0;
+    for (size_t j = 0; j < len; ++j) acc += grad_Z[j] * dZ[j];
+    *dL_dg = acc;
     return RTLB_OK;
 }
 

@@ -253,6 +253,38 @@ __global__ void k_radiance_out(const float4 *__restrict__ dm, float4 *__restrict
     }
 }
 
+// Degree of polarization (Sec. 3.2.1, Eq. 36: sqrt(Q^2 + U^2 + V^2) / I) of
+// the radiance leaving through `side`, out[p][d]; zero for directions that
+// do not leave through it and where I <= 0.  Evaluated in float64 from the
+// float32 Stokes vector, rounded once.
+__global__ void k_dop_out(const float4 *__restrict__ dm, float *__restrict__ out, int nx, int nz, int n,
+                          const int *__restrict__ dir, int side)
+{
+    const int len = (side == RTLB_SIDE_TOP || side == RTLB_SIDE_BOTTOM) ? nx : nz;
+    const size_t nsites = (size_t)nx * nz;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < len * n; j += gridDim.x * blockDim.x) {
+        const int p = j / n, d = j % n;
+        const int cx = dir[d], cz = dir[n + d];
+        int x, z;
+        bool leaves;
+        switch (side) {
+        case RTLB_SIDE_TOP: x = p; z = nz - 1; leaves = cz == 1; break;
+        case RTLB_SIDE_BOTTOM: x = p; z = 0; leaves = cz == -1; break;
+        case RTLB_SIDE_LEFT: x = 0; z = p; leaves = cx == -1; break;
+        default: x = nx - 1; z = p; leaves = cx == 1; break;
+        }
+        float v = 0.f;
+        if (leaves) {
+            const float4 st = dm[(size_t)d * nsites + (size_t)z * nx + x];
+            if (st.x > 0.f) {
+                const double q = st.y, u = st.z, w = st.w;
+                v = (float)(sqrt(q * q + u * u + w * w) / (double)st.x);
+            }
+        }
+        out[j] = v;
+    }
+}
+
 __global__ void k_fill(float *p, size_t count, float v)
 {
     for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < count;
@@ -316,6 +348,15 @@ cudaError_t launch_radiance_out(const float *dm, float *out, int nx, int nz, int
     const int len = (side == RTLB_SIDE_TOP || side == RTLB_SIDE_BOTTOM) ? nx : nz;
     k_radiance_out<<<grid_for((size_t)len * n), kThreads, 0, s>>>(
         reinterpret_cast<const float4 *>(dm), reinterpret_cast<float4 *>(out), nx, nz, n, dir, side);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dop_out(const float *dm, float *out, int nx, int nz, int n, const int *dir, int side,
+                           cudaStream_t s)
+{
+    const int len = (side == RTLB_SIDE_TOP || side == RTLB_SIDE_BOTTOM) ? nx : nz;
+    k_dop_out<<<grid_for((size_t)len * n), kThreads, 0, s>>>(reinterpret_cast<const float4 *>(dm), out, nx, nz, n,
+                                                             dir, side);
     return cudaGetLastError();
 }
 

@@ -14,8 +14,14 @@
 // so at most kMaxBlocks * kChunkVec * 4 = 2^30 floats fit in one call.
 //
 // Host code cannot use the array's name as a device address (it is a
-// host-side stand-in); the first call on each device, with that device
-// current, looks the address up with cudaGetSymbolAddress and caches it.
+// host-side stand-in); the first call in each CUDA context (one per device in
+// the usual runtime use), with that device current, looks the address up
+// with cudaGetSymbolAddress and caches it under the context.  A device reset
+// creates a new context, so the next call looks the address up again instead
+// of reusing one from the freed context.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <mutex>
 
@@ -31,7 +37,11 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_noalloc_partials[3 * kMaxBlocks];
 
 std::mutex g_mutex;
-double *g_partials_addr[kMaxDevices] = {};
+struct CachedAddress {
+    CUcontext ctx = nullptr;
+    double *addr = nullptr;
+};
+CachedAddress g_partials_addr[kMaxDevices];
 
 __device__ __forceinline__ double wmax(double v)
 {
@@ -116,7 +126,23 @@ __global__ void k_residual_fold(const double *__restrict__ partials, int nblocks
     }
 }
 
-// Device address of the fixed scratch array on the current device.
+// The driver's cuCtxGetCurrent, through the runtime's entry-point query (the
+// library links only the runtime).
+PFN_cuCtxGetCurrent_v4000 ctx_get_current()
+{
+    static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *ptr = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &ptr, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(ptr);
+    }
+    return fn;
+}
+
+// Device address of the fixed scratch array in the current device's current
+// context, looked up once per context.
 rtlb_status partials_address(double **addr)
 {
     int dev = 0;
@@ -124,17 +150,35 @@ rtlb_status partials_address(double **addr)
         cudaGetLastError();
         return RTLB_E_CUDA;
     }
+    auto get_ctx = ctx_get_current();
+    CUcontext ctx = nullptr;
+    if (!get_ctx || get_ctx(&ctx) != CUDA_SUCCESS || !ctx) return RTLB_E_CUDA;
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_partials_addr[dev]) {
+    CachedAddress &c = g_partials_addr[dev];
+    if (c.ctx != ctx || !c.addr) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) {
             cudaGetLastError();
             return RTLB_E_CUDA;
         }
-        g_partials_addr[dev] = static_cast<double *>(p);
+        c.ctx = ctx;
+        c.addr = static_cast<double *>(p);
     }
-    *addr = g_partials_addr[dev];
+    *addr = c.addr;
     return RTLB_OK;
+}
+
+// True when p is device (or managed) memory of the current device: a host
+// pointer handed to the kernels would be read as a device address.
+bool on_current_device(const void *p)
+{
+    int dev = 0;
+    cudaPointerAttributes a;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace
@@ -147,6 +191,7 @@ extern "C" rtlb_status rtlb_residual_noalloc(const float *S_old, const float *S_
         (reinterpret_cast<uintptr_t>(out) & 7u))
         return RTLB_E_ARG;
     if (count > RTLB_NOALLOC_MAX_COUNT) return RTLB_E_SHAPE;
+    if (!on_current_device(S_old) || !on_current_device(S_new) || !on_current_device(out)) return RTLB_E_ARG;
     double *partials = nullptr;
     const rtlb_status st = partials_address(&partials);
     if (st != RTLB_OK) return st;

@@ -97,6 +97,8 @@ cudaError_t launch_total_I(const float *dm, size_t nvec, double *partials, int n
                            double *out, cudaStream_t s);
 cudaError_t launch_radiance_out(const float *dm, float *out, int nx, int nz, int n,
                                 const int *dir, int side, cudaStream_t s);
+cudaError_t launch_dop_out(const float *dm, float *out, int nx, int nz, int n, const int *dir, int side,
+                           cudaStream_t s);
 cudaError_t launch_fill(float *p, size_t count, float v, cudaStream_t s);
 // bilinear streaming (k_stream.cu): S(x, d) = sum_k w[d][k] P(x - o[d][k], d) with
 // the ghost rule of the boundary kinds; taps_o = [n][8] (ox0..3, oz0..3), taps_w = [n][4]

@@ -53,12 +53,14 @@ using namespace tccommon;
 
 struct TcState {
     int N4 = 0, KP = 0, C = 0, n_phase = 0;
-    int mode = 1;                    // 1 bf16, 2 bf16 + table lo, 3 hi+lo both, 4 e4m3 block-scaled
+    int mode = 1;                    // 1 bf16, 2 bf16 + table lo, 3 hi+lo both, 4 e4m3 block-scaled, 5 3xTF32
     bool pair = false;               // CTA-pair kernel (table rows split over two CTAs)
     __nv_bfloat16 *d_Zhi = nullptr;  // [n_phase][N4][KP]
     __nv_bfloat16 *d_Zlo = nullptr;
     uint8_t *d_Z8 = nullptr;         // FP8: [n_phase][N4][KP8] e4m3
     uint8_t *d_sfb = nullptr;        // FP8: [n_phase][N4][N4 / 32] UE8M0 block scales of the table
+    float *d_Zt_hi = nullptr;        // TF32X3: [n_phase][N4][N4] tf32 hi part (float32 container)
+    float *d_Zt_lo = nullptr;        // TF32X3: tf32 lo part
     int *d_pure = nullptr;           // tile | class << 24, sorted by class (pairs: 2 per entry)
     int n_pure = 0;
     int *d_mixed = nullptr;          // tile indices
@@ -72,6 +74,7 @@ struct TcState {
     int sm_count = 0;
     int stages = 0;
     size_t smem = 0;
+    int stall_next = 0;              // test hook armed for the next launch (TcParams::stall)
 };
 
 // MODE 1: bf16 operands; 2: bf16 state operand, table as bf16 hi + lo (two
@@ -149,6 +152,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == kProdWarp) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
+            const bool stall = p.stall != 0 && blockIdx.x == 0;
             int prev_cls = -1;
             uint32_t gq[2] = {0, 0}, zr = 0;
             bool ok = true;
@@ -184,6 +188,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ok = mbar_wait(smem_u32(&st_empty[s]), ((local / (uint32_t)(stages / 2)) & 1) ^ 1, abort_flag, p.err,
                                    kErrTimeoutProducer);
                     if (!ok) break;
+                    if (stall && i == 0 && j == 0) continue;   // test hook: this load is never issued
                     const uint32_t fb = smem_u32(&st_full[s]);
                     mbar_expect_tx(fb, kStageBytes);
                     for (int h = 0; h < kTileM / kHalfSites; ++h)
@@ -205,6 +210,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int gr = 0; gr < 2; ++gr)
                 for (uint32_t k = 0; k < (uint32_t)(stages / 2) && k < gq[gr]; ++k) {
                     const uint32_t local = gq[gr] - 1 - k;
+                    if (stall && gr == 0 && local == 0) continue;   // never issued
                     const int s = ring_slot(gr, local, stages / 2);
                     unsigned long long t0 = global_ns();
                     while (!mbar_try(smem_u32(&st_full[s]), (local / (uint32_t)(stages / 2)) & 1) &&
@@ -433,6 +439,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 
     if (warp == kProdWarp) {
         if (lane == 0) {
+            const bool stall = p.stall != 0 && blockIdx.x == 0;   // the even CTA of cluster 0
             int prev_cls = -1;
             uint32_t gq[2] = {0, 0}, zl = 0, zr = 0;
             bool ok = true;
@@ -463,6 +470,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     ok = mbar_wait(smem_u32(&st_empty[s]), ((local / (uint32_t)(stages / 2)) & 1) ^ 1, abort_flag, p.err,
                                    kErrTimeoutProducer);
                     if (!ok) break;
+                    if (stall && i == 0 && j == 0) continue;   // test hook: this load is never issued
                     const uint32_t fb = smem_u32(&st_full[s]);
                     mbar_expect_tx(fb, kStageBytes);
                     for (int h = 0; h < kTileM / kHalfSites; ++h)
@@ -484,6 +492,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             for (int gr = 0; gr < 2; ++gr)
                 for (uint32_t k = 0; k < (uint32_t)(stages / 2) && k < gq[gr]; ++k) {
                     const uint32_t local = gq[gr] - 1 - k;
+                    if (stall && gr == 0 && local == 0) continue;   // never issued
                     const int s = ring_slot(gr, local, stages / 2);
                     unsigned long long t0 = global_ns();
                     while (!mbar_try(smem_u32(&st_full[s]), (local / (uint32_t)(stages / 2)) & 1) &&
@@ -496,7 +505,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             const uint32_t idesc = idesc_bf16(2 * kTileM, N4);
             int prev_cls = -1;
             uint32_t zl = 0;
-            bool ok = true, issued = false;
+            bool ok = true;
             for (int i = 0; i < T && ok; ++i) {
                 const int cls = pair_cls(i);
                 const int b = i & 1;
@@ -521,9 +530,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 }
                 mma_commit_pair(smem_u32(&acc_full[b]), 0x3);
                 if (i + 1 < T && pair_cls(i + 1) != cls) mma_commit_pair(smem_u32(z_free), 0x3);
-                issued = true;
             }
-            if (issued) mma_commit_pair(smem_u32(drain), 0x3);
+            // commit even when nothing was issued (it then arrives at once):
+            // both CTAs wait on `drain` below whenever T > 0, also after an abort
+            if (T > 0) mma_commit_pair(smem_u32(drain), 0x3);
         } else if (lane == 0) {
             // odd CTA: forward each tile's readiness (A rows in shared memory,
             // accumulator initialized in TMEM) to the even CTA.  One
@@ -618,11 +628,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         }
     }
 
-    // every MMA issued into this CTA's TMEM has completed (bounded wait), then
-    // both CTAs leave together and free the pair's TMEM
+    // every MMA issued into this CTA's TMEM has completed (bounded wait, taken
+    // after an abort too: the even CTA commits `drain` once whenever T > 0),
+    // then both CTAs leave together and free the pair's TMEM
     if (warp == kMmaWarp && lane == 0 && T > 0) {
         unsigned long long t0 = global_ns();
-        while (!mbar_try_cluster(smem_u32(drain), 0) && global_ns() - t0 < kTimeoutNs && !*abort_flag) {
+        while (!mbar_try_cluster(smem_u32(drain), 0) && global_ns() - t0 < kTimeoutNs) {
         }
     }
     tc_fence_before();
@@ -674,6 +685,32 @@ bool encode_z_map(CUtensorMap *m, const __nv_bfloat16 *Z, int N4, int KP, int n_
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// tf32 table [n_phase][N4][N4] (float32 containers), boxes of 32 values (one
+// SW128 row of 128 bytes) x N4 rows
+bool encode_zt_map(CUtensorMap *m, const float *Zt, int N4, int n_phase)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)N4, (cuuint64_t)N4, (cuuint64_t)n_phase};
+    cuuint64_t strides[2] = {(cuuint64_t)N4 * 4, (cuuint64_t)N4 * N4 * 4};
+    cuuint32_t box[3] = {32, (cuuint32_t)N4, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(Zt), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Nearest tf32 value (10 stored mantissa bits, ties to even) of a float32.
+float tf32_round(float x)
+{
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    if ((b & 0x7F800000u) != 0x7F800000u) b = (b + 0x0FFFu + ((b >> 13) & 1u)) & 0xFFFFE000u;
+    float r;
+    std::memcpy(&r, &b, 4);
+    return r;
+}
+
 // e4m3 table [n_phase][N4][KP8] bytes, boxes of 128 bytes (one SW128 row) x N4 rows
 bool encode_z8_map(CUtensorMap *m, const uint8_t *Z8, int N4, int KP8, int n_phase)
 {
@@ -708,6 +745,9 @@ void free_tables(TcState *t)
     cudaFree(t->d_Z8);
     cudaFree(t->d_sfb);
     t->d_Z8 = t->d_sfb = nullptr;
+    cudaFree(t->d_Zt_hi);
+    cudaFree(t->d_Zt_lo);
+    t->d_Zt_hi = t->d_Zt_lo = nullptr;
     cudaFree(t->d_fwd);
     cudaFree(t->d_pure);
     cudaFree(t->d_mixed);
@@ -736,6 +776,7 @@ size_t smem_bytes_pair(int N4, int stages)
 int mode_of(int precision)
 {
     if (precision == RTLB_PREC_FP8) return 4;
+    if (precision == RTLB_PREC_TF32X3) return 5;
     return precision == RTLB_PREC_BF16X3 ? 3 : (precision == RTLB_PREC_BF16X2 ? 2 : 1);
 }
 
@@ -748,7 +789,9 @@ int mode_of(int precision)
 int fit_stages(int N4, int mode, bool pair)
 {
     for (int st = RTLB_TC_MAX_STAGES & ~1; st >= 2; st -= 2)
-        if ((pair ? smem_bytes_pair(N4, st) : (mode == 4 ? tc_fp8_smem_bytes(N4, st) : smem_bytes(N4, mode, st))) <=
+        if ((pair ? smem_bytes_pair(N4, st)
+                  : (mode == 4 ? tc_fp8_smem_bytes(N4, st)
+                               : (mode == 5 ? tc_tf32_smem_bytes(N4, st) : smem_bytes(N4, mode, st)))) <=
             (size_t)kSmemLimit)
             return st;
     return 0;
@@ -762,6 +805,7 @@ bool tc_shape_ok(int n, int precision)
 {
     if (!tc_supported(n)) return false;
     const int mode = mode_of(precision);
+    if (mode == 5 && n > 32) return false;      // the split tf32 table of n = 64 (512 KB) fits no CTA
     return fit_stages(4 * n, mode, false) > 0 || (mode == 2 && fit_stages(4 * n, mode, true) > 0);
 }
 
@@ -770,8 +814,9 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
     if (c->opt.precision == RTLB_PREC_FP32) return RTLB_OK;
     const int mode = mode_of(c->opt.precision);
     const bool split = mode == 2 || mode == 3;
-    if (!tc_supported(c->n)) {
-        c->err = "tensor-core forms need n in {8, 16, 32, 64}";
+    const bool tf32 = mode == 5;
+    if (!tc_supported(c->n) || (tf32 && c->n > 32)) {
+        c->err = tf32 ? "the 3xTF32 form needs n in {8, 16, 32}" : "tensor-core forms need n in {8, 16, 32, 64}";
         return RTLB_E_UNSUPPORTED;
     }
     const int N4 = 4 * c->n, KP = ((N4 + 63) / 64) * 64, C = KP / 64;
@@ -814,7 +859,9 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
     std::vector<double> work(tsz);
     const bool fp8 = mode == 4;
     const int KP8 = ((N4 + 127) / 128) * 128, ksteps = N4 / 32;
-    std::vector<__nv_bfloat16> hi(fp8 ? 0 : (size_t)n_phase * psz, __float2bfloat16(0.0f)), lo(hi.size(), __float2bfloat16(0.0f));
+    std::vector<__nv_bfloat16> hi((fp8 || tf32) ? 0 : (size_t)n_phase * psz, __float2bfloat16(0.0f)),
+        lo(hi.size(), __float2bfloat16(0.0f));
+    std::vector<float> thi(tf32 ? (size_t)n_phase * tsz : 0, 0.0f), tlo(thi.size(), 0.0f);
     std::vector<uint8_t> z8(fp8 ? (size_t)n_phase * N4 * KP8 : 0, 0), sfb(fp8 ? (size_t)n_phase * N4 * ksteps : 0, 0);
     if (fp8 && tc_fp8_tmem_columns(N4, n_phase) > 512) {
         c->err = "the FP8 form keeps every class's table scales in tensor memory: too many phase classes for this n";
@@ -857,6 +904,17 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
                         z8[(size_t)ph * N4 * KP8 + (size_t)row * KP8 + 32 * ks + k] =
                             (uint8_t)__nv_cvt_double_to_fp8(std::ldexp(blk[k], -e), __NV_SATFINITE, __NV_E4M3);
                 }
+            continue;
+        }
+        if (tf32) {
+            // tf32 hi = nearest tf32 of the value, lo = nearest tf32 of the
+            // remainder (about 22 significand bits together)
+            for (size_t k = 0; k < tsz; ++k) {
+                const double v = work[k];
+                const float h = tf32_round((float)v);
+                thi[(size_t)ph * tsz + k] = h;
+                tlo[(size_t)ph * tsz + k] = tf32_round((float)(v - (double)h));
+            }
             continue;
         }
         for (int row = 0; row < N4; ++row)
@@ -907,7 +965,12 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
     }
 
     free_tables(t);
-    cudaError_t e = fp8 ? cudaMalloc(&t->d_Z8, z8.size()) : cudaMalloc(&t->d_Zhi, hi.size() * sizeof(__nv_bfloat16));
+    cudaError_t e = fp8    ? cudaMalloc(&t->d_Z8, z8.size())
+                    : tf32 ? cudaMalloc(&t->d_Zt_hi, thi.size() * sizeof(float))
+                           : cudaMalloc(&t->d_Zhi, hi.size() * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess && tf32) e = cudaMalloc(&t->d_Zt_lo, tlo.size() * sizeof(float));
+    if (e == cudaSuccess && tf32) e = cudaMemcpy(t->d_Zt_hi, thi.data(), thi.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && tf32) e = cudaMemcpy(t->d_Zt_lo, tlo.data(), tlo.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && fp8) e = cudaMalloc(&t->d_sfb, sfb.size());
     if (e == cudaSuccess && fp8) e = cudaMemcpy(t->d_Z8, z8.data(), z8.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && fp8) e = cudaMemcpy(t->d_sfb, sfb.data(), sfb.size(), cudaMemcpyHostToDevice);
@@ -916,7 +979,7 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
     if (e == cudaSuccess && split) e = cudaMalloc(&t->d_Zlo, lo.size() * sizeof(__nv_bfloat16));
     if (e == cudaSuccess && !pure.empty()) e = cudaMalloc(&t->d_pure, pure.size() * sizeof(int));
     if (e == cudaSuccess && !mixed.empty()) e = cudaMalloc(&t->d_mixed, mixed.size() * sizeof(int));
-    if (e == cudaSuccess && !fp8)
+    if (e == cudaSuccess && !fp8 && !tf32)
         e = cudaMemcpy(t->d_Zhi, hi.data(), hi.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && split)
         e = cudaMemcpy(t->d_Zlo, lo.data(), lo.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice);
@@ -930,14 +993,17 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
         return e == cudaErrorMemoryAllocation ? RTLB_E_OOM : RTLB_E_CUDA;
     }
     const int box_rows = pair ? N4 / 2 : N4;
-    if (fp8 ? !encode_z8_map(&t->tmZhi, t->d_Z8, N4, KP8, n_phase)
-            : (!encode_z_map(&t->tmZhi, t->d_Zhi, N4, KP, n_phase, box_rows) ||
-               (split && !encode_z_map(&t->tmZlo, t->d_Zlo, N4, KP, n_phase, box_rows)))) {
+    const bool maps_ok =
+        fp8 ? encode_z8_map(&t->tmZhi, t->d_Z8, N4, KP8, n_phase)
+            : tf32 ? (encode_zt_map(&t->tmZhi, t->d_Zt_hi, N4, n_phase) && encode_zt_map(&t->tmZlo, t->d_Zt_lo, N4, n_phase))
+                   : (encode_z_map(&t->tmZhi, t->d_Zhi, N4, KP, n_phase, box_rows) &&
+                      (!split || encode_z_map(&t->tmZlo, t->d_Zlo, N4, KP, n_phase, box_rows)));
+    if (!maps_ok) {
         free_tables(t);
         c->err = "tensor map encoding for the phase tables failed";
         return RTLB_E_CUDA;
     }
-    if (!split) t->tmZlo = t->tmZhi;
+    if (!split && !tf32) t->tmZlo = t->tmZhi;
     t->N4 = N4;
     t->KP = KP;
     t->C = C;
@@ -947,14 +1013,15 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
     t->n_pure = pair ? (int)pure.size() / 2 : (int)pure.size();
     t->n_mixed = (int)mixed.size();
     t->stages = stages;
-    t->smem = pair ? smem_bytes_pair(N4, stages) : (fp8 ? tc_fp8_smem_bytes(N4, stages) : smem_bytes(N4, mode, stages));
+    t->smem = pair ? smem_bytes_pair(N4, stages)
+                   : (fp8 ? tc_fp8_smem_bytes(N4, stages) : (tf32 ? tc_tf32_smem_bytes(N4, stages) : smem_bytes(N4, mode, stages)));
     return RTLB_OK;
 }
 
 rtlb_status tc_step(rtlb_ctx *c, const StepParams &p, cudaStream_t s)
 {
     TcState *t = state_of(c);
-    if (!t || (!t->d_Zhi && !t->d_Z8)) {
+    if (!t || (!t->d_Zhi && !t->d_Z8 && !t->d_Zt_hi)) {
         c->err = "tensor-core tables are not prepared";
         return RTLB_E_STATE;
     }
@@ -981,10 +1048,15 @@ rtlb_status tc_step(rtlb_ctx *c, const StepParams &p, cudaStream_t s)
         tp.n = p.n;
         tp.bcbits = pack_bc(p.bc);
         tp.err = t->d_err;
+        tp.stall = t->stall_next;
+        t->stall_next = 0;
         cudaError_t e = cudaSuccess;
         if (t->mode == 4) {
             e = launch_step_tc_fp8(t->tmS[which], t->tmZhi, tp, t->d_sfb, t->N4, t->stages, t->n_phase,
                                    std::min(t->sm_count, t->n_pure), s);
+        } else if (t->mode == 5) {
+            e = launch_step_tc_tf32(t->tmS[which], t->tmZhi, t->tmZlo, tp, t->N4, t->stages,
+                                    std::min(t->sm_count, t->n_pure), s);
         } else if (t->pair) {
             const int grid = 2 * std::min(t->sm_count / 2, t->n_pure);
             e = cudaFuncSetAttribute(k_step_tc_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem);
@@ -1018,6 +1090,21 @@ rtlb_status tc_step(rtlb_ctx *c, const StepParams &p, cudaStream_t s)
             return RTLB_E_CUDA;
         }
     }
+    return RTLB_OK;
+}
+
+rtlb_status tc_arm_stall(rtlb_ctx *c)
+{
+    TcState *t = state_of(c);
+    if (!t || (!t->d_Zhi && !t->d_Z8 && !t->d_Zt_hi)) {
+        c->err = "the stall hook needs a tensor-core precision with its medium set";
+        return RTLB_E_STATE;
+    }
+    if (t->mode >= 4) {
+        c->err = "the stall hook covers the bf16-class kernels only";
+        return RTLB_E_UNSUPPORTED;
+    }
+    t->stall_next = 1;
     return RTLB_OK;
 }
 

@@ -21,6 +21,10 @@ rtlb_status tc_step(rtlb_ctx *c, const StepParams &p, cudaStream_t s);
 // Reads (synchronizing `s`) and clears the device error flag of the
 // tensor-core kernel; RTLB_E_TIMEOUT when a bounded wait gave up.
 rtlb_status tc_check_error(rtlb_ctx *c, cudaStream_t s);
+// Arms the bounded-wait test hook for the next tensor-core launch (bf16-class
+// kernels): CTA 0 leaves one state load unissued.  RTLB_E_STATE before the
+// tables exist, RTLB_E_UNSUPPORTED for the FP8 kernel.
+rtlb_status tc_arm_stall(rtlb_ctx *c);
 int tc_mixed_tiles(const rtlb_ctx *c);
 void tc_release(rtlb_ctx *c);
 

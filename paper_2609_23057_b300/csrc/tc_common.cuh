@@ -35,6 +35,10 @@ struct TcParams {
     int nx, nz, n;
     int bcbits;
     int *err;
+    // test hook of the bounded waits: when nonzero, CTA 0 leaves the load of
+    // its first staging slot unissued (nothing is then in flight for it), so
+    // its converters' wait runs out and the launch reports a timeout
+    int stall = 0;
 };
 
 enum ErrCode { kErrTimeoutProducer = 1, kErrTimeoutConverter = 2, kErrTimeoutMma = 4, kErrTimeoutEpilogue = 8 };
@@ -147,6 +151,13 @@ __device__ __forceinline__ bool convert_tile(const float4 cf, const float *fwd, 
 }
 
 }  // namespace tccommon
+
+// 3xTF32 form (tc_tf32.cu), 4n <= 128: shared memory for a stage count and the
+// launch (grid CTAs over p.tiles); tables are float32 [n_phase][4n][4n]
+// holding tf32 values, tensor maps with 32-column x 4n-row boxes (SW128).
+size_t tc_tf32_smem_bytes(int N4, int stages);
+cudaError_t launch_step_tc_tf32(const CUtensorMap &tmS, const CUtensorMap &tmZhi, const CUtensorMap &tmZlo,
+                                const tccommon::TcParams &p, int N4, int stages, int grid, cudaStream_t s);
 
 // FP8 block-scaled form (tc_fp8.cu): TMEM columns it needs (D, A scales, the
 // B scales of every class; must be <= 512), shared memory for a stage count,

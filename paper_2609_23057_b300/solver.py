@@ -11,7 +11,7 @@ import numpy as np
 from . import _lib
 from ._lib import Directions, Grid, Options, check, lib
 
-PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2, "bf16x2": 3, "fp8": 4}
+PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2, "bf16x2": 3, "fp8": 4, "tf32x3": 5}
 SURVIVAL = {"linear": 0, "exp": 1}
 ABSORPTION = {"beer_lambert": 0, "taylor": 1}
 SIDES = {"top": 0, "bottom": 1, "left": 2, "right": 3}
@@ -74,6 +74,15 @@ def phase_hg(n_zen: int, n_az: int, g: float, pol_amp: float, mu=None, phi=None,
     check(lib().rtlb_phase_hg(C.byref(d), float(g), float(pol_amp), Z.ctypes.data,
                               dZ.ctypes.data if with_dg else None))
     return (Z, dZ) if with_dg else Z
+
+
+def phase_hg_grad(n_zen: int, n_az: int, g: float, pol_amp: float, grad_Z, mu=None, phi=None) -> float:
+    """dL/dg from dL/dZ of an HG table (rtlb_phase_hg_grad)."""
+    d, keep = _dirs(n_zen, n_az, mu, phi)
+    gZ = np.ascontiguousarray(grad_Z, np.float64)
+    out = C.c_double()
+    check(lib().rtlb_phase_hg_grad(C.byref(d), float(g), float(pol_amp), gZ.ctypes.data, C.byref(out)))
+    return out.value
 
 
 def phase_mix(n_zen: int, n_az: int, m: float, g: float, pol_amp: float, mu=None, phi=None):
@@ -207,6 +216,21 @@ class Solver:
         self._check(lib().rtlb_last_residual(self._ctx, C.byref(r), _stream(stream)))
         return r.value
 
+    def dop_out(self, side="top", out=None, stream=None):
+        """Degree of polarization [len][n] of the radiance leaving through a
+        side (rtlb_dop_out)."""
+        import torch
+        side = SIDES[side] if isinstance(side, str) else int(side)
+        ln = self.nx if side in (0, 1) else self.nz
+        if out is None:
+            out = torch.empty((ln, self.n), dtype=torch.float32, device="cuda")
+        self._check(lib().rtlb_dop_out(self._ctx, side, _ptr(out), _stream(stream)))
+        return out
+
+    def stall_next_step(self):
+        """Arm the bounded-wait test hook (rtlb_test_stall_next_step)."""
+        self._check(lib().rtlb_test_stall_next_step(self._ctx))
+
     def total_intensity(self, stream=None) -> float:
         r = C.c_double()
         self._check(lib().rtlb_total_intensity(self._ctx, C.byref(r), _stream(stream)))
@@ -267,14 +291,13 @@ def solver_for(w, precision: str = "fp32") -> Solver:
 
 
 def _tables_for(solver: Solver, specs, g_value=None, hg_index=None):
-    tabs, dZdg = [], None
+    tabs = []
     for k, sp in enumerate(specs):
         if k == hg_index:
-            Z, dZdg = phase_hg(solver.n_zen, solver.n_az, float(g_value), sp[2], with_dg=True)
-            tabs.append(Z)
+            tabs.append(phase_hg(solver.n_zen, solver.n_az, float(g_value), sp[2]))
         else:
             tabs.append(phase_table_spec(solver.n_zen, solver.n_az, sp))
-    return np.stack(tabs), dZdg
+    return np.stack(tabs)
 
 
 def _make_top_radiance_fn():
@@ -286,18 +309,19 @@ def _make_top_radiance_fn():
         [nz][nx] and the asymmetry g of the HG class `hg_index`.  Forward:
         rtlb_set_medium + rtlb_step + rtlb_radiance_out.  Backward:
         rtlb_adjoint (float32 forward replayed from checkpoints every
-        `checkpoint_every` steps), dL/dg = <dZ/dg, dL/dZ_hg>."""
+        `checkpoint_every` steps) and rtlb_phase_hg_grad for dL/dg."""
 
         @staticmethod
         def forward(ctx, tau, albedo, g, solver, specs, hg_index, phase_index, nsteps, checkpoint_every):
-            tabs, dZdg = _tables_for(solver, specs, g.item(), hg_index)
+            tabs = _tables_for(solver, specs, g.item(), hg_index)
             solver.set_medium(tau.detach().float().contiguous(), albedo.detach().float().contiguous(), tabs,
                               phase_index=phase_index)
             zero = torch.zeros((solver.nz, solver.nx, solver.n, 4), dtype=torch.float32, device="cuda")
             solver.set_state(zero)
             solver.step(nsteps)
             out = solver.radiance_out("top").clone()
-            ctx.solver, ctx.nsteps, ctx.K, ctx.hg_index, ctx.dZdg = solver, nsteps, checkpoint_every, hg_index, dZdg
+            ctx.solver, ctx.nsteps, ctx.K, ctx.hg_index = solver, nsteps, checkpoint_every, hg_index
+            ctx.g, ctx.pol_amp = float(g.item()), (specs[hg_index][2] if hg_index is not None else 0.0)
             ctx.zero = zero
             return out
 
@@ -308,7 +332,8 @@ def _make_top_radiance_fn():
             gt, ga, gZ, _ = s.adjoint(ctx.nsteps, grad_out.contiguous(), checkpoint_every=ctx.K)
             gg = None
             if ctx.hg_index is not None:
-                gg = torch.tensor(float(np.sum(ctx.dZdg * gZ[ctx.hg_index])), dtype=torch.float64, device="cuda")
+                dg = phase_hg_grad(s.n_zen, s.n_az, ctx.g, ctx.pol_amp, gZ[ctx.hg_index])
+                gg = torch.tensor(dg, dtype=torch.float64, device="cuda")
             return gt, ga, gg, None, None, None, None, None, None
 
     return TopRadiance

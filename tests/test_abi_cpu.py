@@ -79,6 +79,27 @@ def test_hg_derivative_matches_central_difference():
     assert np.abs(dZ - fd).max() < 1e-6 * max(1.0, np.abs(fd).max())
 
 
+@pytest.mark.parametrize("nzen,naz,g", [(2, 4, 0.85), (4, 8, 0.85), (8, 8, 0.3)])
+def test_hg_gradient_contraction_matches_oracle_table(orc, nzen, naz, g):
+    """rtlb_phase_hg_grad (dL/dg = <dZ/dg, dL/dZ>) against the same
+    contraction with a central difference of the oracle's own HG table, for a
+    random dL/dZ."""
+    rng = np.random.default_rng(nzen * naz)
+    n = nzen * naz
+    gZ = rng.standard_normal((4 * n, 4 * n))
+    got = S.phase_hg_grad(nzen, naz, g, -0.1, gZ)
+    mu, phi = orc.direction_grid(nzen, naz)
+    h = 1e-6
+    dZ = (orc.phase_table_spec(mu, phi, ("hg", g + h, -0.1)) - orc.phase_table_spec(mu, phi, ("hg", g - h, -0.1))) / (2 * h)
+    ref = float(np.sum(dZ * gZ))
+    assert got == pytest.approx(ref, rel=1e-6, abs=1e-8 * np.abs(dZ).sum())
+    L = _lib.lib()
+    d = _lib.Directions(nzen, naz, None, None)
+    out = C.c_double()
+    assert L.rtlb_phase_hg_grad(C.byref(d), 1.2, -0.1, gZ.ctypes.data, C.byref(out)) == 3   # RTLB_E_RANGE
+    assert L.rtlb_phase_hg_grad(C.byref(d), g, -0.1, None, C.byref(out)) == 1               # RTLB_E_ARG
+
+
 def test_host_helper_argument_errors():
     L = _lib.lib()
     d = _lib.Directions(0, 4, None, None)

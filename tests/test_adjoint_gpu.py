@@ -134,56 +134,142 @@ def test_adjoint_workspace_reuse(torch_cuda, orc):
         assert np.array_equal(a, b)
 
 
-def test_adjoint_crop_fd_and_g(torch_cuda, orc):
-    """16x16 crop of the 1024x256, n = 32 adjoint medium, 100 steps, loss =
-    squared error of the top I, Q, U against a seeded target: GPU adjoint vs
-    oracle adjoint, vs central differences (h = 1e-3) of the oracle forward at
-    64 random cells, and dL/dg of the cloud table (through dZ/dg) vs a central
-    difference in g."""
-    from paper_2609_23057_b300.solver import phase_hg
-    full = W.adjoint(steps=100)
-    w = full.crop(120, 136, 500, 516)
+def _crop32_target(orc, w, nsteps):
+    """Seeded target of the differentiation workload: the top radiance of a
+    forward with tau x 1.1 in the cloud cells (class 1), times 1 + 0.05 N(0, 1)
+    (seed 2)."""
+    wt = W.adjoint(steps=nsteps).crop(112, 144, 496, 528)
+    wt.tau = np.where(wt.phase_index == 1, wt.tau * 1.1, wt.tau)
+    Pt = oracle_problem(orc, wt)
+    top = Pt.radiance_out(Pt.run(Pt.zero_state(), nsteps), orc.SIDE_TOP)
+    return top * (1.0 + 0.05 * np.random.default_rng(2).standard_normal(top.shape))
+
+
+def test_adjoint_crop32_fd_and_g(torch_cuda, orc):
+    """The differentiation workload (1024x256, n = 32, medium seed 2) on its
+    32x32 crop (rows 112-143 across the cloud top, columns 496-527), run as
+    its own problem for 1000 steps.  Loss: squared error of the top I, Q, U
+    against the seeded target.  Checks: the GPU adjoint (checkpoint every 50
+    steps) against the FP64 oracle adjoint (1e-4 of the largest gradient);
+    the oracle adjoint against the oracle's central differences (h = 1e-3,
+    1e-4) at 64 random cells for tau and 16 for albedo, and the GPU gradient
+    against the same differences within the sum of the two bounds; dL/dg
+    (rtlb_phase_hg_grad) against a central difference in g.  The differences
+    run 200 steps: on this crop the top radiance after 200 steps equals the
+    1000-step one to ~1e-11 relative (asserted), so the two losses are the
+    same function to that accuracy, and 2 x 82 oracle forwards of 200 steps
+    take a minute where 1000 steps would take five."""
+    from paper_2609_23057_b300.solver import phase_hg_grad
+    full_steps, fd_steps = 1000, 200
+    w = W.adjoint(steps=full_steps).crop(112, 144, 496, 528)
     P = oracle_problem(orc, w)
     S0 = np.zeros((w.nz, w.nx, w.n, 4))
-    ref_top = P.radiance_out(P.run(S0, w.steps), orc.SIDE_TOP)
-    rng = np.random.default_rng(2)
-    target = ref_top * (1.1 + 0.05 * rng.standard_normal(ref_top.shape))
-    m = np.zeros_like(ref_top)
+    target = _crop32_target(orc, w, fd_steps)
+    m = np.zeros_like(target)
     m[..., :3] = 1.0
+    top_full = P.radiance_out(P.run(S0, full_steps), orc.SIDE_TOP)
+    top_fd = P.radiance_out(P.run(S0, fd_steps), orc.SIDE_TOP)
+    assert np.abs(top_fd - top_full).max() <= 1e-10 * np.abs(top_full).max()
 
     def loss(Pp):
-        top = Pp.radiance_out(Pp.run(S0, w.steps), orc.SIDE_TOP)
+        top = Pp.radiance_out(Pp.run(S0, fd_steps), orc.SIDE_TOP)
         return float(np.sum(m * (top - target) ** 2))
 
-    seed = 2 * m * (ref_top - target)
-    rt, ra, rZ = P.adjoint(S0, w.steps, seed)
-    gt, ga, gZ, _, _ = _gpu_adjoint(torch_cuda, w, S0, w.steps, seed, K=30)
+    seed = 2 * m * (top_full - target)
+    rt, ra, rZ = P.adjoint(S0, full_steps, seed)
+    gt, ga, gZ, _, _ = _gpu_adjoint(torch_cuda, w, S0, full_steps, seed, K=50)
     assert _rel(gt, rt) < TOL and _rel(ga, ra) < TOL and _rel(gZ, rZ) < TOL
-    cells = [tuple(c) for c in rng.integers(0, [w.nz, w.nx], size=(64, 2))]
+    rng = np.random.default_rng(5)
     h = 1e-3
-    for z, x in cells:
-        vals = []
-        for sgn in (1, -1):
-            Pp = oracle_problem(orc, w)
-            Pp.tau[z, x] += sgn * h
-            vals.append(loss(Pp))
-        fd = (vals[0] - vals[1]) / (2 * h)
-        assert abs(fd - gt[z, x]) <= TOL * np.abs(gt).max() + 1e-6 * abs(fd)
-    # cloud g (class 1 is HG with g = 0.85): dL/dg = <dZ/dg, dL/dZ_cloud>.
-    # The loss curves strongly in g near the forward peak: a central
-    # difference with h = 1e-3 carries ~2e-4 relative truncation error, so
-    # the check uses h = 1e-4 (truncation ~2e-6) and the exact oracle adjoint.
-    _, dZdg = phase_hg(w.n_zen, w.n_az, 0.85, -0.1, with_dg=True)
-    g_adj = float(np.sum(dZdg * gZ[1]))
-    assert g_adj == pytest.approx(float(np.sum(dZdg * rZ[1])), rel=TOL)
+    for field, grad, ref, count in (("tau", gt, rt, 64), ("albedo", ga, ra, 16)):
+        cells = [tuple(c) for c in rng.integers(0, [w.nz, w.nx], size=(count, 2))]
+        for z, x in cells:
+            vals = []
+            for sgn in (1, -1):
+                Pp = oracle_problem(orc, w)
+                getattr(Pp, field)[z, x] += sgn * h
+                vals.append(loss(Pp))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(fd - ref[z, x]) <= TOL * np.abs(ref).max(), (field, z, x)
+            assert abs(fd - grad[z, x]) <= 2 * TOL * np.abs(ref).max(), (field, z, x)
+    # cloud g (class 1 is HG with g = 0.85).  The loss curves strongly in g
+    # near the forward peak: a central difference with h = 1e-3 carries ~2e-4
+    # relative truncation error, so this one uses h = 1e-4 (~2e-6).
+    g_adj = phase_hg_grad(w.n_zen, w.n_az, 0.85, -0.1, gZ[1])
+    mu, phi = orc.direction_grid(w.n_zen, w.n_az)
+    hz = 1e-6
+    dZ_orc = (orc.phase_table_spec(mu, phi, ("hg", 0.85 + hz, -0.1)) -
+              orc.phase_table_spec(mu, phi, ("hg", 0.85 - hz, -0.1))) / (2 * hz)
+    assert g_adj == pytest.approx(float(np.sum(dZ_orc * rZ[1])), rel=TOL)
     hg = 1e-4
     vals = []
     for sgn in (1, -1):
-        ww = full.crop(120, 136, 500, 516)
+        ww = W.adjoint(steps=fd_steps).crop(112, 144, 496, 528)
         ww.phase_specs = [("rayleigh",), ("hg", 0.85 + sgn * hg, -0.1)]
         vals.append(loss(oracle_problem(orc, ww)))
     g_fd = (vals[0] - vals[1]) / (2 * hg)
     assert g_adj == pytest.approx(g_fd, rel=TOL)
+
+
+def test_adjoint_full_size_fd_of_gpu_forward(torch_cuda):
+    """1024x256, n = 32, 1000 steps, checkpoint every 50 (the differentiation
+    workload at full size): grad_tau and grad_albedo against central
+    differences (h = 1e-3) of the float32 GPU forward, at the four cells
+    where each gradient is largest and at four random cloud cells for tau.
+    The forward is float32: a perturbed run differs from the base run by
+    rounding noise of ~1e-7 of each top-radiance entry besides the effect of
+    h, which limits what a difference quotient resolves (the first run of this
+    test saw 2.7e-3 relative at an albedo cell whose gradient is 0.8 of the
+    largest); the tolerance is 1e-3 of the largest gradient plus 1e-2 of the
+    cell's own value.  The 32x32 crop test holds the adjoint to 1e-4 against
+    the FP64 oracle."""
+    from paper_2609_23057_b300.solver import solver_for
+    w = W.adjoint(steps=1000)
+    zero = torch_cuda.zeros((w.nz, w.nx, w.n, 4), dtype=torch_cuda.float32, device="cuda")
+
+    def top_after(ww):
+        s = solver_for(ww, "fp32")
+        s.set_state(zero)
+        s.step(ww.steps)
+        top = s.radiance_out("top").cpu().numpy().astype(np.float64)
+        s.close()
+        return top
+
+    wt = W.adjoint(steps=1000)
+    wt.tau = np.where(wt.phase_index == 1, wt.tau * 1.1, wt.tau)
+    target = top_after(wt) * (1.0 + 0.05 * np.random.default_rng(2).standard_normal((w.nx, w.n, 4)))
+    m = np.zeros_like(target)
+    m[..., :3] = 1.0
+    top0 = top_after(w)
+    seed = 2 * m * (top0 - target)
+    s = solver_for(w, "fp32")
+    s.set_state(zero)
+    gt, ga, _, _ = s.adjoint(w.steps, torch_cuda.from_numpy(seed.astype(np.float32)).cuda(), checkpoint_every=50)
+    gt, ga = gt.cpu().numpy().astype(np.float64), ga.cpu().numpy().astype(np.float64)
+    s.close()
+
+    def loss(ww):
+        return float(np.sum(m * (top_after(ww) - target) ** 2))
+
+    rng = np.random.default_rng(6)
+    cloud = np.argwhere(w.phase_index == 1)
+    h = 1e-3
+    for field, grad in (("tau", gt), ("albedo", ga)):
+        cells = [tuple(c) for c in np.argwhere(np.abs(grad) >= np.sort(np.abs(grad).ravel())[-4])[:4]]
+        if field == "tau":
+            cells += [tuple(cloud[k]) for k in rng.integers(0, len(cloud), 4)]
+        for z, x in cells:
+            vals, xs = [], []
+            for sgn in (1, -1):
+                ww = W.adjoint(steps=1000)
+                arr = getattr(ww, field).copy()
+                arr[z, x] = float(np.float32(arr[z, x] + sgn * h))   # the value the library sees
+                xs.append(arr[z, x])
+                setattr(ww, field, arr)
+                vals.append(loss(ww))
+            fd = (vals[0] - vals[1]) / (xs[0] - xs[1])
+            assert abs(fd - grad[z, x]) <= 1e-3 * np.abs(grad).max() + 1e-2 * abs(grad[z, x]), \
+                (field, z, x, fd, grad[z, x])
 
 
 def test_adjoint_full_size_linearity(torch_cuda):

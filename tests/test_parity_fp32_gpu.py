@@ -77,6 +77,12 @@ def test_random_media(torch_cuda, orc, nx, nz, nzen, naz, bc, nph, seed):
         ro = s.radiance_out(side).cpu().numpy()
         rr = oracle_problem(orc, w).radiance_out(ref, side)
         assert np.abs(ro - rr).max() <= 1e-5 * max(np.abs(rr).max(), 1e-30)
+        # degree of polarization of the leaving radiance (Eq. 36), on entries
+        # whose I is above 1e-6 of the side's maximum (zero elsewhere)
+        dp = s.dop_out(side).cpu().numpy().astype(np.float64)
+        mask = rr[..., 0] > 1e-6 * max(np.abs(rr[..., 0]).max(), 1e-300)
+        assert np.abs(dp - orc.dop(rr))[mask].max(initial=0.0) < TOL_DOP
+        assert np.all(dp[rr[..., 0] == 0] == 0)
 
 
 def test_steady_state_small(torch_cuda, orc):
@@ -92,6 +98,26 @@ def test_steady_state_small(torch_cuda, orc):
     assert abs(steps - t_ref) <= max(3, 0.02 * t_ref)
     ref = P.run(P.zero_state(), steps)
     got = _state(s)
+    assert rel_err_I(got, ref) < TOL_I
+    assert abs_err_dop(got, ref) < TOL_DOP
+
+
+def test_steady_state_lattice512_crop128(torch_cuda, orc):
+    """run_to_steady (residual < 1e-6, cap 4000, checked every step) on the
+    128x128 centre crop of the 512x512, n = 32 steady-state medium, run as its
+    own problem: the step count within 2 % of the oracle's own iteration, and
+    the state after those steps within 1e-5 of the oracle's."""
+    w = W.steady().crop(192, 320, 192, 320)
+    P = oracle_problem(orc, w)
+    _, t_ref, r_ref = P.run_to_steady(P.zero_state(), 1e-6, 4000)
+    assert r_ref < 1e-6
+    s = _solver(w)
+    steps, res, ok = s.run_to_steady(1e-6, 4000, check_every=1)
+    assert ok and res < 1e-6
+    assert abs(steps - t_ref) <= max(2, 0.02 * t_ref)
+    ref = P.run(P.zero_state(), steps)
+    got = _state(s)
+    s.close()
     assert rel_err_I(got, ref) < TOL_I
     assert abs_err_dop(got, ref) < TOL_DOP
 

@@ -55,6 +55,13 @@ def test_noalloc_rejects_oversize_and_bad_arguments():
     assert L.rtlb_residual_noalloc(a.data_ptr(), a.data_ptr(), too_many, out.data_ptr(), None) == 2
     assert L.rtlb_residual_noalloc(a.data_ptr(), a.data_ptr(), 6, out.data_ptr(), None) == 1
     assert L.rtlb_residual_noalloc(None, a.data_ptr(), 8, out.data_ptr(), None) == 1
+    # host memory (pageable or pinned) is rejected before any launch
+    h = np.zeros(8, np.float32)
+    hp = torch.zeros(8, dtype=torch.float32).pin_memory()
+    assert L.rtlb_residual_noalloc(h.ctypes.data, a.data_ptr(), 8, out.data_ptr(), None) == 1
+    assert L.rtlb_residual_noalloc(a.data_ptr(), hp.data_ptr(), 8, out.data_ptr(), None) == 1
+    ho = np.zeros(3, np.float64)
+    assert L.rtlb_residual_noalloc(a.data_ptr(), a.data_ptr(), 8, ho.ctypes.data, None) == 1
     assert L.rtlb_residual_noalloc(a.data_ptr(), a.data_ptr(), 8, out.data_ptr(), None) == 0
     torch.cuda.synchronize()
     assert out.cpu().tolist() == [0.0, 0.0, 0.0]
