@@ -75,6 +75,16 @@ typedef enum { RTLB_BC_VACUUM = 0, RTLB_BC_PERIODIC = 1, RTLB_BC_INFLOW = 2 } rt
  *              the FP32 form on the tensor cores.  The split state operand is
  *              kept in tensor memory.  n in {8, 16, 32} (the split tf32 table
  *              of n = 64 is 512 KB, more than any CTA's shared memory).
+ *  FP8X     -- the block-scaled e4m3 MMA with both operands split: the state
+ *              operand beta S~ as two e4m3 terms (hi; the remainder with the
+ *              scale of its own block maximum), the table as three (each the
+ *              e4m3 of what the terms before it left, with its own scale), and
+ *              five MMAs (state term a times table term b for a + b <= 2, b <=
+ *              2, a <= 1); float32 accumulation.  About the accuracy of BF16X2.
+ *              The state terms are kept in tensor memory; with the table
+ *              scales of every class resident there too, n = 64 takes at most
+ *              2 phase classes (RTLB_E_UNSUPPORTED from rtlb_set_medium
+ *              beyond).
  * Tensor-core forms need n in {8, 16, 32, 64} (TF32X3: {8, 16, 32});
  * rtlb_create returns RTLB_E_UNSUPPORTED otherwise.  Tiles of 128 sites that
  * mix phase classes run on the FP32 CUDA-core kernel in every form. */
@@ -84,7 +94,8 @@ typedef enum {
     RTLB_PREC_BF16X3 = 2,
     RTLB_PREC_BF16X2 = 3,
     RTLB_PREC_FP8 = 4,
-    RTLB_PREC_TF32X3 = 5
+    RTLB_PREC_TF32X3 = 5,
+    RTLB_PREC_FP8X = 6
 } rtlb_precision;
 
 /* Survival of unscattered light over one step: LINEAR = 1 - k_scat dt (Eq. 11

@@ -54,6 +54,7 @@ def lib():
         L.orc_step.argtypes = step_args + [_dp, _dp]
         L.orc_run.argtypes = step_args + [_dp, C.c_int]
         L.orc_step_fp8.argtypes = step_args[:12] + [C.c_int] + step_args[12:] + [_dp, _dp]
+        L.orc_step_fp8x.argtypes = step_args[:12] + [C.c_int] + step_args[12:] + [_dp, _dp]
         L.orc_e4m3.argtypes = [C.c_double]
         L.orc_e4m3.restype = C.c_double
         L.orc_fp8_exponent.argtypes = [C.c_double, C.c_int]
@@ -269,6 +270,16 @@ class Problem:
         out = np.empty_like(S)
         a = self._args()
         lib().orc_step_fp8(*a[:12], int(self.Z.shape[0]), *a[12:], S, out)
+        return out
+
+    def step_fp8x(self, S: np.ndarray) -> np.ndarray:
+        """One step in the split FP8 form of the contraction (see
+        orc_step_fp8x: an emulation of that form); S must hold float32
+        values."""
+        S = np.ascontiguousarray(S, np.float64)
+        out = np.empty_like(S)
+        a = self._args()
+        lib().orc_step_fp8x(*a[:12], int(self.Z.shape[0]), *a[12:], S, out)
         return out
 
     def run(self, S: np.ndarray, nsteps: int) -> np.ndarray:

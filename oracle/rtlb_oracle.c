@@ -452,9 +452,12 @@ int orc_fp8_exponent(double amax, int fp32_floor)
     return e;
 }
 
-/* One step in the FP8 block-scaled precision form of the contraction (the
- * CUDA library's FP8 precision), written out in float64 from that form's
- * definition.  The paper fixes no low-precision arithmetic; the form is:
+/* One step in the FP8 block-scaled precision form of the contraction: an
+ * emulation, in float64, of the CUDA library's FP8 precision, written from
+ * that form's definition.  It reproduces the form's quantization choices (it
+ * is not the paper's method: orc_step is); tests use it to check that the
+ * kernel implements the form, and orc_step to measure what the form costs in
+ * accuracy.  The paper fixes no low-precision arithmetic; the form is:
  *   - state operand: S~ = S + e rounded to float32 (S holds float32 values),
  *     beta rounded to float32, b = beta S~ rounded to float32; per site and
  *     block of 8 directions (32 values) the scale 2^ea from the block's
@@ -552,6 +555,130 @@ void orc_step_fp8(int nx, int nz, int n, int ntap, const int *tx, const int *tz,
     free(P);
     free(Bq);
     free(fw);
+}
+
+/* One step in the split FP8 precision form of the contraction: an
+ * emulation, in float64, of the CUDA library's FP8X precision, written from
+ * that form's definition (the paper fixes no low-precision arithmetic).  The
+ * form, against orc_step_fp8's single e4m3 operands:
+ *   - state operand: b = beta S~ as in orc_step_fp8 (float32 roundings); per
+ *     site and block of 8 directions the scale 2^e0 from the block's largest
+ *     |b| (float32 floor), hi term q0 = e4m3(b 2^-e0); the remainder
+ *     r = b 2^-e0 - q0 (exact) gets its own scale 2^d from its block's
+ *     largest |r| (float32 floor), lo term q1 = e4m3(r 2^-d); the two terms
+ *     are q0 2^e0 and q1 2^(e0 + d), the lo term zero when e0 + d < -127;
+ *   - table (forward blocks taken out as in orc_step_fp8): three terms per row
+ *     and block of 32 columns, each e4m3 with the scale of the remainder left
+ *     by the terms before it (from the block's largest |remainder|, no float32
+ *     floor);
+ *   - products kept: state term a times table term b for (a, b) in (0,0),
+ *     (0,1), (0,2), (1,0), (1,1); the dropped (1,2) is below 2^-12 of a
+ *     product.  P = alpha S~ + beta c_i S~ + their sum (exact here), then
+ *     streaming as in orc_step.  n must be a multiple of 8. */
+void orc_step_fp8x(int nx, int nz, int n, int ntap, const int *tx, const int *tz, const double *tw,
+                   const double *tau, const double *albedo, const double *emis, const int *cls,
+                   const double *Z, int n_phase, int surv_mode, int abs_mode, const int *bc,
+                   const double *inflow, const double *S_in, double *S_out)
+{
+    int K = 4 * n;
+    size_t nsite = (size_t)nx * nz;
+    size_t tsz = (size_t)K * K;
+    double *Bt = (double *)malloc((size_t)3 * n_phase * tsz * sizeof(double));   /* [term][class][K][K] */
+    double *fw = (double *)calloc((size_t)n_phase * n, sizeof(double));
+    double *rem = (double *)malloc(tsz * sizeof(double));
+    for (int c = 0; c < n_phase; ++c) {
+        const double *Zc = Z + (size_t)c * tsz;
+        memcpy(rem, Zc, tsz * sizeof(double));
+        int diag = 1;
+        for (int i = 0; i < n && diag; ++i) {
+            double ci = Zc[(size_t)(4 * i) * K + 4 * i];
+            for (int a = 0; a < 4 && diag; ++a)
+                for (int b = 0; b < 4; ++b) {
+                    double want = (a == b) ? ci : 0.0;
+                    if (fabs(Zc[(size_t)(4 * i + a) * K + 4 * i + b] - want) > 1e-14 * fabs(ci)) {
+                        diag = 0;
+                        break;
+                    }
+                }
+        }
+        if (diag)
+            for (int i = 0; i < n; ++i) {
+                double ci = Zc[(size_t)(4 * i) * K + 4 * i];
+                fw[(size_t)c * n + i] = (double)(float)ci;
+                for (int a = 0; a < 4; ++a) rem[(size_t)(4 * i + a) * K + 4 * i + a] = ci - (double)(float)ci;
+            }
+        for (int t = 0; t < 3; ++t) {
+            double *B = Bt + ((size_t)t * n_phase + c) * tsz;
+            for (int row = 0; row < K; ++row)
+                for (int blk = 0; blk < K / 32; ++blk) {
+                    double *r = rem + (size_t)row * K + 32 * blk;
+                    double *q = B + (size_t)row * K + 32 * blk;
+                    double amax = 0.0;
+                    for (int k = 0; k < 32; ++k) amax = fmax(amax, fabs(r[k]));
+                    int e = orc_fp8_exponent(amax, 0);
+                    for (int k = 0; k < 32; ++k) {
+                        q[k] = ldexp(orc_e4m3(ldexp(r[k], -e)), e);
+                        r[k] -= q[k];
+                    }
+                }
+        }
+    }
+    static const int pairs[5][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 0}, {1, 1}};
+    double *P = (double *)malloc(nsite * K * sizeof(double));
+#pragma omp parallel
+    {
+        float *st = (float *)malloc((size_t)K * sizeof(float));
+        double *aq = (double *)malloc((size_t)2 * K * sizeof(double));   /* [term][K] */
+#pragma omp for schedule(static)
+        for (int z = 0; z < nz; ++z)
+            for (int x = 0; x < nx; ++x) {
+                size_t site = (size_t)z * nx + x;
+                int c = cls ? cls[site] : 0;
+                const double *S = S_in + site * K;
+                float e = (float)(emis ? emis[site] : 0.0);
+                for (int k = 0; k < K; ++k) st[k] = (float)S[k];
+                for (int d = 0; d < n; ++d) st[4 * d] = st[4 * d] + e;
+                double t = tau[site], w = albedo[site];
+                double kabs = (1.0 - w) * t, ksca = w * t;
+                double A = (abs_mode == ORC_ABS_TAYLOR) ? 1.0 - kabs : exp(-kabs);
+                double s = (surv_mode == ORC_SURV_EXP) ? exp(-ksca) : 1.0 - ksca;
+                double alpha = A * s;
+                float beta = (float)(A * (1.0 - s));
+                for (int blk = 0; blk < n / 8; ++blk) {
+                    float amax = 0.0f;
+                    for (int k = 32 * blk; k < 32 * blk + 32; ++k) amax = fmaxf(amax, fabsf(beta * st[k]));
+                    int e0 = orc_fp8_exponent((double)amax, 1);
+                    double r[32], rmax = 0.0;
+                    for (int k = 0; k < 32; ++k) {
+                        double bs = ldexp((double)(beta * st[32 * blk + k]), -e0);   /* exact scaling */
+                        double q0 = orc_e4m3(bs);
+                        aq[32 * blk + k] = ldexp(q0, e0);
+                        r[k] = bs - q0;
+                        rmax = fmax(rmax, fabs(r[k]));
+                    }
+                    int d = orc_fp8_exponent(rmax, 1);
+                    for (int k = 0; k < 32; ++k)
+                        aq[K + 32 * blk + k] = (e0 + d < -127) ? 0.0 : ldexp(orc_e4m3(ldexp(r[k], -d)), e0 + d);
+                }
+                double *out = P + site * K;
+                for (int row = 0; row < K; ++row) {
+                    double acc = 0.0;
+                    for (int p = 0; p < 5; ++p) {
+                        const double *B = Bt + ((size_t)pairs[p][1] * n_phase + c) * tsz + (size_t)row * K;
+                        const double *a = aq + (size_t)pairs[p][0] * K;
+                        for (int k = 0; k < K; ++k) acc += B[k] * a[k];
+                    }
+                    out[row] = alpha * st[row] + (double)beta * fw[(size_t)c * n + row / 4] * st[row] + acc;
+                }
+            }
+        free(st);
+        free(aq);
+    }
+    stream_all(nx, nz, n, ntap, tx, tz, tw, bc, inflow, P, S_out);
+    free(P);
+    free(Bt);
+    free(fw);
+    free(rem);
 }
 
 /* Steady-state residual: max |S_new - S_old| / max |S_new| over all entries. */

@@ -228,7 +228,7 @@ rtlb_status rtlb_create(const rtlb_grid *grid, const rtlb_directions *dirs, cons
     if (grid->nx < 1 || grid->nz < 1 || grid->nx > 65535 || grid->nz > 65535) return RTLB_E_SHAPE;
     rtlb_options o{};
     if (opts) o = *opts;
-    if (o.precision < RTLB_PREC_FP32 || o.precision > RTLB_PREC_TF32X3 || o.survival < 0 || o.survival > 1 ||
+    if (o.precision < RTLB_PREC_FP32 || o.precision > RTLB_PREC_FP8X || o.survival < 0 || o.survival > 1 ||
         o.absorption < 0 || o.absorption > 1)
         return RTLB_E_ARG;
     std::vector<double> mu, phi, tap_w;

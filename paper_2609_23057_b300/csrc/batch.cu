@@ -88,7 +88,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t tcols = 2 * kMaxN4;
+    // two accumulators D, then two regions E for the exact float32 part (the
+    // MMAs start D from zero and the epilogue adds E, as in the single-lattice
+    // kernel at 4n <= 128)
+    const uint32_t tcols = 4 * kMaxN4;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
@@ -217,7 +220,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int ksteps = min(4, (N4 - 64 * c) / 16);
                         for (int kk = 0; kk < ksteps; ++kk) {
                             const uint32_t ao = c * a_chunk + kk * 32, zo = c * z_chunk + kk * 32;
-                            mma_bf16(d_tmem, sw128_desc(smem_u32(sA + ao)), sw128_desc(smem_u32(sZ + zo)), idesc, 1u);
+                            const uint32_t acc_in = (c == 0 && kk == 0) ? 0u : 1u;   // the item starts D from zero
+                            mma_bf16(d_tmem, sw128_desc(smem_u32(sA + ao)), sw128_desc(smem_u32(sZ + zo)), idesc, acc_in);
                             if (ZLO) mma_bf16(d_tmem, sw128_desc(smem_u32(sA + ao)), sw128_desc(smem_u32(sZlo + zo)), idesc, 1u);
                         }
                     }
@@ -269,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                                    kErrTimeoutConverter));
             if (!ok) break;
             tc_fence_after();
-            const uint32_t acc = tmem + lane_base + (uint32_t)(b * kMaxN4);
+            const uint32_t acc = tmem + lane_base + (uint32_t)(2 * kMaxN4 + b * kMaxN4);   // E of buffer b
             ok = convert_tile<false>(cf, fwd + (size_t)cls * n, r, lane, grp, n, n / kDirsPerStage, stages, gq, i, acc, sA,
                                      sA, sStage, st_full, st_empty, a_empty, a_chunk, abort_flag, err);
             if (!ok) break;
@@ -317,8 +321,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int dn = n / 2, dbeg = dhalf * dn;
             float4 *out = reinterpret_cast<float4 *>(S_new);
             for (int d0 = dbeg; d0 < dbeg + dn; d0 += 4) {
-                float v[16];
+                float v[16], e[16];
                 tmem_ld16(acc + 4 * d0, v);
+                tmem_ld16(acc + (uint32_t)(2 * kMaxN4) + 4 * d0, e);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) v[k] += e[k];
                 if (interior) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {

@@ -31,6 +31,7 @@
 // frees its TMEM and returns; the host reports RTLB_E_TIMEOUT.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
@@ -53,12 +54,13 @@ using namespace tccommon;
 
 struct TcState {
     int N4 = 0, KP = 0, C = 0, n_phase = 0;
-    int mode = 1;                    // 1 bf16, 2 bf16 + table lo, 3 hi+lo both, 4 e4m3 block-scaled, 5 3xTF32
+    int mode = 1;                    // 1 bf16, 2 bf16 + table lo, 3 hi+lo both, 4 e4m3 block-scaled, 5 3xTF32,
+                                     // 6 split e4m3 (state 2 terms, table 3 terms)
     bool pair = false;               // CTA-pair kernel (table rows split over two CTAs)
     __nv_bfloat16 *d_Zhi = nullptr;  // [n_phase][N4][KP]
     __nv_bfloat16 *d_Zlo = nullptr;
-    uint8_t *d_Z8 = nullptr;         // FP8: [n_phase][N4][KP8] e4m3
-    uint8_t *d_sfb = nullptr;        // FP8: [n_phase][N4][N4 / 32] UE8M0 block scales of the table
+    uint8_t *d_Z8 = nullptr;         // FP8: [n_phase][N4][KP8] e4m3 (FP8X: [3][n_phase][N4][KP8], one per term)
+    uint8_t *d_sfb = nullptr;        // FP8: [n_phase][N4][N4 / 32] UE8M0 block scales of the table (FP8X: [3][...])
     float *d_Zt_hi = nullptr;        // TF32X3: [n_phase][N4][N4] tf32 hi part (float32 container)
     float *d_Zt_lo = nullptr;        // TF32X3: tf32 lo part
     int *d_pure = nullptr;           // tile | class << 24, sorted by class (pairs: 2 per entry)
@@ -115,7 +117,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     int8_t *s_cz = s_cx + kMaxDirs;                              // [n]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t tcols = N4 * 2 <= 32 ? 32u : (N4 * 2 <= 64 ? 64u : (N4 * 2 <= 128 ? 128u : (N4 * 2 <= 256 ? 256u : 512u)));
+    // 4n <= 128: the exact float32 part goes into its own TMEM region E (two
+    // buffers after the two accumulators) and the MMAs start D from zero; the
+    // epilogue adds E.  The tensor core rounds each instruction's float32 sum
+    // toward zero, so an accumulator holding the unscattered light would lose
+    // a fraction of an ulp of it per instruction, step after step.  At 4n =
+    // 256 the two accumulators fill TMEM and the part is written into D.
+    const bool sepE = N4 <= 128;
+    const int need = sepE ? 4 * N4 : 2 * N4;
+    const uint32_t tcols = need <= 32 ? 32u : (need <= 64 ? 64u : (need <= 128 ? 128u : (need <= 256 ? 256u : 512u)));
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
@@ -243,7 +253,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int ksteps = min(4, (N4 - 64 * c) / 16);
                     for (int kk = 0; kk < ksteps; ++kk) {
                         const uint32_t ao = c * a_chunk + kk * 32, zo = c * z_chunk + kk * 32;
-                        mma_bf16(d_tmem, sw128_desc(smem_u32(sA + ao)), sw128_desc(smem_u32(sZ + zo)), idesc, 1u);
+                        const uint32_t acc_in = (sepE && c == 0 && kk == 0) ? 0u : 1u;   // E: the tile starts D from zero
+                        mma_bf16(d_tmem, sw128_desc(smem_u32(sA + ao)), sw128_desc(smem_u32(sZ + zo)), idesc, acc_in);
                         if (ZLO) mma_bf16(d_tmem, sw128_desc(smem_u32(sA + ao)), sw128_desc(smem_u32(sZlo + zo)), idesc, 1u);
                         if (ALO) mma_bf16(d_tmem, sw128_desc(smem_u32(sAlo + ao)), sw128_desc(smem_u32(sZ + zo)), idesc, 1u);
                     }
@@ -286,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                                    kErrTimeoutConverter));
             if (!ok) break;
             tc_fence_after();
-            const uint32_t acc = tmem + lane_base + (uint32_t)(b * N4);
+            const uint32_t acc = tmem + lane_base + (uint32_t)((sepE ? 2 * N4 : 0) + b * N4);   // E, else D
             ok = convert_tile<ALO>(cf, p.fwd + (size_t)(entry >> 24) * n, r, lane, grp, n, groups, stages, gq, i, acc, sA,
                                    sAlo, sStage, st_full, st_empty, a_empty, a_chunk, abort_flag, p.err);
             if (!ok) break;
@@ -319,6 +330,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int d0 = dbeg; d0 < dbeg + dn; d0 += 4) {
                 float v[16];
                 tmem_ld16(acc + 4 * d0, v);
+                if (sepE) {
+                    float e[16];
+                    tmem_ld16(acc + (uint32_t)(2 * N4) + 4 * d0, e);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) v[k] += e[k];
+                }
                 if (interior) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
@@ -777,6 +794,7 @@ int mode_of(int precision)
 {
     if (precision == RTLB_PREC_FP8) return 4;
     if (precision == RTLB_PREC_TF32X3) return 5;
+    if (precision == RTLB_PREC_FP8X) return 6;
     return precision == RTLB_PREC_BF16X3 ? 3 : (precision == RTLB_PREC_BF16X2 ? 2 : 1);
 }
 
@@ -791,7 +809,8 @@ int fit_stages(int N4, int mode, bool pair)
     for (int st = RTLB_TC_MAX_STAGES & ~1; st >= 2; st -= 2)
         if ((pair ? smem_bytes_pair(N4, st)
                   : (mode == 4 ? tc_fp8_smem_bytes(N4, st)
-                               : (mode == 5 ? tc_tf32_smem_bytes(N4, st) : smem_bytes(N4, mode, st)))) <=
+                               : (mode == 5 ? tc_tf32_smem_bytes(N4, st)
+                                            : (mode == 6 ? tc_fp8x_smem_bytes(N4, st) : smem_bytes(N4, mode, st))))) <=
             (size_t)kSmemLimit)
             return st;
     return 0;
@@ -857,14 +876,16 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
     const int n = c->n;
     std::vector<float> fwd((size_t)n_phase * n, 0.0f);
     std::vector<double> work(tsz);
-    const bool fp8 = mode == 4;
+    const bool fp8 = mode == 4 || mode == 6;
+    const int terms = mode == 6 ? 3 : 1;          // e4m3 terms of the table
     const int KP8 = ((N4 + 127) / 128) * 128, ksteps = N4 / 32;
     std::vector<__nv_bfloat16> hi((fp8 || tf32) ? 0 : (size_t)n_phase * psz, __float2bfloat16(0.0f)),
         lo(hi.size(), __float2bfloat16(0.0f));
     std::vector<float> thi(tf32 ? (size_t)n_phase * tsz : 0, 0.0f), tlo(thi.size(), 0.0f);
-    std::vector<uint8_t> z8(fp8 ? (size_t)n_phase * N4 * KP8 : 0, 0), sfb(fp8 ? (size_t)n_phase * N4 * ksteps : 0, 0);
-    if (fp8 && tc_fp8_tmem_columns(N4, n_phase) > 512) {
-        c->err = "the FP8 form keeps every class's table scales in tensor memory: too many phase classes for this n";
+    std::vector<uint8_t> z8(fp8 ? (size_t)terms * n_phase * N4 * KP8 : 0, 0),
+        sfb(fp8 ? (size_t)terms * n_phase * N4 * ksteps : 0, 0);
+    if (fp8 && (mode == 6 ? tc_fp8x_tmem_columns(N4, n_phase) : tc_fp8_tmem_columns(N4, n_phase)) > 512) {
+        c->err = "the FP8 forms keep every class's table scales in tensor memory: too many phase classes for this n";
         return RTLB_E_UNSUPPORTED;
     }
     for (int ph = 0; ph < n_phase; ++ph) {
@@ -891,19 +912,25 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
                 for (int a = 0; a < 4; ++a)
                     work[(size_t)(4 * i + a) * N4 + 4 * i + a] = ci - (double)(float)ci;
             }
-        if (mode == 4) {
-            // e4m3 with one UE8M0 scale per table row and 32-element block
-            for (int row = 0; row < N4; ++row)
-                for (int ks = 0; ks < ksteps; ++ks) {
-                    const double *blk = &work[(size_t)row * N4 + 32 * ks];
-                    double amax = 0.0;
-                    for (int k = 0; k < 32; ++k) amax = std::max(amax, std::fabs(blk[k]));
-                    const int e = table_block_exponent(amax);
-                    sfb[((size_t)ph * N4 + row) * ksteps + ks] = (uint8_t)(e + 127);
-                    for (int k = 0; k < 32; ++k)
-                        z8[(size_t)ph * N4 * KP8 + (size_t)row * KP8 + 32 * ks + k] =
-                            (uint8_t)__nv_cvt_double_to_fp8(std::ldexp(blk[k], -e), __NV_SATFINITE, __NV_E4M3);
-                }
+        if (fp8) {
+            // e4m3 with one UE8M0 scale per table row and 32-element block; the
+            // split form quantizes what the terms before left, each term with
+            // the scale of that remainder
+            for (int t = 0; t < terms; ++t)
+                for (int row = 0; row < N4; ++row)
+                    for (int ks = 0; ks < ksteps; ++ks) {
+                        double *blk = &work[(size_t)row * N4 + 32 * ks];
+                        double amax = 0.0;
+                        for (int k = 0; k < 32; ++k) amax = std::max(amax, std::fabs(blk[k]));
+                        const int e = table_block_exponent(amax);
+                        const size_t tp = (size_t)t * n_phase + ph;
+                        sfb[(tp * N4 + row) * ksteps + ks] = (uint8_t)(e + 127);
+                        for (int k = 0; k < 32; ++k) {
+                            const __nv_fp8_storage_t q = __nv_cvt_double_to_fp8(std::ldexp(blk[k], -e), __NV_SATFINITE, __NV_E4M3);
+                            z8[tp * N4 * KP8 + (size_t)row * KP8 + 32 * ks + k] = (uint8_t)q;
+                            blk[k] -= std::ldexp((double)__half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3))), e);
+                        }
+                    }
             continue;
         }
         if (tf32) {
@@ -994,7 +1021,7 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
     }
     const int box_rows = pair ? N4 / 2 : N4;
     const bool maps_ok =
-        fp8 ? encode_z8_map(&t->tmZhi, t->d_Z8, N4, KP8, n_phase)
+        fp8 ? encode_z8_map(&t->tmZhi, t->d_Z8, N4, KP8, terms * n_phase)
             : tf32 ? (encode_zt_map(&t->tmZhi, t->d_Zt_hi, N4, n_phase) && encode_zt_map(&t->tmZlo, t->d_Zt_lo, N4, n_phase))
                    : (encode_z_map(&t->tmZhi, t->d_Zhi, N4, KP, n_phase, box_rows) &&
                       (!split || encode_z_map(&t->tmZlo, t->d_Zlo, N4, KP, n_phase, box_rows)));
@@ -1014,7 +1041,9 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
     t->n_mixed = (int)mixed.size();
     t->stages = stages;
     t->smem = pair ? smem_bytes_pair(N4, stages)
-                   : (fp8 ? tc_fp8_smem_bytes(N4, stages) : (tf32 ? tc_tf32_smem_bytes(N4, stages) : smem_bytes(N4, mode, stages)));
+                   : (mode == 4 ? tc_fp8_smem_bytes(N4, stages)
+                                : (mode == 6 ? tc_fp8x_smem_bytes(N4, stages)
+                                             : (tf32 ? tc_tf32_smem_bytes(N4, stages) : smem_bytes(N4, mode, stages))));
     return RTLB_OK;
 }
 
@@ -1054,6 +1083,9 @@ rtlb_status tc_step(rtlb_ctx *c, const StepParams &p, cudaStream_t s)
         if (t->mode == 4) {
             e = launch_step_tc_fp8(t->tmS[which], t->tmZhi, tp, t->d_sfb, t->N4, t->stages, t->n_phase,
                                    std::min(t->sm_count, t->n_pure), s);
+        } else if (t->mode == 6) {
+            e = launch_step_tc_fp8x(t->tmS[which], t->tmZhi, tp, t->d_sfb, t->N4, t->stages, t->n_phase,
+                                    std::min(t->sm_count, t->n_pure), s);
         } else if (t->mode == 5) {
             e = launch_step_tc_tf32(t->tmS[which], t->tmZhi, t->tmZlo, tp, t->N4, t->stages,
                                     std::min(t->sm_count, t->n_pure), s);

@@ -2,6 +2,8 @@
 // pair, and the multi-channel batch): tile geometry, warp roles, error codes
 // and the converter routine.
 #pragma once
+#include <cuda_fp8.h>
+
 #include "tc_ptx.cuh"
 
 namespace rtlb {
@@ -150,6 +152,25 @@ __device__ __forceinline__ bool convert_tile(const float4 cf, const float *fwd, 
     return true;
 }
 
+// UE8M0 exponent of a block whose largest |value| is amax (float32): the
+// smallest e with amax / 2^e <= 448 (the largest finite e4m3), clamped to the
+// scale range; zero and subnormal amax take the smallest scale.
+__device__ __forceinline__ int block_exponent(float amax)
+{
+    const uint32_t bits = __float_as_uint(amax);
+    const int ex = (int)((bits >> 23) & 0xFFu);
+    if (ex == 0) return -127;
+    const int e = ex - 127 - 8 + ((bits & 0x7FFFFFu) > 0x600000u ? 1 : 0);   // mantissa above 1.75
+    return e < -127 ? -127 : e;
+}
+
+// Two e4m3 values (round to nearest even, saturating at +-448), first in the
+// low byte.
+__device__ __forceinline__ uint32_t e4m3x2(float lo, float hi)
+{
+    return (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(lo, hi), __NV_SATFINITE, __NV_E4M3);
+}
+
 }  // namespace tccommon
 
 // 3xTF32 form (tc_tf32.cu), 4n <= 128: shared memory for a stage count and the
@@ -158,6 +179,14 @@ __device__ __forceinline__ bool convert_tile(const float4 cf, const float *fwd, 
 size_t tc_tf32_smem_bytes(int N4, int stages);
 cudaError_t launch_step_tc_tf32(const CUtensorMap &tmS, const CUtensorMap &tmZhi, const CUtensorMap &tmZlo,
                                 const tccommon::TcParams &p, int N4, int stages, int grid, cudaStream_t s);
+
+// Split FP8 form (tc_fp8x.cu): state operand in two e4m3 terms, table in
+// three (z8 [3][n_phase][4n][KP8], sfb [3][n_phase][4n][4n / 32]); TMEM
+// columns it needs (<= 512), shared memory for a stage count, and the launch.
+int tc_fp8x_tmem_columns(int N4, int n_phase);
+size_t tc_fp8x_smem_bytes(int N4, int stages);
+cudaError_t launch_step_tc_fp8x(const CUtensorMap &tmS, const CUtensorMap &tmZ, const tccommon::TcParams &p,
+                                const uint8_t *sfb, int N4, int stages, int n_phase, int grid, cudaStream_t s);
 
 // FP8 block-scaled form (tc_fp8.cu): TMEM columns it needs (D, A scales, the
 // B scales of every class; must be <= 512), shared memory for a stage count,

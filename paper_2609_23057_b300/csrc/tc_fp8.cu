@@ -50,25 +50,6 @@ using namespace tccommon;
 // (columns + n / 32 used, N4 <= 256).
 constexpr int kSfCols = 8;
 
-// UE8M0 exponent of a block whose largest |value| is amax (float32): the
-// smallest e with amax / 2^e <= 448 (the largest finite e4m3), clamped to the
-// scale range; zero and subnormal amax take the smallest scale.
-__device__ __forceinline__ int block_exponent(float amax)
-{
-    const uint32_t bits = __float_as_uint(amax);
-    const int ex = (int)((bits >> 23) & 0xFFu);
-    if (ex == 0) return -127;
-    const int e = ex - 127 - 8 + ((bits & 0x7FFFFFu) > 0x600000u ? 1 : 0);   // mantissa above 1.75
-    return e < -127 ? -127 : e;
-}
-
-// Two e4m3 values (round to nearest even, saturating at +-448), first in the
-// low byte.
-__device__ __forceinline__ uint32_t e4m3x2(float lo, float hi)
-{
-    return (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(lo, hi), __NV_SATFINITE, __NV_E4M3);
-}
-
 __global__ void __launch_bounds__(kThreads, 1)
     k_step_tc_fp8(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmZ, TcParams p,
                   const uint8_t *__restrict__ sfb, int N4, int stages, int n_phase, uint32_t tcols, int colA, int colB)

@@ -11,7 +11,7 @@ import numpy as np
 from . import _lib
 from ._lib import Directions, Grid, Options, check, lib
 
-PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2, "bf16x2": 3, "fp8": 4, "tf32x3": 5}
+PRECISIONS = {"fp32": 0, "bf16": 1, "bf16x3": 2, "bf16x2": 3, "fp8": 4, "tf32x3": 5, "fp8x": 6}
 SURVIVAL = {"linear": 0, "exp": 1}
 ABSORPTION = {"beer_lambert": 0, "taylor": 1}
 SIDES = {"top": 0, "bottom": 1, "left": 2, "right": 3}

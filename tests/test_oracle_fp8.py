@@ -153,3 +153,97 @@ def test_fp8_step_within_e4m3_bound(n):
     err = np.abs(got.ravel() - ref.ravel())
     assert np.all(err <= bound)
     assert err.max() > 0          # the form does round
+
+
+# ---- the split form (orc_step_fp8x): state in two e4m3 terms, table in three
+
+
+def _bits_table(rng, K, mant_bits, k_lo):
+    """Entries (1 + j / 2^mant_bits) 2^k with one exponent k per 32-entry block
+    (k in [k_lo, k_lo + 5]), random signs, 20 % zeros: a block's terms then
+    carry 4 significant bits each, so 4 mantissa bits fit one e4m3 term, 8 two
+    and 11 three."""
+    m = 1 + rng.integers(0, 2 ** mant_bits, size=(K, K)) / 2.0 ** mant_bits
+    k = np.repeat(rng.integers(k_lo, k_lo + 6, size=(K, K // 32)), 32, axis=1)
+    Z = m * 2.0 ** k * rng.choice([-1.0, 1.0], size=(K, K))
+    Z[rng.random((K, K)) < 0.2] = 0.0
+    return Z
+
+
+@pytest.mark.parametrize("n", [8, 32])
+@pytest.mark.parametrize("z_lo,s_lo", [(-6, -3), (-16, -20), (10, 6)])
+@pytest.mark.parametrize("state_bits,table_bits", [(7, 7), (3, 11)])
+def test_fp8x_step_exact_when_representable(n, z_lo, s_lo, state_bits, table_bits):
+    """beta = 0.25, alpha = 0.75 exactly (as above).  A state with 7-bit
+    mantissas needs both state terms and a table with 7-bit mantissas two of
+    its three terms: every product the form keeps is exact and the one it
+    drops (state lo x table term 3) is zero, so the form equals the FP64
+    step; likewise a 3-bit state (one term) with an 11-bit table (all three
+    terms).  Dropping any kept product, or a wrong scale for a lo term, breaks
+    the equality."""
+    rng = np.random.default_rng([n, z_lo + 100, state_bits])
+    K = 4 * n
+    Z = _bits_table(rng, K, table_bits, z_lo)
+    mant = 1 + rng.integers(0, 2 ** state_bits, size=K) / 2.0 ** state_bits
+    kexp = np.repeat(rng.integers(s_lo, s_lo + 2, size=K // 32), 32)   # one exponent range per block
+    S = (mant * 2.0 ** kexp).reshape(1, 1, n, 4)
+    P = _single_site(n, Z, S, 0.25, 1.0, orc.SURV_LINEAR)
+    ref = P.step(S)
+    got = P.step_fp8x(S)
+    scat = 0.25 * Z @ S.ravel()
+    assert np.abs(got.ravel() - ref.ravel()).max() <= 1e-14 * np.abs(scat).max()
+    # the single-term form does not represent these operands
+    if state_bits > 3 or table_bits > 3:
+        assert np.abs(P.step_fp8(S).ravel() - ref.ravel()).max() > 1e-6 * np.abs(scat).max()
+
+
+@pytest.mark.parametrize("n", [8, 32, 64])
+def test_fp8x_step_within_split_bound(n):
+    """Realistic table (HG + polarization) and state.  The two state terms
+    leave at most u^2 |x| of each value (u = 2^-4), the three table terms
+    u^3 |w|, and the dropped product (state lo x table term 3) is below
+    u^3 (1 + u)^2 |x| |w|, so |P_fp8x - P| <= (u^2 + 2.3 u^3) beta
+    sum_k |Z_rk| |S~_k| plus an absolute floor for entries far below their
+    block's largest (subnormal spacing of the lo terms).  The split form is
+    also far closer than the single-term form."""
+    nzen, naz = {8: (2, 4), 32: (4, 8), 64: (8, 8)}[n]
+    mu, phi = orc.direction_grid(nzen, naz)
+    Z = orc.phase_table(mu, phi, orc.PHASE_HG, 0.85, -0.1)
+    rng = np.random.default_rng(n + 7)
+    S = rng.random((1, 1, n, 4)).astype(np.float32).astype(np.float64)
+    S[..., 1:] *= 0.3
+    tau, w = 0.6, 0.95
+    P = _single_site(n, Z, S, tau, w, orc.SURV_EXP)
+    ref = P.step(S)
+    got = P.step_fp8x(S)
+    A = np.exp(-(1 - w) * tau)
+    beta = A * (1 - np.exp(-w * tau))
+    u = 2.0 ** -4
+    mag = beta * (np.abs(Z) @ np.abs(S.ravel()))
+    bound = (u * u + 2.3 * u ** 3) * mag + 2.0 ** -20 * beta * np.abs(S).max() * np.abs(Z).sum(axis=1) \
+        + 1e-6 * np.abs(ref).max() * 2.0 ** -10
+    err = np.abs(got.ravel() - ref.ravel())
+    assert np.all(err <= bound)
+    assert err.max() > 0
+    err1 = np.abs(P.step_fp8(S).ravel() - ref.ravel())
+    assert err.max() < 0.1 * err1.max()
+
+
+@pytest.mark.parametrize("n", [8, 32])
+def test_fp8x_lo_term_has_its_own_scale(n):
+    """Each 32-value block of the state holds one large value that e4m3 holds
+    exactly (so it leaves no remainder) and small values with 7-bit mantissas
+    2^12 below it.  The hi term's scale is set by the large value; the small
+    values' remainders lie below e4m3's smallest subnormal at that scale, so
+    only a lo term scaled from the remainders' own maximum keeps them, and
+    then the form is exact (table exact in one term)."""
+    rng = np.random.default_rng(n + 11)
+    K = 4 * n
+    Z = _bits_table(rng, K, 3, -4)
+    S = (1 + rng.integers(0, 128, size=K) / 128.0) * 2.0 ** -12
+    S[::32] = 1.5                                  # one e4m3-exact value per block
+    S = S.reshape(1, 1, n, 4)
+    P = _single_site(n, Z, S, 0.25, 1.0, orc.SURV_LINEAR)
+    ref = P.step(S)
+    scat = 0.25 * Z @ S.ravel()
+    assert np.abs(P.step_fp8x(S).ravel() - ref.ravel()).max() <= 1e-14 * np.abs(scat).max()

@@ -119,21 +119,18 @@ def test_full_size_sampled_sites_tc(torch_cuda, orc, prec):
         assert rel_err_I(g, r) < 2 * 2 * U_BF16, (z, x)
 
 
-def test_crop_radiance_error_1000_steps_split_table(torch_cuda, orc):
+def test_crop_radiance_error_1000_steps_split_table(torch_cuda, orc, crop_ref_1000):
     """Same crop, 1000 steps: the split-table form (bf16 state operand, table
     as bf16 hi + lo; n = 64 runs on CTA pairs) meets the 1e-3 relative error
     on the top radiance and on its degree of polarization."""
-    w = W.precision_crop(steps=1000)
-    P = oracle_problem(orc, w)
-    ref = P.run(P.zero_state(), w.steps)
-    top_ref = P.radiance_out(ref, orc.SIDE_TOP)
+    w, P, ref, top_ref = crop_ref_1000
     got = _run(torch_cuda, w, "bf16x2", np.zeros((w.nz, w.nx, w.n, 4)), w.steps)
     top_got = P.radiance_out(got, orc.SIDE_TOP)
     assert rel_err_I(top_got, top_ref, floor_frac=1e-3) < 1e-3
     assert abs_err_dop(top_got, top_ref, floor_frac=1e-3) < 1e-3
 
 
-def test_crop_radiance_error_1000_steps(torch_cuda, orc):
+def test_crop_radiance_error_1000_steps(torch_cuda, orc, crop_ref_1000):
     """The 256x256 crop [896,1152)^2 of the 2048x2048 n = 64 medium, run for
     1000 steps from zero as its own problem: top-of-domain radiance of the
     single-MMA bf16 form against the FP64 oracle.  The error is set by the
@@ -141,10 +138,7 @@ def test_crop_radiance_error_1000_steps(torch_cuda, orc):
     step): a CPU emulation with an exact table and bf16 state gives 8e-4,
     with an exact state and bf16 table 2.2e-3.  Bound 5e-3 (2.5 u); the
     float32 path meets 1e-5 on the same case."""
-    w = W.precision_crop(steps=1000)
-    P = oracle_problem(orc, w)
-    ref = P.run(P.zero_state(), w.steps)
-    top_ref = P.radiance_out(ref, orc.SIDE_TOP)
+    w, P, ref, top_ref = crop_ref_1000
     got = _run(torch_cuda, w, "bf16", np.zeros((w.nz, w.nx, w.n, 4)), w.steps)
     top_got = P.radiance_out(got, orc.SIDE_TOP)
     assert rel_err_I(top_got, top_ref, floor_frac=1e-3) < 2.5 * 2 * U_BF16
