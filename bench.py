@@ -258,7 +258,8 @@ def _measured_traffic(kernel, sites):
             rec = json.load(f)[kernel]
     except (OSError, KeyError, ValueError):
         return None
-    files = ("tc_fp8.cu" if kernel == "k_step_tc_fp8" else "tc.cu", "step_common.cuh", "tc_common.cuh", "tc_ptx.cuh")
+    src_of = {"k_step_tc_fp8": "tc_fp8.cu", "k_step_tc_fp8x": "tc_fp8x.cu", "k_step_tc_tf32": "tc_tf32.cu"}
+    files = (src_of.get(kernel, "tc.cu"), "step_common.cuh", "tc_common.cuh", "tc_ptx.cuh")
     src = b"".join(open(os.path.join(HERE, "paper_2609_23057_b300", "csrc", fn), "rb").read() for fn in files)
     if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"]:
         return None
@@ -279,8 +280,9 @@ def _roofline(precision, n, sdu_per_launch, avg_launch_s, peaks, src):
             "traffic": None, "peak_source": f"hbm_gbs of {src} MEASURED_PEAKS"}
 
 
-# tensor-core kernel of each precision at n = 64
-KERNEL = {"bf16": "k_step_tc", "bf16x2": "k_step_tc_pair", "bf16x3": "k_step_tc", "fp8": "k_step_tc_fp8"}
+# tensor-core kernel of each precision at n = 64 (tf32x3: n <= 32)
+KERNEL = {"bf16": "k_step_tc", "bf16x2": "k_step_tc_pair", "bf16x3": "k_step_tc", "fp8": "k_step_tc_fp8",
+          "fp8x": "k_step_tc_fp8x", "tf32x3": "k_step_tc_tf32"}
 
 
 def accuracy(precisions, steps):
@@ -313,18 +315,22 @@ def accuracy(precisions, steps):
 
 def fp32_class(steps: int, peaks, src):
     """The float32-accuracy forms on the 512x512, n = 32 steady-state medium:
-    BF16X3 (tensor cores, bf16 hi+lo operands, three MMAs) against FP32 (CUDA
-    cores): CUDA-event time per step over `steps` steps, and the error of each
-    against the FP64 oracle on the 128x128 centre crop run as its own problem
-    for 100 steps from zero."""
+    TF32X3 (tensor cores, tf32 hi+lo operands, three MMAs, state operand in
+    tensor memory) and BF16X3 (bf16 hi+lo operands) against FP32 (CUDA cores):
+    CUDA-event time per step over `steps` steps, and the error of each against
+    the FP64 oracle on the 128x128 centre crop run as its own problem for 100
+    steps from zero (relative on I, absolute on the degree of
+    polarization)."""
     import torch
     import oracle
     from paper_2609_23057_b300.solver import solver_for
     sys.path.insert(0, os.path.join(HERE, "tests"))
     from _util import oracle_problem, rel_err_I
+    from _util import abs_err_dop
     w = W.steady()
     out = {"workload": w.name, "steps": steps}
-    for prec in ("bf16x3", "fp32"):
+    forms = ("tf32x3", "bf16x3", "fp32")
+    for prec in forms:
         s = solver_for(w, prec)
         s.step(3)
         torch.cuda.synchronize()
@@ -333,18 +339,20 @@ def fp32_class(steps: int, peaks, src):
         ms = tot / len(per)
         sdu = w.sites * w.n
         entry = {"ms_per_step": ms, "value": sdu / (ms * 1e-3), "unit": UNIT}
-        if prec == "bf16x3":
+        if prec != "fp32":
             entry["roofline"] = _roofline(prec, w.n, sdu, statistics.mean(per) * 1e-3, peaks, src)
+            entry["roofline"]["kernel"] = KERNEL[prec]
         out[prec] = entry
     c = w.crop(192, 320, 192, 320, name="lattice512_n32_crop128")
     P = oracle_problem(oracle, c)
     ref = P.run(P.zero_state(), 100)
-    for prec in ("bf16x3", "fp32"):
+    for prec in forms:
         s = solver_for(c, prec)
         s.step(100)
         got = s.get_state().cpu().numpy().astype(np.float64)
         s.close()
         out[prec]["rel_err_I_state_crop128_100steps"] = rel_err_I(got, ref, floor_frac=1e-3)
+        out[prec]["abs_err_dop_state_crop128_100steps"] = abs_err_dop(got, ref, floor_frac=1e-3)
     return out
 
 
@@ -463,10 +471,11 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if args.nx == 2048 and args.nz == 2048:
+    if args.nx == 2048 and args.nz == 2048 and (args.nzen, args.naz) == (8, 8):
         w = W.precision(seed=1, steps=args.steps)
     else:
-        w = W.cloud(f"lattice{args.nx}x{args.nz}_n64", args.nx, args.nz, 8, 8, seed=1, steps=args.steps)
+        w = W.cloud(f"lattice{args.nx}x{args.nz}_n{args.nzen * args.naz}", args.nx, args.nz, args.nzen, args.naz,
+                    seed=1, steps=args.steps)
     n, sites = w.n, w.sites
     sdu_per_step = sites * n
     stream = torch.cuda.current_stream(dev)
@@ -513,7 +522,7 @@ def run_ours(args):
     # comparison forms after the headline, each on its own context; a form
     # that fails records its error instead of ending the run
     compare = {}
-    others = [] if args.no_compare else [p for p in ("fp32", "bf16", "fp8") if p != args.precision]
+    others = [] if args.no_compare else [p for p in ("fp32", "bf16", "fp8", "fp8x") if p != args.precision]
     for prec in others:
         def one(prec=prec):
             sc = SV.solver_for(w, prec)
@@ -535,7 +544,7 @@ def run_ours(args):
 
     roof = _roofline(args.precision, n, sdu_per_step, statistics.mean(per_launch) * 1e-3, peaks, src)
     if args.precision != "fp32":
-        kern = KERNEL[args.precision] if n == 64 else ("k_step_tc_fp8" if args.precision == "fp8" else "k_step_tc")
+        kern = KERNEL[args.precision] if (n == 64 or args.precision != "bf16x2") else "k_step_tc"
         roof["kernel"] = kern
         roof["traffic"] = _measured_traffic(kern, sites)
         roof["traffic_note"] = "DRAM bytes per launch from profiles/traffic.json, scaled by sites"
@@ -545,7 +554,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x2": "bf16x2", "bf16x3": "bf16x3",
-                      "fp8": "e4m3"}[args.precision],
+                      "fp8": "e4m3", "fp8x": "e4m3x2/e4m3x3", "tf32x3": "tf32x3"}[args.precision],
             "data": "synthetic",
             "config": {"workload": w.name, "nx": w.nx, "nz": w.nz, "n_dirs": n,
                        "precision": args.precision,
@@ -554,7 +563,10 @@ def run_ours(args):
                                       "bf16x2": "bf16 state operand, bf16 hi+lo table (2 MMAs), float32 accumulate",
                                       "bf16x3": "bf16 hi+lo operands (3 MMAs), float32 accumulate",
                                       "fp8": "e4m3 operands with UE8M0 scales per 32-element block "
-                                             "(block-scaled MMA), float32 accumulate, float32 state"}[args.precision],
+                                             "(block-scaled MMA), float32 accumulate, float32 state",
+                                      "fp8x": "state operand as 2 and table as 3 block-scaled e4m3 terms "
+                                              "(5 MMAs), float32 accumulate, float32 state",
+                                      "tf32x3": "tf32 hi+lo operands (3 MMAs), float32 accumulate"}[args.precision],
                        "sites": sites, "phase_classes": 2,
                        "l2": "inputs larger than L2 (4.3 GB state per buffer)",
                        "parallelism": f"replicas{ws}" if ws > 1 else "single"},
@@ -577,7 +589,7 @@ def run_ours(args):
         if ws == 1 and args.fp32_class_steps > 0:
             line["fp32_class"] = _leg(fp32_class, args.fp32_class_steps, peaks, src)
         if ws == 1 and args.accuracy_steps > 0:
-            precs = [args.precision] + [p for p in ("bf16", "fp8", "fp32") if p != args.precision]
+            precs = [args.precision] + [p for p in ("fp8x", "bf16", "fp8", "fp32") if p != args.precision]
             line["accuracy"] = _leg(accuracy, precs, args.accuracy_steps)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = _leg(cpu_baseline, args.steps)
@@ -593,7 +605,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x2", "bf16x3", "fp8"], default="bf16x2",
+    ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x2", "bf16x3", "fp8", "fp8x", "tf32x3"], default="bf16x2",
                     help="headline form; bf16x2 is the tensor-core form that meets 1e-3 on the crop")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the FP32 comparison form")
@@ -607,6 +619,8 @@ def main():
                     help="steps of the 1024x256 adjoint timing (0 = skip)")
     ap.add_argument("--nx", type=int, default=2048, help="lattice width (profiling of smaller cases)")
     ap.add_argument("--nz", type=int, default=2048, help="lattice height (profiling of smaller cases)")
+    ap.add_argument("--nzen", type=int, default=8, help="zenith directions (profiling of other n)")
+    ap.add_argument("--naz", type=int, default=8, help="azimuth directions (profiling of other n)")
     ap.add_argument("--accuracy-steps", type=int, default=1000,
                     help="steps of the 256x256 crop compared with the oracle (0 = skip)")
     args = ap.parse_args()

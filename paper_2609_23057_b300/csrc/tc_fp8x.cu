@@ -64,9 +64,8 @@ using namespace tccommon;
 
 constexpr int kSfCols = 8;     // scale regions start on 8-column boundaries
 constexpr int kTerms = 3;      // table terms
-constexpr int kPairs = 5;
-__constant__ int kPairA[kPairs] = {0, 0, 0, 1, 1};
-__constant__ int kPairB[kPairs] = {0, 1, 2, 0, 1};
+// products issued per K step: (state term, table term) = (0,0), (0,1), (0,2),
+// (1,0), (1,1)
 
 // D[tmem] (+)= A[tmem] . B[smem]^T, e4m3 operands, block scales (see mma_mxf8).
 __device__ __forceinline__ void mma_mxf8_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
@@ -261,6 +260,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == kMmaWarp) {
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
+            // descriptors of the three table terms; a byte offset o (a multiple
+            // of 16) moves a descriptor by o >> 4 (its start-address field)
+            uint64_t bz[kTerms];
+#pragma unroll
+            for (int b = 0; b < kTerms; ++b) bz[b] = sw128_desc(smem_u32(sZ + (uint32_t)(b * C8) * z_chunk));
             int prev_cls = -1;
             uint32_t zl = 0;
             bool ok = true, issued = false;
@@ -275,18 +279,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ok = mbar_wait(smem_u32(t_ready), i & 1, abort_flag, p.err, kErrTimeoutMma);
                 if (!ok) break;
                 tc_fence_after();
-                for (int ks = 0; ks < ksteps; ++ks) {
-                    const uint32_t off = (uint32_t)(ks & 3) * 32u + (uint32_t)(ks / 4) * z_chunk;
-                    const uint32_t idesc = idesc_mxf8(kTileM, N4, ks >> 1, ks & 3);
+                uint32_t sbb[kTerms];                  // B scale columns of this class, per term
 #pragma unroll
-                    for (int pr = 0; pr < kPairs; ++pr) {
-                        const int a = kPairA[pr], b = kPairB[pr];
-                        const uint32_t at = tmem + (uint32_t)((a ? colA1 : colA0) + 8 * ks);
-                        const uint64_t bd = sw128_desc(smem_u32(sZ + (uint32_t)(b * C8) * z_chunk + off));
-                        const uint32_t sa = tmem + (uint32_t)(colSA + kSfCols * (2 * a + (ks & 1)));
-                        const uint32_t sb = tmem + (uint32_t)(colSB + ((b * n_phase + cls) * bsets + ks / 4) * kSfCols);
-                        mma_mxf8_ts(tmem, at, bd, idesc, sa, sb, 1u);
-                    }
+                for (int b = 0; b < kTerms; ++b) sbb[b] = tmem + (uint32_t)(colSB + (b * n_phase + cls) * bsets * kSfCols);
+                for (int ks = 0; ks < ksteps; ++ks) {
+                    const uint64_t doff = (uint64_t)(((uint32_t)(ks & 3) * 32u + (uint32_t)(ks / 4) * z_chunk) >> 4);
+                    const uint32_t idesc = idesc_mxf8(kTileM, N4, ks >> 1, ks & 3);
+                    const uint32_t sa0 = tmem + (uint32_t)(colSA + kSfCols * (ks & 1));   // term 0; term 1 two regions on
+                    const uint32_t sbo = (uint32_t)((ks / 4) * kSfCols);
+                    const uint32_t a0 = tmem + (uint32_t)(colA0 + 8 * ks), a1 = tmem + (uint32_t)(colA1 + 8 * ks);
+                    mma_mxf8_ts(tmem, a0, bz[0] + doff, idesc, sa0, sbb[0] + sbo, 1u);
+                    mma_mxf8_ts(tmem, a0, bz[1] + doff, idesc, sa0, sbb[1] + sbo, 1u);
+                    mma_mxf8_ts(tmem, a0, bz[2] + doff, idesc, sa0, sbb[2] + sbo, 1u);
+                    mma_mxf8_ts(tmem, a1, bz[0] + doff, idesc, sa0 + 2 * kSfCols, sbb[0] + sbo, 1u);
+                    mma_mxf8_ts(tmem, a1, bz[1] + doff, idesc, sa0 + 2 * kSfCols, sbb[1] + sbo, 1u);
                 }
                 mma_commit(smem_u32(acc_full));
                 if (i + 1 < T && (p.tiles[t_begin + i + 1] >> 24) != cls) mma_commit(smem_u32(z_free));

@@ -26,13 +26,17 @@
 // The split state operand does not fit in shared memory beside the split
 // table at n = 32 (2 x 64 KB each), so A_hi and A_lo live in tensor memory
 // and the MMA reads A from there (the TS form of tcgen05.mma), stored by the
-// converter warps with tcgen05.st.  TMEM: D, E, A_hi, A_lo, 4n columns each
-// (<= 512).  D and E are single-buffered and handed back per staging slot: the
-// epilogue arrives on d_free[j] once it has read slot j's columns of D and E,
-// and the next tile's converters write slot j's E and A chunk only after that
-// (which also means the previous tile's MMAs completed).  A K chunk is 32 tf32
-// values: 8 directions, one 128-byte swizzle row of the table, one staging
-// slot.
+// converter warps with tcgen05.st.  Because the accumulator no longer holds
+// the exact part, the MMAs need not wait for the whole tile: A is a ring of
+// K chunks (32 tf32 values = 8 directions = one staging slot = one 128-byte
+// swizzle row of the table), each converter group owning its own slots, and
+// the MMA thread takes chunk j as soon as its group has written it
+// (a_full), releasing the ring slot when those MMAs complete (a_empty).
+// TMEM at n = 32 (512 columns): two accumulators D (so the epilogue of one
+// tile overlaps the MMAs of the next), one region E handed back per staging
+// slot (the epilogue arrives on e_free[j] once it has read slot j, and the
+// next tile's converter writes slot j of E only then), and the A ring (one
+// chunk of hi + lo per group; two at smaller n).
 //
 // Warp roles as in the bf16 kernel: warps 0-7 epilogue, 8-15 converters (two
 // groups of four on alternate staging slots), 16 TMA producer, 17 MMA issuer.
@@ -89,6 +93,10 @@ __device__ __forceinline__ void tmem_st8u(uint32_t taddr, const uint32_t v[8])
                  : "memory");
 }
 
+// A ring slots per converter group (TMEM: 3 * 4n columns for D, D, E, then
+// 64 columns per ring slot: 32 hi + 32 lo)
+__host__ __device__ constexpr int tf32_ring(int N4) { return N4 >= 128 ? 1 : 2; }
+
 __global__ void __launch_bounds__(kThreads, 1)
     k_step_tc_tf32(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmZhi,
                    const __grid_constant__ CUtensorMap tmZlo, TcParams p, int N4, int stages)
@@ -99,8 +107,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int n = p.n;
     const int nsites = p.nx * p.nz;
     const uint32_t z_chunk = (uint32_t)N4 * 128u;  // bytes per K chunk of one table part
-    const int colE = N4, colAh = 2 * N4, colAl = 3 * N4;   // TMEM columns (D at 0)
-    const uint32_t tcols = (uint32_t)(4 * N4);
+    const int Rg = tf32_ring(N4);                  // A ring slots per converter group
+    const int colE = 2 * N4, colR = 3 * N4;        // TMEM columns (D[b] at b * 4n)
+    const int need = colR + 2 * Rg * 2 * kChunkK;
+    const uint32_t tcols = need <= 128 ? 128u : (need <= 256 ? 256u : 512u);
 
     uint8_t *sZ = smem;
     uint8_t *sZlo = sZ + G * z_chunk;
@@ -108,10 +118,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *bars = reinterpret_cast<uint64_t *>(sStage + (size_t)stages * kStageBytes);
     uint64_t *st_full = bars;
     uint64_t *st_empty = st_full + stages;
-    uint64_t *d_free = st_empty + stages;      // [G] the epilogue has read slot j of D and E
-    uint64_t *t_ready = d_free + G;            // [1] converters: E and A of a tile written
-    uint64_t *acc_full = t_ready + 1;          // [1] MMAs of a tile completed
-    uint64_t *z_full = acc_full + 1;           // [1]
+    uint64_t *a_full = st_empty + stages;      // [2 Rg] a group wrote a ring slot
+    uint64_t *a_empty = a_full + 2 * Rg;       // [2 Rg] the MMAs on a ring slot completed
+    uint64_t *e_free = a_empty + 2 * Rg;       // [G] the epilogue has read slot j of E
+    uint64_t *acc_full = e_free + G;           // [2]
+    uint64_t *acc_empty = acc_full + 2;        // [2]
+    uint64_t *z_full = acc_empty + 2;          // [1]
     uint64_t *drain = z_full + 1;              // [1]
     uint64_t *z_free = drain + 1;              // [1]
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(z_free + 1);
@@ -122,16 +134,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // epilogue warps reading each slot: four (one per quadrant), eight when a
     // slot spans both halves of the directions (n = 8)
-    const int dfree_count = (n / 2) % kDirsPerStage == 0 ? 4 : 8;
+    const int efree_count = (n / 2) % kDirsPerStage == 0 ? 4 : 8;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
             mbar_init(smem_u32(&st_full[s]), 1);
             mbar_init(smem_u32(&st_empty[s]), 4);
         }
-        for (int j = 0; j < G; ++j) mbar_init(smem_u32(&d_free[j]), dfree_count);
-        mbar_init(smem_u32(t_ready), kConvWarps);
-        mbar_init(smem_u32(acc_full), 1);
+        for (int k = 0; k < 2 * Rg; ++k) {
+            mbar_init(smem_u32(&a_full[k]), 4);
+            mbar_init(smem_u32(&a_empty[k]), 1);
+        }
+        for (int j = 0; j < G; ++j) mbar_init(smem_u32(&e_free[j]), efree_count);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&acc_full[b]), 1);
+            mbar_init(smem_u32(&acc_empty[b]), kEpiWarps);
+        }
         mbar_init(smem_u32(z_full), 1);
         mbar_init(smem_u32(drain), 1);
         mbar_init(smem_u32(z_free), 1);
@@ -201,34 +219,47 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_tf32(kTileM, N4);
+            // descriptors of the two table parts; a byte offset o (a multiple of
+            // 16) moves a descriptor by o >> 4 (its start-address field)
+            const uint64_t bh0 = sw128_desc(smem_u32(sZ)), bl0 = sw128_desc(smem_u32(sZlo));
             int prev_cls = -1;
-            uint32_t zl = 0;
+            uint32_t zl = 0, mc[2] = {0, 0};
             bool ok = true, issued = false;
             for (int i = 0; i < T && ok; ++i) {
                 const int cls = p.tiles[t_begin + i] >> 24;
+                const int b = i & 1;
                 if (cls != prev_cls) {
                     ok = mbar_wait(smem_u32(z_full), zl & 1, abort_flag, p.err, kErrTimeoutMma);
                     ++zl;
                     prev_cls = cls;
                     if (!ok) break;
                 }
-                ok = mbar_wait(smem_u32(t_ready), i & 1, abort_flag, p.err, kErrTimeoutMma);
+                // the epilogue of tile i - 2 has read accumulator b
+                ok = mbar_wait(smem_u32(&acc_empty[b]), ((i >> 1) & 1) ^ 1, abort_flag, p.err, kErrTimeoutMma);
                 if (!ok) break;
-                tc_fence_after();
-                for (int c = 0; c < G; ++c) {
+                const uint32_t d_tmem = tmem + (uint32_t)(b * N4);
+                for (int j = 0; j < G && ok; ++j) {
+                    const int g = j & 1;
+                    const uint32_t m = mc[g]++;
+                    const int k = g * Rg + (int)(m % (uint32_t)Rg);
+                    ok = mbar_wait(smem_u32(&a_full[k]), (m / (uint32_t)Rg) & 1, abort_flag, p.err, kErrTimeoutMma);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t ah = tmem + (uint32_t)(colR + k * 2 * kChunkK), al = ah + kChunkK;
+                    const uint64_t bh = bh0 + (uint64_t)((j * z_chunk) >> 4), bl = bl0 + (uint64_t)((j * z_chunk) >> 4);
+#pragma unroll
                     for (int kk = 0; kk < kChunkK / 8; ++kk) {       // K = 8 per instruction (32 bytes)
-                        const uint32_t zo = c * z_chunk + kk * 32;
-                        const uint32_t acol = (uint32_t)(kChunkK * c + 8 * kk);
-                        const uint64_t bh = sw128_desc(smem_u32(sZ + zo)), bl = sw128_desc(smem_u32(sZlo + zo));
                         // the tile's first instruction starts D from zero
-                        mma_tf32_ts(tmem, tmem + (uint32_t)colAh + acol, bh, idesc, (c | kk) ? 1u : 0u);
-                        mma_tf32_ts(tmem, tmem + (uint32_t)colAh + acol, bl, idesc, 1u);
-                        mma_tf32_ts(tmem, tmem + (uint32_t)colAl + acol, bh, idesc, 1u);
+                        mma_tf32_ts(d_tmem, ah + 8 * kk, bh + 2 * kk, idesc, (j | kk) ? 1u : 0u);
+                        mma_tf32_ts(d_tmem, ah + 8 * kk, bl + 2 * kk, idesc, 1u);
+                        mma_tf32_ts(d_tmem, al + 8 * kk, bh + 2 * kk, idesc, 1u);
                     }
+                    mma_commit(smem_u32(&a_empty[k]));
+                    issued = true;
                 }
-                mma_commit(smem_u32(acc_full));
+                if (!ok) break;
+                mma_commit(smem_u32(&acc_full[b]));
                 if (i + 1 < T && (p.tiles[t_begin + i + 1] >> 24) != cls) mma_commit(smem_u32(z_free));
-                issued = true;
             }
             if (issued) {
                 // drain: all MMAs this thread issued have completed before TMEM is freed
@@ -247,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int half = r / kHalfSites, hr = r % kHalfSites;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         const int ring = stages / 2;
-        uint32_t gq = 0;
+        uint32_t gq = 0, mc = 0;
         bool ok = true;
         int e_next = T > 0 ? p.tiles[t_begin] : 0, e_after = T > 1 ? p.tiles[t_begin + 1] : 0;
         float4 cf_next = T > 0 ? load_coef(p.coef, (e_next & 0xFFFFFF) * kTileM + r, nsites) : float4{};
@@ -273,17 +304,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 const uint32_t local = gq++;
                 const int s = ring_slot(grp, local, ring);
+                const uint32_t m = mc++;
+                const int ka = grp * Rg + (int)(m % (uint32_t)Rg);
                 ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&st_full[s]), (local / (uint32_t)ring) & 1, abort_flag,
                                                        p.err, kErrTimeoutConverter));
-                if (!ok) break;
-                // the previous tile's epilogue has read slot j of D and E, so its
-                // MMAs (and their reads of A chunk j) completed
-                ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&d_free[j]), (i & 1) ^ 1, abort_flag, p.err,
-                                                       kErrTimeoutConverter));
+                // slot j of E has been read by the previous tile's epilogue, and
+                // the MMAs on this group's ring slot completed
+                ok = ok && __all_sync(0xffffffffu, mbar_wait(smem_u32(&e_free[j]), (i & 1) ^ 1, abort_flag, p.err,
+                                                             kErrTimeoutConverter));
+                ok = ok && __all_sync(0xffffffffu, mbar_wait(smem_u32(&a_empty[ka]), ((m / (uint32_t)Rg) & 1) ^ 1,
+                                                             abort_flag, p.err, kErrTimeoutConverter));
                 if (!ok) break;
                 tc_fence_after();
                 const float4 *stg = reinterpret_cast<const float4 *>(sStage + (size_t)s * kStageBytes) +
                                     half * (kDirsPerStage * kHalfSites) + hr;
+                const uint32_t ah = tmem + lane_base + (uint32_t)(colR + ka * 2 * kChunkK), al = ah + kChunkK;
 #pragma unroll
                 for (int dl = 0; dl < kDirsPerStage; dl += 2) {
                     const int d = d_beg + dl;
@@ -293,33 +328,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const float sv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
                     const float g0 = fmaf(cf.z, fw[dl], cf.y), g1 = fmaf(cf.z, fw[dl + 1], cf.y);
                     float init[8];
-                    uint32_t ah[8], al[8];
+                    uint32_t hi[8], lo[8];
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         init[k] = fmaf(cf.x, sv[k], (k < 4 ? g0 : g1) * sv[k]);   // exact float32 part
                         const float x = cf.z * sv[k];                              // beta S~
-                        ah[k] = to_tf32(x);
-                        al[k] = to_tf32(x - __uint_as_float(ah[k]));
+                        hi[k] = to_tf32(x);
+                        lo[k] = to_tf32(x - __uint_as_float(hi[k]));
                     }
                     tmem_st8(tmem + lane_base + (uint32_t)(colE + 4 * d), init);
-                    tmem_st8u(tmem + lane_base + (uint32_t)(colAh + 4 * d), ah);
-                    tmem_st8u(tmem + lane_base + (uint32_t)(colAl + 4 * d), al);
+                    tmem_st8u(ah + 4 * dl, hi);
+                    tmem_st8u(al + 4 * dl, lo);
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&st_empty[s]));
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&a_full[ka]));
             }
-            if (!ok) break;
-            tmem_wait_st();
-            tc_fence_before();
-            __syncwarp();
-            // arrive for tile i only once t_ready's phase for tile i - 1 has
-            // completed: a warp with no slot in a tile (group 1 at n = 8) would
-            // otherwise run ahead and its arrivals for later tiles would
-            // complete tile i's phase before the other group wrote E and A
-            ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(t_ready), (i & 1) ^ 1, abort_flag, p.err,
-                                                   kErrTimeoutConverter));
-            if (!ok) break;
-            if (lane == 0) mbar_arrive(smem_u32(t_ready));
         }
     } else {
         // ------------------------------------------------------------ epilogue
@@ -332,18 +359,27 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
         for (int i = 0; i < T && ok; ++i) {
             const int tile = p.tiles[t_begin + i] & 0xFFFFFF;
+            const int b = i & 1;
             const int site = tile * kTileM + r;
             const int z = site / p.nx, x = site - z * p.nx;
             const bool interior = site < nsites && x > 0 && x < p.nx - 1 && z > 0 && z < p.nz - 1;
-            ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(acc_full), i & 1, abort_flag, p.err, kErrTimeoutEpilogue));
+            ok = __all_sync(0xffffffffu,
+                            mbar_wait(smem_u32(&acc_full[b]), (i >> 1) & 1, abort_flag, p.err, kErrTimeoutEpilogue));
             if (!ok) break;
             tc_fence_after();
             for (int d0 = dbeg; d0 < dbeg + dn; d0 += 4) {
                 float v[16], e[16];
-                tmem_ld16(tmem + lane_base + (uint32_t)(4 * d0), v);
+                tmem_ld16(tmem + lane_base + (uint32_t)(b * N4 + 4 * d0), v);
                 tmem_ld16(tmem + lane_base + (uint32_t)(colE + 4 * d0), e);
 #pragma unroll
                 for (int k = 0; k < 16; ++k) v[k] += e[k];
+                // hand slot j of E back once this warp has read all of its columns
+                const int next = d0 + 4;
+                if (next % kDirsPerStage == 0 || next == dbeg + dn) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&e_free[(next - 1) / kDirsPerStage]));
+                }
                 if (interior) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
@@ -357,14 +393,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         push_store(p.dir, p.inflow, p.bcbits, p.S_new, p.nx, p.nz, n, site, d0 + k,
                                    make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
                 }
-                // hand a slot back once this warp has read all of its columns
-                const int next = d0 + 4;
-                if (next % kDirsPerStage == 0 || next == dbeg + dn) {
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&d_free[(next - 1) / kDirsPerStage]));
-                }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acc_empty[b]));
         }
     }
 
@@ -379,8 +411,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 size_t tc_tf32_smem_bytes(int N4, int stages)
 {
     const int G = N4 / kChunkK;
-    const size_t b = (size_t)2 * G * N4 * 128 + (size_t)stages * kStageBytes + (size_t)(2 * stages + G + 5) * 8 + 16 +
-                     2 * kMaxDirs;
+    const size_t b = (size_t)2 * G * N4 * 128 + (size_t)stages * kStageBytes +
+                     (size_t)(2 * stages + 4 * tf32_ring(N4) + G + 7) * 8 + 16 + 2 * kMaxDirs;
     return b + 1024;  // alignment slack
 }
 
