@@ -116,6 +116,16 @@ __host__ __device__ inline FxCols fx_cols(int N4)
     return c;
 }
 
+// Order in which a tile's staging slots are loaded and converted.  The two
+// halves of the epilogue warps hand the accumulator back slot by slot from
+// the start of each half of the directions; at n = 64 (8 slots) the order
+// 0, 1, 4, 5, 2, 3, 6, 7 gives each converter group its slots in the order
+// they are handed back (group 0: 0, 4, 2, 6; group 1: 1, 5, 3, 7).
+__device__ __forceinline__ int slot_of(int k, int groups)
+{
+    return groups == 8 ? ((k & 1) | ((k >> 1) & 1) << 2 | (k >> 2) << 1) : k;
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     k_step_tc_fp8x(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmZ, TcParams p,
                    const uint8_t *__restrict__ sfb, int N4, int stages, int n_phase, uint32_t tcols)
@@ -221,7 +231,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                             tma_load_3d(smem_u32(sZ + (t * C8 + c) * z_chunk), &tmZ, zb, 128 * c, 0, t * n_phase + cls);
                     prev_cls = cls;
                 }
-                for (int j = 0; j < groups && ok; ++j) {
+                for (int kq = 0; kq < groups && ok; ++kq) {
+                    const int j = slot_of(kq, groups);
                     const int gr = j & 1;
                     const uint32_t local = gq[gr]++;
                     const int s = ring_slot(gr, local, stages / 2);
@@ -236,8 +247,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (RTLB_TC_FP8X_PREFETCH_SLOTS > 0) {
                         // two staging slots hold ~32 KB in flight: the chunk a
                         // few slots ahead goes to L2 meanwhile
-                        const int ahead = i * groups + j + RTLB_TC_FP8X_PREFETCH_SLOTS;
-                        const int ia = ahead / groups, ja = ahead - ia * groups;
+                        const int ahead = i * groups + kq + RTLB_TC_FP8X_PREFETCH_SLOTS;
+                        const int ia = ahead / groups, ja = slot_of(ahead - ia * groups, groups);
                         if (ia < T) {
                             const int ta = p.tiles[t_begin + ia] & 0xFFFFFF;
                             for (int h = 0; h < kTileM / kHalfSites; ++h)
@@ -328,7 +339,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const float *fwd = p.fwd + (size_t)(entry >> 24) * n;
             uint32_t sc0 = 0, sc1 = 0;                 // this group's packed scale bytes (four slots)
-            for (int j = grp; j < groups && ok; j += 2) {
+            for (int kq = grp; kq < groups && ok; kq += 2) {
+                const int j = slot_of(kq, groups);     // same group: slot_of keeps the parity
                 const int d_beg = 8 * j;
                 float fw[8];
 #pragma unroll
@@ -346,46 +358,38 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!ok) break;
                 const float4 *stg = reinterpret_cast<const float4 *>(sStage + (size_t)s * kStageBytes) +
                                     half * (kDirsPerStage * kHalfSites) + hr;
+                // the slot's 32 values S~ = S + e (emission on I) into registers;
+                // the staging slot goes back to the producer at once, and all
+                // the quantization happens before the wait for this slot's
+                // accumulator columns
+                float sv[32];
+#pragma unroll
+                for (int dl = 0; dl < kDirsPerStage; ++dl) {
+                    const float4 v = stg[dl * kHalfSites];
+                    sv[4 * dl] = v.x + cf.w;
+                    sv[4 * dl + 1] = v.y;
+                    sv[4 * dl + 2] = v.z;
+                    sv[4 * dl + 3] = v.w;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&st_empty[s]));
                 // hi scale: largest |beta S~| of the slot's 32 values
                 float amax = 0.f;
 #pragma unroll
-                for (int dl = 0; dl < kDirsPerStage; ++dl) {
-                    float4 v = stg[dl * kHalfSites];
-                    v.x += cf.w;
-                    amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
-                }
+                for (int k = 0; k < 32; ++k) amax = fmaxf(amax, fabsf(sv[k]));
                 const int e0 = block_exponent(fabsf(cf.z) * amax);
                 const float inv0 = __uint_as_float((uint32_t)(127 - e0) << 23);   // 2^-e0, exact
-                // the previous tile's epilogue has read this slot's columns, so
-                // its MMAs (and their reads of A and its scales) completed
-                ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&d_free[j]), (i & 1) ^ 1, abort_flag, p.err,
-                                                       kErrTimeoutConverter));
-                if (!ok) break;
-                tc_fence_after();
                 uint32_t w0[8];
                 float rmax = 0.f;
 #pragma unroll
-                for (int dl = 0; dl < kDirsPerStage; dl += 2) {
-                    const int d = d_beg + dl;
-                    float4 v0 = stg[dl * kHalfSites], v1 = stg[(dl + 1) * kHalfSites];
-                    v0.x += cf.w;                               // emission (I only)
-                    v1.x += cf.w;
-                    const float sv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-                    const float g0 = fmaf(cf.z, fw[dl], cf.y), g1 = fmaf(cf.z, fw[dl + 1], cf.y);
-                    float init[8], x[8];
+                for (int dl = 0; dl < kDirsPerStage; ++dl) {
+                    float x[4], h[4];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        init[k] = fmaf(cf.x, sv[k], (k < 4 ? g0 : g1) * sv[k]);   // exact float32 part
-                        x[k] = (cf.z * sv[k]) * inv0;                             // beta S~ / 2^e0
-                    }
-                    tmem_st8(tmem + lane_base + (uint32_t)(4 * d), init);
+                    for (int k = 0; k < 4; ++k) x[k] = (cf.z * sv[4 * dl + k]) * inv0;   // beta S~ / 2^e0
                     w0[dl] = e4m3x2(x[0], x[1]) | (e4m3x2(x[2], x[3]) << 16);
-                    w0[dl + 1] = e4m3x2(x[4], x[5]) | (e4m3x2(x[6], x[7]) << 16);
-                    float h[8];
                     e4m3x4_to_float(w0[dl], h);
-                    e4m3x4_to_float(w0[dl + 1], h + 4);
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) rmax = fmaxf(rmax, fabsf(x[k] - h[k]));   // exact remainders
+                    for (int k = 0; k < 4; ++k) rmax = fmaxf(rmax, fabsf(x[k] - h[k]));   // exact remainders
                 }
                 // lo scale from the remainders' own maximum; a lo term below the
                 // smallest scale (e0 + d < -127) is left out
@@ -395,16 +399,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint32_t w1[8];
 #pragma unroll
                 for (int dl = 0; dl < kDirsPerStage; ++dl) {
-                    const float4 v = stg[dl * kHalfSites];
-                    const float sv[4] = {v.x + cf.w, v.y, v.z, v.w};
                     float h[4], y[4];
                     e4m3x4_to_float(w0[dl], h);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) y[k] = lo_on ? ((cf.z * sv[k]) * inv0 - h[k]) * invd : 0.f;
+                    for (int k = 0; k < 4; ++k) y[k] = lo_on ? ((cf.z * sv[4 * dl + k]) * inv0 - h[k]) * invd : 0.f;
                     w1[dl] = e4m3x2(y[0], y[1]) | (e4m3x2(y[2], y[3]) << 16);
                 }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&st_empty[s]));
+                // the previous tile's epilogue has read this slot's columns, so
+                // its MMAs (and their reads of A and its scales) completed
+                ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&d_free[j]), (i & 1) ^ 1, abort_flag, p.err,
+                                                       kErrTimeoutConverter));
+                if (!ok) break;
+                tc_fence_after();
+#pragma unroll
+                for (int dl = 0; dl < kDirsPerStage; dl += 2) {
+                    const float g0 = fmaf(cf.z, fw[dl], cf.y), g1 = fmaf(cf.z, fw[dl + 1], cf.y);
+                    float init[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        init[k] = fmaf(cf.x, sv[4 * dl + k], (k < 4 ? g0 : g1) * sv[4 * dl + k]);   // exact float32 part
+                    tmem_st8(tmem + lane_base + (uint32_t)(4 * (d_beg + dl)), init);
+                }
                 tmem_st8w(tmem + lane_base + (uint32_t)(colA0 + 8 * j), w0);
                 tmem_st8w(tmem + lane_base + (uint32_t)(colA1 + 8 * j), w1);
                 const int e1 = lo_on ? e0 + dlo : -127;
@@ -444,27 +459,36 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(acc_full), i & 1, abort_flag, p.err, kErrTimeoutEpilogue));
             if (!ok) break;
             tc_fence_after();
-            for (int d0 = dbeg; d0 < dbeg + dn; d0 += 4) {
-                float v[16];
-                tmem_ld16(tmem + lane_base + (uint32_t)(4 * d0), v);
+            // two slots (16 directions, 64 columns) per load where the half
+            // holds them, fewer at small n; the slots go back to the converters
+            // as soon as their columns are in registers, before the stores
+            // (which proceed at the SM's share of the write bandwidth)
+            const int step = dn >= 16 ? 16 : (dn >= kDirsPerStage ? kDirsPerStage : 4);
+            for (int d0 = dbeg; d0 < dbeg + dn; d0 += step) {
+                float v[64];
+                if (step == 16) tmem_ld64(tmem + lane_base + (uint32_t)(4 * d0), v);
+                else if (step == kDirsPerStage) tmem_ld32(tmem + lane_base + (uint32_t)(4 * d0), v);
+                else tmem_ld16(tmem + lane_base + (uint32_t)(4 * d0), v);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    for (int sl = d0 / kDirsPerStage; sl * kDirsPerStage < d0 + step; ++sl)
+                        mbar_arrive(smem_u32(&d_free[sl]));
                 if (interior) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int d = d0 + k;
-                        const long long t = (long long)d * nsites + site + s_cx[d] + (long long)s_cz[d] * p.nx;
-                        __stcs(&out[t], make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
+                    for (int k = 0; k < 16; ++k) {
+                        if (k < step) {
+                            const int d = d0 + k;
+                            const long long t = (long long)d * nsites + site + s_cx[d] + (long long)s_cz[d] * p.nx;
+                            __stcs(&out[t], make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
+                        }
                     }
                 } else if (site < nsites) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        push_store(p.dir, p.inflow, p.bcbits, p.S_new, p.nx, p.nz, n, site, d0 + k,
-                                   make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
-                }
-                const int next = d0 + 4;
-                if (next % kDirsPerStage == 0 || next == dbeg + dn) {
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&d_free[(next - 1) / kDirsPerStage]));
+                    for (int k = 0; k < 16; ++k)
+                        if (k < step)
+                            push_store(p.dir, p.inflow, p.bcbits, p.S_new, p.nx, p.nz, n, site, d0 + k,
+                                       make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
                 }
             }
         }

@@ -23,20 +23,19 @@
 // step.  Started from zero, D holds only the scattered part and its
 // truncation is relative to that part; E + D is one round-to-nearest add.
 //
-// The split state operand does not fit in shared memory beside the split
-// table at n = 32 (2 x 64 KB each), so A_hi and A_lo live in tensor memory
-// and the MMA reads A from there (the TS form of tcgen05.mma), stored by the
-// converter warps with tcgen05.st.  Because the accumulator no longer holds
-// the exact part, the MMAs need not wait for the whole tile: A is a ring of
-// K chunks (32 tf32 values = 8 directions = one staging slot = one 128-byte
-// swizzle row of the table), each converter group owning its own slots, and
-// the MMA thread takes chunk j as soon as its group has written it
-// (a_full), releasing the ring slot when those MMAs complete (a_empty).
-// TMEM at n = 32 (512 columns): two accumulators D (so the epilogue of one
-// tile overlaps the MMAs of the next), one region E handed back per staging
-// slot (the epilogue arrives on e_free[j] once it has read slot j, and the
-// next tile's converter writes slot j of E only then), and the A ring (one
-// chunk of hi + lo per group; two at smaller n).
+// Memory plan at n = 32.  TMEM (512 columns): two accumulators D and two
+// regions E, so every role can run a tile ahead of the next (the converters
+// of tile i + 2 and its MMAs wait only for the epilogue of tile i).  Shared
+// memory: the split table (2 x 64 KB), a ring of split state chunks (a K
+// chunk is 32 tf32 values = 8 directions = one staging slot = one 128-byte
+// swizzle row; hi and lo, 16 KB each; one ring slot per converter group at
+// n = 32, two below) and two staging slots, with the state chunk a few slots
+// ahead prefetched into L2.  Because D starts from zero, the MMAs need not
+// wait for the whole tile: the MMA thread takes chunk j as soon as its group
+// has written it (a_full) and releases the ring slot when those MMAs complete
+// (a_empty).  (A layout with the state operand in tensor memory and one E
+// region handed back per slot coupled each tile's conversion to the previous
+// tile's epilogue and measured 0.59 of HBM at 1024x1024.)
 //
 // Warp roles as in the bf16 kernel: warps 0-7 epilogue, 8-15 converters (two
 // groups of four on alternate staging slots), 16 TMA producer, 17 MMA issuer.
@@ -66,15 +65,15 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n)
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-// D[tmem] (+)= A[tmem] . B[smem]^T, tf32 operands, f32 accumulate, M = 128.
-__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
-                                            uint32_t accumulate)
+// D[tmem] (+)= A[smem] . B[smem]^T, tf32 operands, f32 accumulate, M = 128.
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -86,16 +85,13 @@ __device__ __forceinline__ uint32_t to_tf32(float x)
     return r;
 }
 
-__device__ __forceinline__ void tmem_st8u(uint32_t taddr, const uint32_t v[8])
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
-                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
-                 : "memory");
-}
-
-// A ring slots per converter group (TMEM: 3 * 4n columns for D, D, E, then
-// 64 columns per ring slot: 32 hi + 32 lo)
+// A ring slots per converter group (shared memory, 32 KB each: hi and lo)
 __host__ __device__ constexpr int tf32_ring(int N4) { return N4 >= 128 ? 1 : 2; }
+constexpr uint32_t kRingBytes = (uint32_t)kTileM * 128u;   // one term of one chunk
+
+#ifndef RTLB_TC_TF32_PREFETCH_SLOTS
+#define RTLB_TC_TF32_PREFETCH_SLOTS 4
+#endif
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_step_tc_tf32(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmZhi,
@@ -108,21 +104,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int nsites = p.nx * p.nz;
     const uint32_t z_chunk = (uint32_t)N4 * 128u;  // bytes per K chunk of one table part
     const int Rg = tf32_ring(N4);                  // A ring slots per converter group
-    const int colE = 2 * N4, colR = 3 * N4;        // TMEM columns (D[b] at b * 4n)
-    const int need = colR + 2 * Rg * 2 * kChunkK;
-    const uint32_t tcols = need <= 128 ? 128u : (need <= 256 ? 256u : 512u);
+    const int colE = 2 * N4;                       // TMEM: D[b] at b * 4n, E[b] at 2 * 4n + b * 4n
+    const uint32_t tcols = N4 * 4 <= 128 ? 128u : (N4 * 4 <= 256 ? 256u : 512u);
 
     uint8_t *sZ = smem;
     uint8_t *sZlo = sZ + G * z_chunk;
-    uint8_t *sStage = sZlo + G * z_chunk;
+    uint8_t *sRing = sZlo + G * z_chunk;           // [2 Rg][hi, lo][128 rows x 128 B]
+    uint8_t *sStage = sRing + (size_t)2 * Rg * 2 * kRingBytes;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sStage + (size_t)stages * kStageBytes);
     uint64_t *st_full = bars;
     uint64_t *st_empty = st_full + stages;
     uint64_t *a_full = st_empty + stages;      // [2 Rg] a group wrote a ring slot
     uint64_t *a_empty = a_full + 2 * Rg;       // [2 Rg] the MMAs on a ring slot completed
-    uint64_t *e_free = a_empty + 2 * Rg;       // [G] the epilogue has read slot j of E
-    uint64_t *acc_full = e_free + G;           // [2]
-    uint64_t *acc_empty = acc_full + 2;        // [2]
+    uint64_t *acc_full = a_empty + 2 * Rg;     // [2]
+    uint64_t *acc_empty = acc_full + 2;        // [2] the epilogue has read D[b] and E[b]
     uint64_t *z_full = acc_empty + 2;          // [1]
     uint64_t *drain = z_full + 1;              // [1]
     uint64_t *z_free = drain + 1;              // [1]
@@ -132,9 +127,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     int8_t *s_cz = s_cx + kMaxDirs;                              // [n]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // epilogue warps reading each slot: four (one per quadrant), eight when a
-    // slot spans both halves of the directions (n = 8)
-    const int efree_count = (n / 2) % kDirsPerStage == 0 ? 4 : 8;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
@@ -145,7 +137,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(smem_u32(&a_full[k]), 4);
             mbar_init(smem_u32(&a_empty[k]), 1);
         }
-        for (int j = 0; j < G; ++j) mbar_init(smem_u32(&e_free[j]), efree_count);
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&acc_full[b]), 1);
             mbar_init(smem_u32(&acc_empty[b]), kEpiWarps);
@@ -202,6 +193,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int h = 0; h < kTileM / kHalfSites; ++h)
                         tma_load_2d(smem_u32(sStage + (size_t)s * kStageBytes + h * (kStageBytes / 2)), &tmS, fb,
                                     4 * (tile * kTileM + h * kHalfSites), j * kDirsPerStage);
+                    if (RTLB_TC_TF32_PREFETCH_SLOTS > 0) {
+                        // few staging slots fit beside the table and the ring: the
+                        // chunk a few slots ahead goes to L2 meanwhile
+                        const int ahead = i * G + j + RTLB_TC_TF32_PREFETCH_SLOTS;
+                        const int ia = ahead / G, ja = ahead - ia * G;
+                        if (ia < T) {
+                            const int ta = p.tiles[t_begin + ia] & 0xFFFFFF;
+                            for (int h = 0; h < kTileM / kHalfSites; ++h)
+                                tma_prefetch_2d(&tmS, 4 * (ta * kTileM + h * kHalfSites), ja * kDirsPerStage);
+                        }
+                    }
                 }
             }
             // drain: wait (bounded) for the loads this thread issued into each stage
@@ -219,9 +221,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_tf32(kTileM, N4);
-            // descriptors of the two table parts; a byte offset o (a multiple of
-            // 16) moves a descriptor by o >> 4 (its start-address field)
+            // descriptors of the table parts and ring slots; a byte offset o (a
+            // multiple of 16) moves a descriptor by o >> 4 (its address field)
             const uint64_t bh0 = sw128_desc(smem_u32(sZ)), bl0 = sw128_desc(smem_u32(sZlo));
+            const uint64_t ar0 = sw128_desc(smem_u32(sRing));
             int prev_cls = -1;
             uint32_t zl = 0, mc[2] = {0, 0};
             bool ok = true, issued = false;
@@ -245,14 +248,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ok = mbar_wait(smem_u32(&a_full[k]), (m / (uint32_t)Rg) & 1, abort_flag, p.err, kErrTimeoutMma);
                     if (!ok) break;
                     tc_fence_after();
-                    const uint32_t ah = tmem + (uint32_t)(colR + k * 2 * kChunkK), al = ah + kChunkK;
+                    const uint64_t ah = ar0 + (uint64_t)((2u * k * kRingBytes) >> 4), al = ah + (kRingBytes >> 4);
                     const uint64_t bh = bh0 + (uint64_t)((j * z_chunk) >> 4), bl = bl0 + (uint64_t)((j * z_chunk) >> 4);
 #pragma unroll
                     for (int kk = 0; kk < kChunkK / 8; ++kk) {       // K = 8 per instruction (32 bytes)
                         // the tile's first instruction starts D from zero
-                        mma_tf32_ts(d_tmem, ah + 8 * kk, bh + 2 * kk, idesc, (j | kk) ? 1u : 0u);
-                        mma_tf32_ts(d_tmem, ah + 8 * kk, bl + 2 * kk, idesc, 1u);
-                        mma_tf32_ts(d_tmem, al + 8 * kk, bh + 2 * kk, idesc, 1u);
+                        mma_tf32(d_tmem, ah + 2 * kk, bh + 2 * kk, idesc, (j | kk) ? 1u : 0u);
+                        mma_tf32(d_tmem, ah + 2 * kk, bl + 2 * kk, idesc, 1u);
+                        mma_tf32(d_tmem, al + 2 * kk, bh + 2 * kk, idesc, 1u);
                     }
                     mma_commit(smem_u32(&a_empty[k]));
                     issued = true;
@@ -285,11 +288,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int i = 0; i < T && ok; ++i) {
             const int entry = e_next;
             const float4 cf = cf_next;
+            const int b = i & 1;
             if (i + 1 < T) {
                 e_next = e_after;
                 cf_next = load_coef(p.coef, (e_next & 0xFFFFFF) * kTileM + r, nsites);
                 if (i + 2 < T) e_after = p.tiles[t_begin + i + 2];
             }
+            // the epilogue of tile i - 2 has read E[b]
+            ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_empty[b]), ((i >> 1) & 1) ^ 1, abort_flag, p.err,
+                                                   kErrTimeoutConverter));
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t eb = tmem + lane_base + (uint32_t)(colE + b * N4);
             const float *fwd = p.fwd + (size_t)(entry >> 24) * n;
             for (int j = grp; j < G && ok; j += 2) {
                 const int d_beg = kDirsPerStage * j;
@@ -308,17 +318,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int ka = grp * Rg + (int)(m % (uint32_t)Rg);
                 ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&st_full[s]), (local / (uint32_t)ring) & 1, abort_flag,
                                                        p.err, kErrTimeoutConverter));
-                // slot j of E has been read by the previous tile's epilogue, and
                 // the MMAs on this group's ring slot completed
-                ok = ok && __all_sync(0xffffffffu, mbar_wait(smem_u32(&e_free[j]), (i & 1) ^ 1, abort_flag, p.err,
-                                                             kErrTimeoutConverter));
                 ok = ok && __all_sync(0xffffffffu, mbar_wait(smem_u32(&a_empty[ka]), ((m / (uint32_t)Rg) & 1) ^ 1,
                                                              abort_flag, p.err, kErrTimeoutConverter));
                 if (!ok) break;
-                tc_fence_after();
                 const float4 *stg = reinterpret_cast<const float4 *>(sStage + (size_t)s * kStageBytes) +
                                     half * (kDirsPerStage * kHalfSites) + hr;
-                const uint32_t ah = tmem + lane_base + (uint32_t)(colR + ka * 2 * kChunkK), al = ah + kChunkK;
+                // this row of the ring slot: 128 bytes (32 tf32) per term, 16-byte
+                // units at position u ^ (r & 7) (128-byte swizzle)
+                uint8_t *rh = sRing + (size_t)2 * ka * kRingBytes + (uint32_t)r * 128u;
+                uint8_t *rl = rh + kRingBytes;
 #pragma unroll
                 for (int dl = 0; dl < kDirsPerStage; dl += 2) {
                     const int d = d_beg + dl;
@@ -336,13 +345,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                         hi[k] = to_tf32(x);
                         lo[k] = to_tf32(x - __uint_as_float(hi[k]));
                     }
-                    tmem_st8(tmem + lane_base + (uint32_t)(colE + 4 * d), init);
-                    tmem_st8u(ah + 4 * dl, hi);
-                    tmem_st8u(al + 4 * dl, lo);
+                    tmem_st8(eb + 4 * d, init);
+                    const uint32_t u0 = (uint32_t)dl, u1 = (uint32_t)dl + 1u;   // the two 16-byte units of this pair
+                    const uint32_t o0 = ((u0 ^ (uint32_t)(r & 7)) << 4), o1 = ((u1 ^ (uint32_t)(r & 7)) << 4);
+                    *reinterpret_cast<uint4 *>(rh + o0) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                    *reinterpret_cast<uint4 *>(rh + o1) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+                    *reinterpret_cast<uint4 *>(rl + o0) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                    *reinterpret_cast<uint4 *>(rl + o1) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&st_empty[s]));
                 tmem_wait_st();
+                fence_proxy_async();                        // the ring is read by the tensor core
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&a_full[ka]));
@@ -370,16 +384,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int d0 = dbeg; d0 < dbeg + dn; d0 += 4) {
                 float v[16], e[16];
                 tmem_ld16(tmem + lane_base + (uint32_t)(b * N4 + 4 * d0), v);
-                tmem_ld16(tmem + lane_base + (uint32_t)(colE + 4 * d0), e);
+                tmem_ld16(tmem + lane_base + (uint32_t)(colE + b * N4 + 4 * d0), e);
 #pragma unroll
                 for (int k = 0; k < 16; ++k) v[k] += e[k];
-                // hand slot j of E back once this warp has read all of its columns
-                const int next = d0 + 4;
-                if (next % kDirsPerStage == 0 || next == dbeg + dn) {
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&e_free[(next - 1) / kDirsPerStage]));
-                }
                 if (interior) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
@@ -411,8 +418,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 size_t tc_tf32_smem_bytes(int N4, int stages)
 {
     const int G = N4 / kChunkK;
-    const size_t b = (size_t)2 * G * N4 * 128 + (size_t)stages * kStageBytes +
-                     (size_t)(2 * stages + 4 * tf32_ring(N4) + G + 7) * 8 + 16 + 2 * kMaxDirs;
+    const size_t b = (size_t)2 * G * N4 * 128 + (size_t)2 * tf32_ring(N4) * 2 * kRingBytes + (size_t)stages * kStageBytes +
+                     (size_t)(2 * stages + 4 * tf32_ring(N4) + 7) * 8 + 16 + 2 * kMaxDirs;
     return b + 1024;  // alignment slack
 }
 
