@@ -380,9 +380,22 @@ def adjoint_ratio(steps: int, headline: str):
         torch.cuda.synchronize()
         fwd[prec] = a.elapsed_time(b)
         s.close()
+    # the float32-accuracy forms: the CUDA-core step, and the 3xTF32
+    # tensor-core step (its context also runs the adjoint's forward and
+    # replays on the tensor cores)
+    s = solver_for(w, "tf32x3")
+    s.step(5)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    s.step(steps)
+    b.record()
+    torch.cuda.synchronize()
+    fwd["tf32x3"] = a.elapsed_time(b)
+    s.close()
     seed = torch.randn((w.nx, w.n, 4), device="cuda")
-    for K in (50, 1):
-        s = solver_for(w, "fp32")
+    for K, prec in ((50, "fp32"), (1, "fp32"), (50, "tf32x3")):
+        s = solver_for(w, prec)
         # warm-up: the same call, which also sizes the workspace the context
         # keeps between adjoint calls (the timed call allocates nothing)
         s.adjoint(steps, seed, checkpoint_every=K)
@@ -394,13 +407,15 @@ def adjoint_ratio(steps: int, headline: str):
         s.close()
         del s
         torch.cuda.empty_cache()
-        out[f"checkpoint_every_{K}"] = {"adjoint_ms": adj_ms,
-                                        "adjoint_over_forward": {p: adj_ms / v for p, v in fwd.items()}}
+        key = f"checkpoint_every_{K}" + ("" if prec == "fp32" else f"_{prec}")
+        out[key] = {"adjoint_ms": adj_ms, "forward_precision": prec,
+                    "adjoint_over_forward": {p: adj_ms / v for p, v in fwd.items()}}
     out.update({"forward_ms": fwd, "adjoint_over_forward": out["checkpoint_every_50"]["adjoint_over_forward"],
-                "note": "each adjoint call includes its own float32 forward pass; checkpoint_every = 50 (the "
-                        "differentiation workload's setting) replays each segment once, checkpoint_every = 1 "
-                        "keeps every state (134 GB) and replays none; the workspace is the one the warm-up "
-                        "call left in the context"})
+                "note": "each adjoint call includes its own float32-accuracy forward pass (the CUDA-core step "
+                        "in an fp32 context, the 3xTF32 tensor-core step in a tf32x3 context); "
+                        "checkpoint_every = 50 (the differentiation workload's setting) replays each segment "
+                        "once, checkpoint_every = 1 keeps every state (134 GB) and replays none; the workspace "
+                        "is the one the warm-up call left in the context"})
     return out
 
 
@@ -586,6 +601,9 @@ def run_ours(args):
             adj = _leg(adjoint_ratio, args.adjoint_steps, args.precision)
             line["adjoint"] = adj
             line["adjoint_over_forward"] = adj["adjoint_over_forward"]["fp32"] if "error" not in adj else None
+            if "error" not in adj:
+                # the same ratio with the 3xTF32 tensor-core step doing the forward work on both sides
+                line["adjoint_over_forward_tf32x3"] = adj["checkpoint_every_50_tf32x3"]["adjoint_over_forward"]["tf32x3"]
         if ws == 1 and args.fp32_class_steps > 0:
             line["fp32_class"] = _leg(fp32_class, args.fp32_class_steps, peaks, src)
         if ws == 1 and args.accuracy_steps > 0:

@@ -217,8 +217,10 @@ rtlb_status rtlb_dop_out(rtlb_ctx *ctx, int32_t side, float *out, void *stream);
  * scattering and reversed streaming) of a loss L whose gradient with respect to
  * the top radiance radiance_out(TOP) after nsteps steps is dL_dout[nx][n][4]
  * (host or device).  Starting from the current state S^0 the call runs nsteps
- * float32 steps (whatever the context's precision; the state afterwards is
- * S^N, as after rtlb_step), keeping a checkpoint every checkpoint_every steps,
+ * float32-accurate steps (the 3xTF32 tensor-core step when the context's
+ * precision is TF32X3, the FP32 CUDA-core step for every other precision; the
+ * state afterwards is S^N, as after rtlb_step), keeping a checkpoint every
+ * checkpoint_every steps,
  * then walks back segment by segment, recomputing each segment's states from
  * its checkpoint.  Outputs (each may be NULL): grad_tau, grad_albedo [nz][nx]
  * float32 (host or device) -- dL/dtau and dL/dalbedo per cell; grad_Z host

@@ -201,15 +201,24 @@ StepParams make_params(rtlb_ctx *c)
 
 // One float32 CUDA-core step from S_in to S_out with the context's streaming
 // scheme (the adjoint's forward and replay).
+// One float32-accurate step from S_in into S_out for the adjoint's forward
+// pass and replays: the 3xTF32 tensor-core step when that is the context's
+// precision (same accuracy, a third of the time), the CUDA-core float32 step
+// otherwise.
 cudaError_t fp32_step_into(rtlb_ctx *c, const float *S_in, float *S_out, cudaStream_t s)
 {
     StepParams p = make_params(c);
     p.S = S_in;
     p.S_new = S_out;
-    if (!bilinear(c)) return launch_step_fp32(p, s);
+    const bool tf32 = c->opt.precision == RTLB_PREC_TF32X3;
+    auto collide = [&](const StepParams &q) -> cudaError_t {
+        if (!tf32) return launch_step_fp32(q, s);
+        return tc_step(c, q, s) == RTLB_OK ? cudaSuccess : cudaErrorLaunchFailure;
+    };
+    if (!bilinear(c)) return collide(p);
     p.dir = c->d_dir0;
     p.S_new = c->d_post;
-    cudaError_t e = launch_step_fp32(p, s);
+    cudaError_t e = collide(p);
     if (e != cudaSuccess) return e;
     return launch_stream_bilinear(c->d_post, S_out, c->d_tap_o, c->d_tap_w, c->d_inflow, c->nx, c->nz, c->n,
                                   pack_bc(c->bc), s);
@@ -866,6 +875,7 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
 #undef AK
     if (adjoint_table_tc_take_error() > 0) return fail(c, RTLB_E_TIMEOUT, "the table-gradient kernel gave up waiting");
     if (adjoint_step_tc_take_error() > 0) return fail(c, RTLB_E_TIMEOUT, "the tensor-core reverse step gave up waiting");
+    if (c->opt.precision == RTLB_PREC_TF32X3) return tc_check_error(c, s);   // the forward's tensor-core steps
     return RTLB_OK;
 }
 

@@ -25,9 +25,9 @@ def _rel(a, b):
     return float(np.abs(np.asarray(a, np.float64) - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-def _gpu_adjoint(torch, w, S0, nsteps, seed, K):
+def _gpu_adjoint(torch, w, S0, nsteps, seed, K, prec="fp32"):
     from paper_2609_23057_b300.solver import solver_for
-    s = solver_for(w, "fp32")
+    s = solver_for(w, prec)
     s.set_state(torch.from_numpy(np.asarray(S0, np.float32)).cuda())
     gt, ga, gZ, gS = s.adjoint(nsteps, torch.from_numpy(np.asarray(seed, np.float32)).cuda(), checkpoint_every=K,
                                want_S0=True)
@@ -59,6 +59,32 @@ def test_adjoint_matches_oracle(torch_cuda, orc, nx, nz, nzen, naz, bc, surv, ab
     assert _rel(gZ, rZ) < TOL
     assert _rel(gS, rS) < TOL
     # the state afterwards is the forward result
+    assert _rel(SN, P.run(S0, w.steps)) < 1e-5
+
+
+@pytest.mark.parametrize("K", [1, 5])
+@pytest.mark.parametrize("nx,nz,nzen,naz,bc,nph", [
+    (130, 5, 2, 4, (2, 0, 1, 1), 2),
+    (256, 6, 4, 4, (2, 0, 0, 0), 2),
+    (384, 4, 4, 8, (1, 1, 2, 0), 2),       # n = 32: tensor-core reverse step too
+])
+def test_adjoint_with_tf32x3_forward(torch_cuda, orc, nx, nz, nzen, naz, bc, nph, K):
+    """A TF32X3 context runs the adjoint's forward pass and replays on the
+    3xTF32 tensor-core step (float32 accuracy): gradients against the oracle
+    adjoint at the same 1e-4, rows alternating class so most tiles are
+    single-class (the rest run on the CUDA cores)."""
+    w = W.random_medium(nx, nz, nzen, naz, seed=nx + 7 * nz, bc=bc, n_phase=nph, steps=9, surv_mode=1)
+    w.tau = np.minimum(w.tau, 0.9)
+    w.phase_index = (np.arange(nz)[:, None] % nph * np.ones((1, nx))).astype(np.uint8)
+    P = oracle_problem(orc, w)
+    S0 = W.random_state(nz, nx, w.n, seed=4)
+    seed = np.random.default_rng(5).standard_normal((nx, w.n, 4)).astype(np.float32).astype(np.float64)
+    rt, ra, rZ, rS = P.adjoint(S0, w.steps, seed, want_S0=True)
+    gt, ga, gZ, gS, SN = _gpu_adjoint(torch_cuda, w, S0, w.steps, seed, K=K, prec="tf32x3")
+    assert _rel(gt, rt) < TOL
+    assert _rel(ga, ra) < TOL
+    assert _rel(gZ, rZ) < TOL
+    assert _rel(gS, rS) < TOL
     assert _rel(SN, P.run(S0, w.steps)) < 1e-5
 
 
