@@ -249,19 +249,20 @@ def _time_steps(torch, s, stream, steps):
     return [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)], ev[0].elapsed_time(ev[-1])
 
 
-def _measured_traffic(kernel, sites):
+def _measured_traffic(kernel, sites, n_dirs=64):
     """DRAM bytes per launch from the committed ncu capture of `kernel`,
     scaled to `sites`, or None when the kernel source changed since."""
     import hashlib
     try:
         with open(os.path.join(HERE, "profiles", "traffic.json")) as f:
-            rec = json.load(f)[kernel]
+            recs = json.load(f)
+        rec = recs.get(f"{kernel}@n{n_dirs}") or recs[kernel]
     except (OSError, KeyError, ValueError):
         return None
     src_of = {"k_step_tc_fp8": "tc_fp8.cu", "k_step_tc_fp8x": "tc_fp8x.cu", "k_step_tc_tf32": "tc_tf32.cu"}
     files = (src_of.get(kernel, "tc.cu"), "step_common.cuh", "tc_common.cuh", "tc_ptx.cuh")
     src = b"".join(open(os.path.join(HERE, "paper_2609_23057_b300", "csrc", fn), "rb").read() for fn in files)
-    if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"]:
+    if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"] or rec.get("n_dirs", 64) != n_dirs:
         return None
     return (rec["dram_bytes_read"] + rec["dram_bytes_write"]) * sites / rec["captured_sites"]
 
@@ -342,6 +343,7 @@ def fp32_class(steps: int, peaks, src):
         if prec != "fp32":
             entry["roofline"] = _roofline(prec, w.n, sdu, statistics.mean(per) * 1e-3, peaks, src)
             entry["roofline"]["kernel"] = KERNEL[prec]
+            entry["roofline"]["traffic"] = _measured_traffic(KERNEL[prec], w.sites, w.n)
         out[prec] = entry
     c = w.crop(192, 320, 192, 320, name="lattice512_n32_crop128")
     P = oracle_problem(oracle, c)
@@ -561,7 +563,7 @@ def run_ours(args):
     if args.precision != "fp32":
         kern = KERNEL[args.precision] if (n == 64 or args.precision != "bf16x2") else "k_step_tc"
         roof["kernel"] = kern
-        roof["traffic"] = _measured_traffic(kern, sites)
+        roof["traffic"] = _measured_traffic(kern, sites, n)
         roof["traffic_note"] = "DRAM bytes per launch from profiles/traffic.json, scaled by sites"
     if rank == 0:
         line = {
