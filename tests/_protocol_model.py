@@ -67,8 +67,13 @@ class Wait:
 
 
 class Machine:
-    def __init__(self, seed):
+    """`slow` maps a role-name prefix to a scheduling weight (default 1):
+    roles given a small weight run rarely, which lets a test reach orders
+    where one role lags far behind the others."""
+
+    def __init__(self, seed, slow=None):
         self.rng = random.Random(seed)
+        self.slow = dict(slow or {})
         self.roles = {}                 # name -> [generator, pending Wait or None]
         self.tma = []                   # outstanding TMA loads: callables run on completion
         self.mma = []                   # FIFO of ("mma", fn) / ("commit", barrier)
@@ -112,7 +117,12 @@ class Machine:
             if not choices:
                 waits = {n: f"{w.bar.name}[phase {w.k}, {w.bar.completed} done]" for n, (g, w) in self.roles.items()}
                 raise ProtocolError(f"deadlock: {waits}")
-            kind, name = self.rng.choice(choices)
+            if self.slow:
+                weights = [next((w for pre, w in self.slow.items() if k == "role" and n.startswith(pre)), 1.0)
+                           for k, n in choices]
+                kind, name = self.rng.choices(choices, weights)[0]
+            else:
+                kind, name = self.rng.choice(choices)
             if kind == "role":
                 w = self.roles[name][1]
                 if w is not None:
@@ -415,7 +425,7 @@ def fp8_step(items, stages, seed, gate_t_ready=True):
     return M.steps
 
 
-def pair_step(keys, stages, seed, n=64):
+def pair_step(keys, stages, seed, n=64, gate_acc_empty=True, slow=None):
     """The CTA-pair kernel (cta_group::2, bf16 state operand and split table):
     each entry of `keys` is one pair of tiles (one per CTA) of the same table
     key.  Per CTA: a producer (its half of the table and its own tile's
@@ -425,8 +435,10 @@ def pair_step(keys, stages, seed, n=64):
     barriers of both CTAs.  The odd CTA's converters arrive on a local
     barrier that one thread forwards to the even CTA's t_ready (count 9); the
     odd producer forwards the completion of its table half to the even z_full
-    (count 2)."""
-    M = Machine(seed)
+    (count 2).  gate_acc_empty=False lets the converters write a tile's
+    accumulator init without waiting for the epilogue of two tiles before (a
+    planted flaw)."""
+    M = Machine(seed, slow)
     T = len(keys)
     G, C, ring = _groups(n), _chunks(n), stages // 2
     R = (0, 1)
@@ -483,7 +495,8 @@ def pair_step(keys, stages, seed, n=64):
         gq = 0
         for i, key in enumerate(keys):
             b = i & 1
-            yield Wait(acc_empty[(r, b)], (i >> 1) - 1, who)
+            if gate_acc_empty:
+                yield Wait(acc_empty[(r, b)], (i >> 1) - 1, who)
             for c in range(C):
                 j = 2 * c + grp
                 local = gq

@@ -67,3 +67,16 @@ def test_cta_pair_step_is_race_free(stages):
     multicast commits to both CTAs' barriers."""
     for seed in range(10):
         P.pair_step([0, 0, 0, 1, 1, 0, 0], stages, seed)
+    # orders where one role lags far behind the rest
+    for slow in ("epi0", "epi1", "conv1", "forwarder", "producer1", "mma"):
+        for seed in range(5):
+            P.pair_step([0, 0, 1, 1, 0, 0], stages, seed, slow={slow: 0.01})
+
+
+def test_cta_pair_model_sees_unreleased_accumulator():
+    """Converters that write a tile's accumulator init before the epilogue
+    of two tiles earlier has read that buffer: with the epilogue lagging, the
+    model must report the overwrite."""
+    with pytest.raises(P.ProtocolError, match="accumulator"):
+        for seed in range(20):
+            P.pair_step([0] * 6, 2, seed, gate_acc_empty=False, slow={"epi1": 0.01})
