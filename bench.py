@@ -425,7 +425,8 @@ def batch_throughput(steps: int, count: int = 256):
     """256 independent spectral channels (lattices from {64..512} x {64..256},
     n in {8, 16, 32}, per-channel Rayleigh/HG mixtures), bf16 scattering with
     float32 state, one persistent launch per step replayed from a CUDA graph;
-    pipeline depth from the autotuner.  Returns site-direction updates/s."""
+    pipeline depth and work balance from the autotuner.  Returns
+    site-direction updates/s."""
     import torch
     from paper_2609_23057_b300.solver import Batch, autotune_batch, solver_for
     ws = W.channels(count=count, steps=steps)
@@ -443,7 +444,7 @@ def batch_throughput(steps: int, count: int = 256):
     ms = a.elapsed_time(e)
     sdu = b.site_direction_updates_per_step * steps
     out = {"workload": f"{count} channels, n in {{8,16,32}}, bf16", "steps": steps, "ms": ms,
-           "value": sdu / (ms * 1e-3), "unit": UNIT, "stages": stages,
+           "value": sdu / (ms * 1e-3), "unit": UNIT, "stages": stages, "tile_cost": b.tile_cost,
            "sdu_per_step": b.site_direction_updates_per_step,
            "gbs_algorithmic": sum((32.0 + 16.0 / s.n) * s.nx * s.nz * s.n for s in ss) * steps / (ms * 1e-3) / 1e9}
     b.close()

@@ -282,6 +282,13 @@ rtlb_status rtlb_batch_create(int32_t count, rtlb_ctx *const *channels, rtlb_bat
  * values give RTLB_E_RANGE).  Results do not depend on it. */
 rtlb_status rtlb_batch_configure(rtlb_batch *batch, int32_t stages);
 
+/* Work balance of the batch kernel: each CTA takes one contiguous range of
+ * the batch's tiles (sorted by n, channel, class), ranges of equal estimated
+ * work, a tile counting n + tile_cost directions' worth (default 4; 0 = bytes
+ * only).  tile_cost in [0, 64], else RTLB_E_RANGE.  Synchronizes the device
+ * (launches in flight read the ranges); results do not depend on it. */
+rtlb_status rtlb_batch_balance(rtlb_batch *batch, int32_t tile_cost);
+
 /* Advance every channel nsteps steps on `stream`; pairs of steps replay a
  * captured CUDA graph (one persistent launch per step plus any mixed-tile
  * launches). */

@@ -28,7 +28,7 @@ EXPORTS = [
     "rtlb_total_intensity", "rtlb_steps_done", "rtlb_last_error", "rtlb_destroy",
     "rtlb_stream_offsets", "rtlb_phase_rayleigh", "rtlb_phase_hg", "rtlb_phase_mix",
     "rtlb_residual_noalloc", "rtlb_adjoint", "rtlb_phase_conserve_intensity",
-    "rtlb_batch_create", "rtlb_batch_configure", "rtlb_batch_step", "rtlb_batch_check",
+    "rtlb_batch_create", "rtlb_batch_configure", "rtlb_batch_balance", "rtlb_batch_step", "rtlb_batch_check",
     "rtlb_batch_last_error", "rtlb_batch_destroy", "rtlb_stream_taps", "rtlb_release_workspace",
     "rtlb_dop_out", "rtlb_phase_hg_grad", "rtlb_test_stall_next_step",
 ]
@@ -93,6 +93,7 @@ def lib() -> C.CDLL:
     L.rtlb_release_workspace.argtypes = [vp]
     L.rtlb_batch_create.argtypes = [i32, C.POINTER(vp), C.POINTER(vp)]
     L.rtlb_batch_configure.argtypes = [vp, i32]
+    L.rtlb_batch_balance.argtypes = [vp, i32]
     L.rtlb_batch_step.argtypes = [vp, i32, vp]
     L.rtlb_batch_check.argtypes = [vp, vp]
     L.rtlb_batch_last_error.argtypes = [vp]

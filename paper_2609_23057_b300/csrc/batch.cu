@@ -372,6 +372,8 @@ struct rtlb_batch {
     int n_items = 0;
     int *d_bounds = nullptr;           // [grid + 1] item range of each CTA
     int grid = 0;
+    std::vector<int> item_n;           // direction count of each work item (for the balance)
+    int tile_cost = RTLB_BATCH_TILE_COST;
     std::vector<int> mixed_channels;   // channels with tiles that mix classes
     int *d_err = nullptr, *h_err = nullptr;
     int sm_count = 148;
@@ -387,6 +389,26 @@ rtlb_status batch_fail(rtlb_batch *b, rtlb_status st, const std::string &msg)
 {
     if (b) b->err = msg;
     return st;
+}
+
+// One contiguous item range per CTA, of equal work: a tile moves 32 n bytes
+// per site and carries a fixed cost besides (`cost` directions' worth), so
+// equal tile counts would leave the CTAs holding n = 32 tiles with about twice
+// the work of those holding n = 8.
+std::vector<int> balance_bounds(const std::vector<int> &item_n, int grid, int cost)
+{
+    const int n_items = (int)item_n.size();
+    std::vector<int> bounds(grid + 1, n_items);
+    std::vector<double> pre(item_n.size() + 1, 0.0);
+    for (size_t i = 0; i < item_n.size(); ++i) pre[i + 1] = pre[i] + item_n[i] + cost;
+    size_t i = 0;
+    for (int g = 0; g < grid; ++g) {
+        const double target = pre.back() * g / grid;
+        while (i < item_n.size() && pre[i] < target) ++i;
+        bounds[g] = (int)i;
+    }
+    bounds[grid] = n_items;
+    return bounds;
 }
 
 void drop_graph(rtlb_batch *b)
@@ -498,23 +520,10 @@ rtlb_status rtlb_batch_create(int32_t count, rtlb_ctx *const *channels, rtlb_bat
     });
     cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, channels[0]->dev);
     b->n_items = (int)items.size();
-    // one contiguous item range per CTA, of equal work: a tile moves 32 n
-    // bytes per site and carries a fixed cost besides (RTLB_BATCH_TILE_COST
-    // directions' worth), so equal tile counts would leave the CTAs holding
-    // n = 32 tiles with about twice the work of those holding n = 8
     b->grid = std::min(b->sm_count, b->n_items);
-    std::vector<int> bounds(b->grid + 1, b->n_items);
-    {
-        std::vector<double> pre(items.size() + 1, 0.0);
-        for (size_t i = 0; i < items.size(); ++i) pre[i + 1] = pre[i] + channels[items[i].x]->n + RTLB_BATCH_TILE_COST;
-        size_t i = 0;
-        for (int g = 0; g < b->grid; ++g) {
-            const double target = pre.back() * g / b->grid;
-            while (i < items.size() && pre[i] < target) ++i;
-            bounds[g] = (int)i;
-        }
-        bounds[b->grid] = b->n_items;
-    }
+    b->item_n.resize(items.size());
+    for (size_t i = 0; i < items.size(); ++i) b->item_n[i] = channels[items[i].x]->n;
+    const std::vector<int> bounds = balance_bounds(b->item_n, b->grid, b->tile_cost);
     cudaError_t e = cudaMalloc(&b->d_desc, desc.size() * sizeof(ChanDesc));
     if (e == cudaSuccess && !items.empty()) e = cudaMalloc(&b->d_items, items.size() * sizeof(int2));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_bounds, bounds.size() * sizeof(int));
@@ -541,6 +550,24 @@ rtlb_status rtlb_batch_configure(rtlb_batch *b, int32_t stages)
         return batch_fail(b, RTLB_E_RANGE, "stages must be 2, 4, 6 or 8 and fit in shared memory");
     if (stages != b->stages) drop_graph(b);
     b->stages = stages;
+    return RTLB_OK;
+}
+
+rtlb_status rtlb_batch_balance(rtlb_batch *b, int32_t tile_cost)
+{
+    if (!b) return RTLB_E_ARG;
+    if (tile_cost < 0 || tile_cost > 64) return batch_fail(b, RTLB_E_RANGE, "tile_cost must be in [0, 64]");
+    if (b->grid == 0) {
+        b->tile_cost = tile_cost;
+        return RTLB_OK;
+    }
+    const std::vector<int> bounds = balance_bounds(b->item_n, b->grid, tile_cost);
+    // the ranges are read by launches in flight: wait for them first
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_bounds, bounds.data(), bounds.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return batch_fail(b, RTLB_E_CUDA, std::string("balance: ") + cudaGetErrorString(e));
+    b->tile_cost = tile_cost;
     return RTLB_OK;
 }
 

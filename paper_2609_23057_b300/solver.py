@@ -362,6 +362,7 @@ class Batch:
         check(lib().rtlb_batch_create(len(self.solvers), arr, C.byref(b)))
         self._b = b
         self.stages = 4
+        self.tile_cost = 4
 
     def _check(self, st):
         if st != _lib.RTLB_OK:
@@ -371,6 +372,12 @@ class Batch:
     def configure(self, stages: int):
         self._check(lib().rtlb_batch_configure(self._b, int(stages)))
         self.stages = int(stages)
+
+    def balance(self, tile_cost: int):
+        """Work estimate of a tile in the CTAs' item ranges: n + tile_cost
+        directions' worth (rtlb_batch_balance)."""
+        self._check(lib().rtlb_batch_balance(self._b, int(tile_cost)))
+        self.tile_cost = int(tile_cost)
 
     def step(self, nsteps: int = 1, stream=None):
         self._check(lib().rtlb_batch_step(self._b, int(nsteps), _stream(stream)))
@@ -399,11 +406,16 @@ def _tune_cache_path():
     return os.environ.get("RTLB_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "rtlb_tune.json")
 
 
-def autotune_batch(batch: Batch, candidates=(2, 4, 6, 8), trial_steps: int = 4, cache_path=None) -> int:
-    """Pick the batch kernel's pipeline depth by timing `trial_steps` real
-    steps per candidate (every candidate computes the same result, so the
-    channels simply advance), remember the choice in a JSON cache keyed by
-    device, precision and workload shape, and apply it."""
+def autotune_batch(batch: Batch, candidates=(2, 4, 6, 8), costs=(4, 0, 8, 16), trial_steps: int = 4,
+                   cache_path=None) -> int:
+    """Tune the batch kernel on its own workload: every pipeline depth in
+    `candidates` crossed with every work-balance tile cost in `costs`
+    (rtlb_batch_configure, rtlb_batch_balance), each timed over `trial_steps`
+    real steps (every setting computes the same result, so the channels simply
+    advance; on a tie the setting tried first, the default cost 4, stays).
+    The fastest pair is applied and remembered in a JSON cache
+    keyed by device, precision and workload shape; a cached choice is applied
+    without timing.  Returns the chosen depth (the cost is batch.tile_cost)."""
     import json
     import os
 
@@ -420,26 +432,33 @@ def autotune_batch(batch: Batch, candidates=(2, 4, 6, 8), trial_steps: int = 4, 
         cache = {}
     if key in cache:
         batch.configure(cache[key]["stages"])
+        batch.balance(cache[key].get("tile_cost", 4))
         return cache[key]["stages"]
     best, best_ms = None, float("inf")
-    for st in candidates:
+    for cost in costs:
         try:
-            batch.configure(st)
+            batch.balance(cost)
         except _lib.RtlbError:
             continue
-        batch.step(2)                          # capture + warm
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        batch.step(trial_steps)
-        b.record()
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / trial_steps
-        if ms < best_ms:
-            best, best_ms = st, ms
-    batch.configure(best)
-    cache[key] = {"stages": best, "ms_per_step": best_ms}
+        for st in candidates:
+            try:
+                batch.configure(st)
+            except _lib.RtlbError:
+                continue
+            batch.step(2)                          # capture + warm
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            batch.step(trial_steps)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / trial_steps
+            if ms < best_ms:
+                best, best_ms = (st, cost), ms
+    batch.configure(best[0])
+    batch.balance(best[1])
+    cache[key] = {"stages": best[0], "tile_cost": best[1], "ms_per_step": best_ms}
     os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
     with open(path, "w") as f:
         json.dump(cache, f, indent=1, sort_keys=True)
-    return best
+    return best[0]

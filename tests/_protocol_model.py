@@ -425,6 +425,310 @@ def fp8_step(items, stages, seed, gate_t_ready=True):
     return M.steps
 
 
+def _slot_order(G):
+    """Order in which the FP8X kernel loads and converts a tile's staging
+    slots (its slot_of): 0, 1, 4, 5, 2, 3, 6, 7 at eight slots, in order
+    otherwise."""
+    if G == 8:
+        return [(k & 1) | ((k >> 1) & 1) << 2 | (k >> 2) << 1 for k in range(8)]
+    return list(range(G))
+
+
+def fp8x_step(items, stages, seed, early_handback=False, slow=None):
+    """The split-FP8 kernel (FP8X): as fp8_step (one accumulator handed back
+    per slot through d_free, one t_ready gated on its previous phase, one
+    acc_full), with the slots loaded and converted in the order the epilogue
+    hands them back (_slot_order), the staging slot released before the wait
+    for the slot's hand-off (its values are kept in registers), the A terms
+    and init written after it, each group's packed scale cell written once all
+    of its slots of the tile passed their hand-off, and an epilogue that loads
+    up to two slots at a time and hands them back before storing.
+    early_handback=True: the epilogue arrives on d_free before it has read
+    the columns (a planted flaw)."""
+    M = Machine(seed, slow)
+    T = len(items)
+    n = items[0][0]
+    assert all(it[0] == n for it in items)
+    G, ring = _groups(n), stages // 2
+    order = _slot_order(G)
+    dn = n // 2
+    step = 16 if dn >= 16 else (8 if dn >= 8 else 4)
+    dfree_count = 4 if dn % 8 == 0 else 8
+    st_full = [Barrier(f"st_full[{s}]", 1) for s in range(stages)]
+    st_empty = [Barrier(f"st_empty[{s}]", 4) for s in range(stages)]
+    d_free = [Barrier(f"d_free[{j}]", dfree_count) for j in range(G)]
+    t_ready, acc_full = Barrier("t_ready", 8), Barrier("acc_full", 1)
+    z_full, z_free = Barrier("z_full", 1), Barrier("z_free", 1)
+    stage = [None] * stages
+    A, SA, acc, z, mma_done = {}, {}, {}, [None], [-1]
+
+    def producer():
+        prev, zr, gq = None, 0, [0, 0]
+        for i, (_, key) in enumerate(items):
+            if key != prev:
+                if i > 0:
+                    yield Wait(z_free, zr, "producer")
+                    zr += 1
+                z_full.expect_tx(1)
+
+                def land_z(key=key):
+                    z[0] = key
+                    z_full.complete_tx(1)
+                M.tma_load(land_z)
+                prev = key
+            for j in order:
+                gr = j & 1
+                local = gq[gr]
+                gq[gr] += 1
+                s = gr * ring + local % ring
+                yield Wait(st_empty[s], local // ring - 1, "producer")
+                st_full[s].expect_tx(1)
+
+                def land(s=s, tag=(i, j)):
+                    stage[s] = tag
+                    st_full[s].complete_tx(1)
+                M.tma_load(land)
+
+    def converter(q, grp):
+        who = f"converter(q{q},g{grp})"
+        gq = 0
+        mine = [j for j in order if j & 1 == grp]
+        for i, _ in enumerate(items):
+            for j in mine:
+                local = gq
+                gq += 1
+                s = grp * ring + local % ring
+                yield Wait(st_full[s], local // ring, who)
+                if stage[s] != (i, j):
+                    raise ProtocolError(f"{who} tile {i} slot {j}: staging slot {s} holds {stage[s]}")
+                st_empty[s].arrive()                       # values kept in registers
+                yield Wait(d_free[j], i - 1, who)
+                cell = acc.get((j, q))
+                if cell is not None and cell[0] != "free":
+                    raise ProtocolError(f"{who} tile {i}: accumulator slot {j} still {cell[0]} for tile {cell[1]}")
+                acc[(j, q)] = ["init", i, 0]
+                if mma_done[0] < i - 1:
+                    raise ProtocolError(f"{who} tile {i}: A slot {j} rewritten before tile {i - 1}'s MMAs completed")
+                A[(j, q)] = i
+            if mine:
+                if mma_done[0] < i - 1:
+                    raise ProtocolError(f"{who} tile {i}: scale cell rewritten before tile {i - 1}'s MMAs completed")
+                SA[(grp, q)] = i
+            yield Wait(t_ready, i - 1, who)
+            t_ready.arrive()
+
+    def mma():
+        prev, zl = None, 0
+        for i, (_, key) in enumerate(items):
+            if key != prev:
+                yield Wait(z_full, zl, "mma")
+                zl += 1
+                prev = key
+            yield Wait(t_ready, i, "mma")
+
+            def done(i=i, key=key):
+                for j in range(G):
+                    for q in range(4):
+                        if A.get((j, q)) != i:
+                            raise ProtocolError(f"MMA tile {i}: A slot ({j},{q}) holds tile {A.get((j, q))}")
+                        cell = acc.get((j, q))
+                        if cell is None or cell[0] != "init" or cell[1] != i:
+                            raise ProtocolError(f"MMA tile {i}: accumulator slot ({j},{q}) is {cell}")
+                        cell[0] = "done"
+                for g in range(min(2, G)):
+                    for q in range(4):
+                        if SA.get((g, q)) != i:
+                            raise ProtocolError(f"MMA tile {i}: scale cell ({g},{q}) holds tile {SA.get((g, q))}")
+                if z[0] != key:
+                    raise ProtocolError(f"MMA tile {i}: table {z[0]} resident, {key} needed")
+                mma_done[0] = i
+            M.issue_mma(done)
+            M.commit(acc_full)
+            if i + 1 < T and items[i + 1][1] != key:
+                M.commit(z_free)
+
+    def epilogue(q, dh):
+        who = f"epilogue(q{q},h{dh})"
+        for i, _ in enumerate(items):
+            yield Wait(acc_full, i, who)
+            for d0 in range(dh * dn, dh * dn + dn, step):
+                slots = sorted({d // 8 for d in range(d0, d0 + step)})
+                if early_handback:
+                    for j in slots:
+                        d_free[j].arrive()
+                    yield None                              # the converters may run here
+                for j in slots:
+                    cell = acc.get((j, q))
+                    if cell is None or cell[0] not in ("done", "read") or cell[1] != i:
+                        raise ProtocolError(f"{who} tile {i}: accumulator slot {j} is {cell}")
+                    cell[0] = "read"
+                    cell[2] += 1
+                    if cell[2] == (2 if dn < 8 else 1):
+                        cell[0] = "free"
+                if not early_handback:
+                    for j in slots:
+                        d_free[j].arrive()
+
+    M.add_role("producer", producer())
+    M.add_role("mma", mma())
+    for q in range(4):
+        for grp in range(2):
+            M.add_role(f"conv{q}{grp}", converter(q, grp))
+        for dh in range(2):
+            M.add_role(f"epi{q}{dh}", epilogue(q, dh))
+    M.run()
+    return M.steps
+
+
+def tf32_step(items, stages, seed, gate_ring=True, slow=None):
+    """The 3xTF32 kernel (4n <= 128): two accumulators D and two exact-part
+    regions E in TMEM, a ring of split state chunks in shared memory (Rg
+    slots per converter group: 1 at n = 32, 2 below).  Per tile the
+    converters wait for the epilogue of tile i - 2 (acc_empty[b]) before
+    writing E[b]; per staging slot j (group j & 1) they wait for the slot's
+    load and for the MMAs on their next ring slot (a_empty), write the hi and
+    lo chunk and E's columns, release the staging slot and report the ring
+    slot (a_full, count 4).  The MMA thread waits for acc_empty[b], then
+    chunk by chunk on a_full (the first MMA of a tile starts D from zero)
+    and commits a_empty per chunk, acc_full per tile.  gate_ring=False: the
+    converters skip the a_empty wait (a planted flaw)."""
+    M = Machine(seed, slow)
+    T = len(items)
+    n = items[0][0]
+    assert all(it[0] == n for it in items) and 4 * n <= 128
+    G, ring = _groups(n), stages // 2
+    Rg = 1 if 4 * n >= 128 else 2
+    st_full = [Barrier(f"st_full[{s}]", 1) for s in range(stages)]
+    st_empty = [Barrier(f"st_empty[{s}]", 4) for s in range(stages)]
+    a_full = [Barrier(f"a_full[{k}]", 4) for k in range(2 * Rg)]
+    a_empty = [Barrier(f"a_empty[{k}]", 1) for k in range(2 * Rg)]
+    acc_full = [Barrier(f"acc_full[{b}]", 1) for b in range(2)]
+    acc_empty = [Barrier(f"acc_empty[{b}]", 8) for b in range(2)]
+    z_full, z_free = Barrier("z_full", 1), Barrier("z_free", 1)
+    stage = [None] * stages
+    ringd, E, D, z = {}, {}, {}, [None]
+
+    def producer():
+        prev, zr, gq = None, 0, [0, 0]
+        for i, (_, key) in enumerate(items):
+            if key != prev:
+                if i > 0:
+                    yield Wait(z_free, zr, "producer")
+                    zr += 1
+                z_full.expect_tx(1)
+
+                def land_z(key=key):
+                    z[0] = key
+                    z_full.complete_tx(1)
+                M.tma_load(land_z)
+                prev = key
+            for j in range(G):
+                gr = j & 1
+                local = gq[gr]
+                gq[gr] += 1
+                s = gr * ring + local % ring
+                yield Wait(st_empty[s], local // ring - 1, "producer")
+                st_full[s].expect_tx(1)
+
+                def land(s=s, tag=(i, j)):
+                    stage[s] = tag
+                    st_full[s].complete_tx(1)
+                M.tma_load(land)
+
+    def converter(q, grp):
+        who = f"converter(q{q},g{grp})"
+        gq, mc = 0, 0
+        for i, _ in enumerate(items):
+            b = i & 1
+            yield Wait(acc_empty[b], (i >> 1) - 1, who)
+            for j in range(grp, G, 2):
+                local = gq
+                gq += 1
+                s = grp * ring + local % ring
+                m = mc
+                mc += 1
+                k = grp * Rg + m % Rg
+                yield Wait(st_full[s], local // ring, who)
+                if gate_ring:
+                    yield Wait(a_empty[k], m // Rg - 1, who)
+                if stage[s] != (i, j):
+                    raise ProtocolError(f"{who} tile {i} slot {j}: staging slot {s} holds {stage[s]}")
+                cell = ringd.get((k, q))
+                if cell is not None and cell[1] != "used":
+                    raise ProtocolError(f"{who} tile {i} slot {j}: ring slot {k} still holds {cell} unread")
+                ringd[(k, q)] = [(i, j), "written"]
+                e = E.get((b, j, q))
+                if e is not None and e[1] != "read":
+                    raise ProtocolError(f"{who} tile {i}: exact part {b} slot {j} still {e}")
+                E[(b, j, q)] = [i, "written"]
+                st_empty[s].arrive()
+                a_full[k].arrive()
+
+    def mma():
+        prev, zl, mc = None, 0, [0, 0]
+        for i, (_, key) in enumerate(items):
+            b = i & 1
+            if key != prev:
+                yield Wait(z_full, zl, "mma")
+                zl += 1
+                prev = key
+            yield Wait(acc_empty[b], (i >> 1) - 1, "mma")
+            for j in range(G):
+                g = j & 1
+                m = mc[g]
+                mc[g] += 1
+                k = g * Rg + m % Rg
+                yield Wait(a_full[k], m // Rg, "mma")
+
+                def done(i=i, b=b, j=j, k=k, key=key):
+                    if z[0] != key:
+                        raise ProtocolError(f"MMA tile {i}: table {z[0]} resident, {key} needed")
+                    for q in range(4):
+                        cell = ringd.get((k, q))
+                        if cell is None or cell[0] != (i, j) or cell[1] != "written":
+                            raise ProtocolError(f"MMA tile {i} chunk {j}: ring slot {k} ({q}) is {cell}")
+                        cell[1] = "used"
+                        for dh in range(2):
+                            d = D.get((b, q, dh))
+                            if j == 0:
+                                if d is not None and d[1] != "read":
+                                    raise ProtocolError(f"MMA tile {i}: accumulator {b} ({q},{dh}) still {d}")
+                            elif d != [i, "partial"]:
+                                raise ProtocolError(f"MMA tile {i} chunk {j}: accumulator {b} ({q},{dh}) is {d}")
+                            D[(b, q, dh)] = [i, "done" if j == G - 1 else "partial"]
+                M.issue_mma(done)
+                M.commit(a_empty[k])
+            M.commit(acc_full[b])
+            if i + 1 < T and items[i + 1][1] != key:
+                M.commit(z_free)
+
+    def epilogue(q, dh):
+        who = f"epilogue(q{q},h{dh})"
+        for i, _ in enumerate(items):
+            b = i & 1
+            yield Wait(acc_full[b], i >> 1, who)
+            d = D.get((b, q, dh))
+            if d != [i, "done"]:
+                raise ProtocolError(f"{who} tile {i}: accumulator {b} is {d}")
+            d[1] = "read"
+            for j in sorted({dd // 8 for dd in range(dh * n // 2, (dh + 1) * n // 2)}):
+                e = E.get((b, j, q))
+                if e is None or e[0] != i:
+                    raise ProtocolError(f"{who} tile {i}: exact part {b} slot {j} is {e}")
+                e[1] = "read"
+            acc_empty[b].arrive()
+
+    M.add_role("producer", producer())
+    M.add_role("mma", mma())
+    for q in range(4):
+        for grp in range(2):
+            M.add_role(f"conv{q}{grp}", converter(q, grp))
+        for dh in range(2):
+            M.add_role(f"epi{q}{dh}", epilogue(q, dh))
+    M.run()
+    return M.steps
+
+
 def pair_step(keys, stages, seed, n=64, gate_acc_empty=True, slow=None):
     """The CTA-pair kernel (cta_group::2, bf16 state operand and split table):
     each entry of `keys` is one pair of tiles (one per CTA) of the same table

@@ -41,10 +41,11 @@ def _mixed_n_channels():
     return ws
 
 
-@pytest.mark.parametrize("stages", [2, 4, 6, 8])
-def test_batch_mixed_direction_counts_every_depth(torch_cuda, stages):
-    """Bitwise equality with single stepping at every pipeline depth on a
-    batch whose CTA slices mix n = 8, 16 and 32."""
+@pytest.mark.parametrize("stages,tile_cost", [(2, 4), (4, 4), (6, 4), (8, 4), (4, 0), (2, 16), (8, 64)])
+def test_batch_mixed_direction_counts_every_depth(torch_cuda, stages, tile_cost):
+    """Bitwise equality with single stepping at every pipeline depth and at
+    several work balances (other CTA item ranges) on a batch whose CTA slices
+    mix n = 8, 16 and 32."""
     from paper_2609_23057_b300.solver import Batch, solver_for
     ws = _mixed_n_channels()
     states = [W.random_state(w.nz, w.nx, w.n, seed=300 + k, dtype=np.float32) for k, w in enumerate(ws)]
@@ -56,6 +57,7 @@ def test_batch_mixed_direction_counts_every_depth(torch_cuda, stages):
             lst.append(s)
     b = Batch(bs)
     b.configure(stages)
+    b.balance(tile_cost)
     b.step(6)
     b.check()
     for s in single:
@@ -76,6 +78,10 @@ def test_batch_rejects_odd_depth(torch_cuda):
     for st in (1, 3, 5, 10):
         with pytest.raises(_lib.RtlbError) as ei:
             b.configure(st)
+        assert ei.value.status == 3
+    for cost in (-1, 65):
+        with pytest.raises(_lib.RtlbError) as ei:
+            b.balance(cost)
         assert ei.value.status == 3
     b.close()
     for s in ss:
@@ -137,10 +143,10 @@ def test_autotune_picks_and_caches(torch_cuda, tmp_path):
     ss = [solver_for(w, "bf16") for w in ws]
     b = Batch(ss)
     cache = tmp_path / "tune.json"
-    st = autotune_batch(b, candidates=(2, 4, 8), trial_steps=2, cache_path=str(cache))
-    assert st in (2, 4, 8)
+    st = autotune_batch(b, candidates=(2, 4, 8), costs=(4, 0, 16), trial_steps=2, cache_path=str(cache))
+    assert st in (2, 4, 8) and b.tile_cost in (4, 0, 16)
     data = json.loads(cache.read_text())
-    assert list(data.values())[0]["stages"] == st
+    assert list(data.values())[0]["stages"] == st and list(data.values())[0]["tile_cost"] == b.tile_cost
     assert autotune_batch(b, cache_path=str(cache)) == st      # served from the cache
     b.check()
     b.close()

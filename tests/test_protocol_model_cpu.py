@@ -80,3 +80,45 @@ def test_cta_pair_model_sees_unreleased_accumulator():
     with pytest.raises(P.ProtocolError, match="accumulator"):
         for seed in range(20):
             P.pair_step([0] * 6, 2, seed, gate_acc_empty=False, slow={"epi1": 0.01})
+
+
+@pytest.mark.parametrize("n", [8, 16, 32, 64])
+@pytest.mark.parametrize("stages", [2, 4])
+def test_fp8x_step_is_race_free(n, stages):
+    """The split-FP8 kernel: slots in hand-back order, staging released before
+    the hand-off wait, packed scale cells per group, two-slot epilogue loads;
+    also with one role lagging far behind."""
+    for seed in range(6):
+        P.fp8x_step([(n, 0), (n, 0), (n, 1), (n, 1), (n, 0)], stages, seed)
+    for slow in ("epi", "conv1", "mma", "producer"):
+        P.fp8x_step([(n, 0), (n, 0), (n, 1)], stages, 0, slow={slow: 0.01})
+
+
+def test_fp8x_model_sees_early_handback():
+    """An epilogue that hands a slot back before reading its columns lets the
+    next tile's init overwrite them: the model must report it."""
+    with pytest.raises(P.ProtocolError, match="accumulator"):
+        for seed in range(5):
+            P.fp8x_step([(64, 0)] * 4, 2, seed, early_handback=True)
+
+
+@pytest.mark.parametrize("n", [8, 16, 32])
+@pytest.mark.parametrize("stages", [2, 4, 6])
+def test_tf32_step_is_race_free(n, stages):
+    """The 3xTF32 kernel: ring of split chunks (a_full / a_empty), double D
+    and E, chunk-wise MMAs from a zero accumulator; also with one role
+    lagging far behind."""
+    for seed in range(6):
+        P.tf32_step([(n, 0), (n, 0), (n, 1), (n, 1), (n, 0)], stages, seed)
+    for slow in ("epi", "conv1", "mma", "producer"):
+        P.tf32_step([(n, 0), (n, 0), (n, 1)], stages, 0, slow={slow: 0.01})
+
+
+def test_tf32_model_sees_ungated_ring():
+    """At n = 32 (one ring slot per group) converters that skip the wait for
+    the MMAs on their ring slot overwrite a chunk the MMA has not read: the
+    model must report it.  (At n <= 16 the wait on the epilogue of tile
+    i - 2 already implies it.)"""
+    with pytest.raises(P.ProtocolError, match="ring slot"):
+        for seed in range(5):
+            P.tf32_step([(32, 0)] * 4, 2, seed, gate_ring=False)
