@@ -599,7 +599,7 @@ def run_ours(args):
             line["bilinear"] = _leg(bilinear_throughput, args.precision, args.bilinear_steps, t_max / args.steps, peaks,
                                     src)
         if ws == 1 and args.batch_steps > 0:
-            line["batch"] = _leg(batch_throughput, args.batch_steps)
+            line["batch"] = _leg(batch_throughput, args.batch_steps, args.batch_channels)
         if ws == 1 and args.adjoint_steps > 0:
             adj = _leg(adjoint_ratio, args.adjoint_steps, args.precision)
             line["adjoint"] = adj
@@ -632,6 +632,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip timing the FP32 comparison form")
     ap.add_argument("--bilinear-steps", type=int, default=50,
                     help="steps of the bilinear-streaming timing (0 = skip)")
+    ap.add_argument("--batch-channels", type=int, default=256,
+                    help="channels of the batch leg (profiling of smaller cases)")
     ap.add_argument("--batch-steps", type=int, default=500,
                     help="steps of the 256-channel batch timing (0 = skip)")
     ap.add_argument("--fp32-class-steps", type=int, default=100,
