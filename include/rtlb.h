@@ -231,11 +231,14 @@ rtlb_status rtlb_dop_out(rtlb_ctx *ctx, int32_t side, float *out, void *stream);
  * Device memory: ceil(nsteps/checkpoint_every) + max(checkpoint_every - 1, 2)
  * + 3 states (checkpoint_every = 1: nsteps + 3, and no step is recomputed;
  * one more for BILINEAR) plus the table-gradient accumulators.  n must be in
- * {8, 16, 32, 64}.  At n = 32 with NEAREST streaming the reverse step's
- * transposed contraction and the table gradient run on the tensor cores with
- * bf16 hi + lo operands (about 16 significand bits per product, float32
- * accumulation; the first call after rtlb_set_medium builds the transposed
- * tables); elsewhere on the CUDA cores in float32.  Two identical calls return
+ * {8, 16, 32, 64}.  At n in {8, 16, 32} with NEAREST streaming the reverse
+ * step's transposed contraction runs on the tensor cores with bf16 hi + lo
+ * operands (about 16 significand bits per product, float32 accumulation; the
+ * first call after rtlb_set_medium builds the transposed tables) -- at n = 8
+ * and 16 only when every 128-site tile of the medium is of one phase class;
+ * elsewhere it runs on the CUDA cores in float32.  The table gradient runs on
+ * the tensor cores (same split) where n <= 32 and n_phase * 4n <= 512, on the
+ * CUDA cores otherwise.  Two identical calls return
  * identical results (no atomics in the sums).  The workspace stays allocated
  * after the call (see rtlb_release_workspace).  Synchronizes. */
 rtlb_status rtlb_adjoint(rtlb_ctx *ctx, int32_t nsteps, int32_t checkpoint_every, const float *dL_dout,

@@ -1,4 +1,4 @@
-// Tensor-core reverse step of the adjoint (4n = 128), transposed-stream form.
+// Tensor-core reverse step of the adjoint (4n in {32, 64, 128}), transposed-stream form.
 //
 // With nu^t = T^T lambda^{t+1} (the adjoint state already pulled back along
 // the streaming), one reverse step of the affine step S^{t+1} = T (C S^t + c0)
@@ -15,8 +15,10 @@
 // bits per operand, float32 accumulation).
 //
 // Warp roles as in the forward tensor-core step: warps 0-7 epilogue, 8-15
-// converters (two groups on alternate staging slots), 16 TMA producer, 17
-// MMA issuer.  TMEM holds two buffers of [Y | nu] (4 x 4n = 512 columns): the
+// converters (two groups on alternate staging slots; at 4n = 32 the tile has
+// one slot and group 1 only reports), 16 TMA producer, 17 MMA issuer.  K is
+// padded to whole 64-column chunks in shared memory and the tables; the MMAs
+// stop at K = 4n.  TMEM holds two buffers of [Y | nu] (4 x 4n columns): the
 // converters copy nu into TMEM beside the accumulator so the epilogue has both
 // without reading nu again.  The epilogue reads S^t from HBM for the dot
 // products; the two halves of a site's directions (warps q and q + 4) add
@@ -43,11 +45,16 @@ namespace {
 using namespace tcptx;
 using namespace tccommon;
 
-constexpr int kN4 = 128;                       // 4n (n = 32)
-constexpr int kC = kN4 / 64;                   // 64-wide bf16 K chunks
-constexpr int kGroups = kN4 / 4 / kDirsPerStage;   // staging slots per tile
-constexpr uint32_t kZChunk = (uint32_t)kN4 * 128u;
 constexpr uint32_t kAChunk = (uint32_t)kTileM * 128u;
+
+// Shape constants of the form at 4n = N4.
+template <int N4>
+struct AdjTcShape {
+    static constexpr int C = (N4 + 63) / 64;                 // 64-wide bf16 K chunks (K padded)
+    static constexpr int G = N4 / 4 / kDirsPerStage;         // staging slots per tile
+    static constexpr uint32_t ZChunk = (uint32_t)N4 * 128u;  // one K chunk of one table part
+    static constexpr uint32_t TCols = 4u * N4;               // two buffers of [Y | nu]
+};
 
 struct AdjTcParams {
     const float4 *S;        // S^t, direction-major
@@ -65,10 +72,13 @@ struct AdjTcParams {
 
 __device__ int g_adj_tc_err;
 
+template <int kN4>
 __global__ void __launch_bounds__(kThreads, 1)
     k_adj_step_tc(const __grid_constant__ CUtensorMap tmNu, const __grid_constant__ CUtensorMap tmZhi,
                   const __grid_constant__ CUtensorMap tmZlo, AdjTcParams p, int stages)
 {
+    constexpr int kC = AdjTcShape<kN4>::C, kGroups = AdjTcShape<kN4>::G;
+    constexpr uint32_t kZChunk = AdjTcShape<kN4>::ZChunk;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const int n = p.n;
@@ -95,7 +105,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int8_t *s_cz = s_cx + kMaxDirs;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t tcols = 512;                // two buffers of [Y | nu]
+    const uint32_t tcols = AdjTcShape<kN4>::TCols;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
@@ -193,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(b * 2 * kN4);       // Y of buffer b
                 for (int c = 0; c < kC; ++c) {
-                    for (int kk = 0; kk < 4; ++kk) {
+                    for (int kk = 0; kk < 4 && 64 * c + 16 * kk < kN4; ++kk) {   // K stops at 4n
                         const uint32_t ao = c * kAChunk + kk * 32, zo = c * kZChunk + kk * 32;
                         const uint64_t ah = sw128_desc(smem_u32(sA + ao)), al = sw128_desc(smem_u32(sAlo + ao));
                         const uint64_t zh = sw128_desc(smem_u32(sZ + zo)), zlo = sw128_desc(smem_u32(sZlo + zo));
@@ -234,6 +244,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t nu_t = tmem + lane_base + (uint32_t)(b * 2 * kN4 + kN4);
             for (int c = 0; c < kC && ok; ++c) {
                 const int j = 2 * c + grp;                 // this group's staging slot of K chunk c
+                if (j >= kGroups) continue;                // 4n = 32: group 1 has no slot
                 const int d_beg = kDirsPerStage * j;
                 const uint32_t local = gq++;
                 const int s = ring_slot(grp, local, ring);
@@ -361,18 +372,46 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == kMmaWarp) tmem_dealloc(tmem, tcols);
 }
 
+template <int N4>
 size_t adj_tc_smem(int stages)
 {
-    return (size_t)2 * kC * kZChunk + (size_t)2 * kC * kAChunk + (size_t)stages * kStageBytes +
-           (size_t)(2 * stages + kC + 9) * 8 + 16 + 2 * kMaxDirs + 1024;
+    constexpr int C = AdjTcShape<N4>::C;
+    return (size_t)2 * C * AdjTcShape<N4>::ZChunk + (size_t)2 * C * kAChunk + (size_t)stages * kStageBytes +
+           (size_t)(2 * stages + C + 9) * 8 + 16 + 2 * kMaxDirs + 1024;
+}
+
+size_t adj_tc_smem_n(int n, int stages)
+{
+    switch (4 * n) {
+    case 32: return adj_tc_smem<32>(stages);
+    case 64: return adj_tc_smem<64>(stages);
+    case 128: return adj_tc_smem<128>(stages);
+    default: return 0;
+    }
+}
+
+template <int N4>
+cudaError_t launch_tc(const CUtensorMap &tmNu, const CUtensorMap &tmZhi, const CUtensorMap &tmZlo, const AdjTcParams &p,
+                      int stages, int grid, cudaStream_t s)
+{
+    const size_t smem = adj_tc_smem<N4>(stages);
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(k_adj_step_tc<N4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_adj_step_tc<N4><<<grid, kThreads, smem, s>>>(tmNu, tmZhi, tmZlo, p, stages);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-int adjoint_tc_stages()
+int adjoint_tc_stages(int n)
 {
+    if (n != 8 && n != 16 && n != 32) return 0;
     for (int st = 8; st >= 2; st -= 2)
-        if (adj_tc_smem(st) <= (size_t)kSmemLimit) return st;
+        if (adj_tc_smem_n(n, st) <= (size_t)kSmemLimit) return st;
     return 0;
 }
 
@@ -399,17 +438,15 @@ cudaError_t launch_adjoint_step_tc(const CUtensorMap &tmNu, const CUtensorMap &t
         if (e != cudaSuccess) return e;
     }
     p.err = err;
-    const int stages = adjoint_tc_stages();
-    const size_t smem = adj_tc_smem(stages);
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(k_adj_step_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    const int stages = adjoint_tc_stages(a.n);
+    if (stages == 0) return cudaErrorInvalidValue;
     const int grid = std::min(a.sm_count, a.n_tiles);
-    k_adj_step_tc<<<grid, kThreads, smem, s>>>(tmNu, tmZhi, tmZlo, p, stages);
-    return cudaGetLastError();
+    switch (4 * a.n) {
+    case 32: return launch_tc<32>(tmNu, tmZhi, tmZlo, p, stages, grid, s);
+    case 64: return launch_tc<64>(tmNu, tmZhi, tmZlo, p, stages, grid, s);
+    case 128: return launch_tc<128>(tmNu, tmZhi, tmZlo, p, stages, grid, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // Nonzero when the reverse-step kernel gave up waiting since the last call

@@ -412,8 +412,9 @@ cudaError_t launch_adjoint_step(const AdjointParams &p, double *slots, cudaStrea
 
 cudaError_t launch_adjoint_step_nu_mixed(const AdjointParams &p, int n_tiles, cudaStream_t s)
 {
-    if (p.n != 32) return cudaErrorInvalidValue;
-    return n_tiles > 0 ? launch_adj<128, true>(p, n_tiles, s) : cudaSuccess;
+    if (n_tiles == 0) return cudaSuccess;
+    if (p.n != 32) return cudaErrorInvalidValue;   // the variant exists for 4n = 128 only
+    return launch_adj<128, true>(p, n_tiles, s);
 }
 
 cudaError_t launch_adjoint_table(const AdjointParams &p, double *slots, cudaStream_t s)

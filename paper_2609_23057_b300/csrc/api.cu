@@ -583,18 +583,19 @@ static rtlb_status prepare_adj_tc(rtlb_ctx *c)
     AdjTcState &a = c->adj_tc;
     if (a.gen == c->medium_gen) return RTLB_OK;
     a.release();
-    const int n = c->n, N4 = 4 * n, np = c->n_phase;
-    const size_t ns = c->nsites(), tsz = (size_t)N4 * N4;
+    const int n = c->n, N4 = 4 * n, np = c->n_phase, KP = (N4 + 63) / 64 * 64;
+    const size_t ns = c->nsites(), tsz = (size_t)N4 * N4, psz = (size_t)N4 * KP;
     std::vector<float> Z((size_t)np * tsz);
     CK(c, cudaMemcpy(Z.data(), c->d_Z, Z.size() * sizeof(float), cudaMemcpyDeviceToHost), "adjoint tables");
-    std::vector<__nv_bfloat16> hi(Z.size()), lo(Z.size());
+    // Z^T rows (one per output of the transposed contraction), K padded with zeros
+    std::vector<__nv_bfloat16> hi((size_t)np * psz, __float2bfloat16(0.f)), lo((size_t)np * psz, __float2bfloat16(0.f));
     for (int ph = 0; ph < np; ++ph)
         for (int col = 0; col < N4; ++col)
             for (int k = 0; k < N4; ++k) {
                 const float v = Z[(size_t)ph * tsz + (size_t)k * N4 + col];
                 const __nv_bfloat16 h = __float2bfloat16(v);
-                hi[(size_t)ph * tsz + (size_t)col * N4 + k] = h;
-                lo[(size_t)ph * tsz + (size_t)col * N4 + k] = __float2bfloat16(v - __bfloat162float(h));
+                hi[(size_t)ph * psz + (size_t)col * KP + k] = h;
+                lo[(size_t)ph * psz + (size_t)col * KP + k] = __float2bfloat16(v - __bfloat162float(h));
             }
     std::vector<uint8_t> cls(ns);
     CK(c, cudaMemcpy(cls.data(), c->d_cls, ns, cudaMemcpyDeviceToHost), "adjoint classes");
@@ -624,8 +625,8 @@ static rtlb_status prepare_adj_tc(rtlb_ctx *c)
     if (!mixed.empty())
         CK(c, cudaMemcpy(a.mixed.p, mixed.data(), mixed.size() * sizeof(int), cudaMemcpyHostToDevice), "adjoint tiles");
     CK(c, cudaMemcpy(a.dirT.p, dirT.data(), dirT.size() * sizeof(int), cudaMemcpyHostToDevice), "adjoint offsets");
-    if (!tc_encode_table_map(&a.tmZhi, a.zhi.as<__nv_bfloat16>(), N4, N4, np, N4) ||
-        !tc_encode_table_map(&a.tmZlo, a.zlo.as<__nv_bfloat16>(), N4, N4, np, N4))
+    if (!tc_encode_table_map(&a.tmZhi, a.zhi.as<__nv_bfloat16>(), N4, KP, np, N4) ||
+        !tc_encode_table_map(&a.tmZlo, a.zlo.as<__nv_bfloat16>(), N4, KP, np, N4))
         return fail(c, RTLB_E_CUDA, "tensor map encoding for the adjoint tables failed");
     a.n_pure = (int)pure.size();
     a.n_mixed = (int)mixed.size();
@@ -697,12 +698,16 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
     } while (0)
     int bcT[4];
     for (int k = 0; k < 4; ++k) bcT[k] = c->bc[k] == RTLB_BC_PERIODIC ? RTLB_BC_PERIODIC : RTLB_BC_VACUUM;
-    // 4n = 128 with nearest-neighbour streaming: the reverse step runs on the
-    // tensor cores in the transposed-stream form
-    const bool nu_form = c->n == 32 && !bilinear(c) && adjoint_tc_stages() > 0;
+    // 4n in {32, 64, 128} with nearest-neighbour streaming: the reverse step
+    // runs on the tensor cores in the transposed-stream form.  Tiles that mix
+    // phase classes take a CUDA-core variant of that form, which exists for
+    // 4n = 128 only: at n = 8 and 16 a medium with such tiles keeps the
+    // lambda form on the CUDA cores.
+    bool nu_form = !bilinear(c) && adjoint_tc_stages(c->n) > 0;
     if (nu_form) {
         st = prepare_adj_tc(c);
         if (st != RTLB_OK) return st;
+        if (c->n != 32 && c->adj_tc.n_mixed > 0) nu_form = false;
     }
     if (bilinear(c)) {
         st = ensure_post(c);

@@ -28,12 +28,13 @@ rtlb_status tc_arm_stall(rtlb_ctx *c);
 int tc_mixed_tiles(const rtlb_ctx *c);
 void tc_release(rtlb_ctx *c);
 
-// Tensor-core reverse step of the adjoint (adj_tc.cu), 4n = 128 only: reads
+// Tensor-core reverse step of the adjoint (adj_tc.cu), 4n in {32, 64, 128}: reads
 // nu^t (tensor map tmNu, direction-major) and S^t, writes nu^{t-1} pushed
 // along the negated offsets (push = 1) or lambda^0 in place (push = 0), and
 // adds the per-site gradient sums into g_alpha / g_beta, each [2][nsites]
 // (one half per group of directions).  Tables: Z^T as bf16 hi and lo,
-// [n_phase][128][128], tensor maps with 128-row boxes.  `tiles` lists
+// [n_phase][4n][KP] (K padded with zeros to KP = 4n rounded up to 64), tensor
+// maps with 4n-row boxes.  `tiles` lists
 // single-class 128-site tiles sorted by class (tile | class << 24).
 struct AdjTcLaunch {
     const float *S;
@@ -48,7 +49,7 @@ struct AdjTcLaunch {
     int push;
     int sm_count;
 };
-int adjoint_tc_stages();
+int adjoint_tc_stages(int n);   // 0 where the form does not exist (n not in {8, 16, 32})
 cudaError_t launch_adjoint_step_tc(const CUtensorMap &tmNu, const CUtensorMap &tmZhi, const CUtensorMap &tmZlo,
                                    const AdjTcLaunch &a, cudaStream_t s);
 int adjoint_step_tc_take_error();

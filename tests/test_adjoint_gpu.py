@@ -107,17 +107,24 @@ def test_adjoint_many_chunks_per_block(torch_cuda, orc, nzen, naz):
     assert _rel(gS, rS) < TOL
 
 
-@pytest.mark.parametrize("nx,nz,bc,nph,K", [
-    (256, 6, (2, 0, 1, 1), 2, 5),      # rows alternate class, 128 | nx: every tile single-class
-    (200, 7, (2, 0, 0, 0), 2, 1),      # tiles straddle rows: single-class and mixed tiles
-    (130, 3, (1, 1, 2, 0), 1, 4),      # one class, ragged last tile, periodic z
-    (384, 4, (2, 2, 1, 1), 3, 12),
+@pytest.mark.parametrize("nx,nz,bc,nph,K,nzen,naz", [
+    (256, 6, (2, 0, 1, 1), 2, 5, 4, 8),      # rows alternate class, 128 | nx: every tile single-class
+    (200, 7, (2, 0, 0, 0), 2, 1, 4, 8),      # tiles straddle rows: single-class and mixed tiles
+    (130, 3, (1, 1, 2, 0), 1, 4, 4, 8),      # one class, ragged last tile, periodic z
+    (384, 4, (2, 2, 1, 1), 3, 12, 4, 8),
+    (256, 6, (2, 0, 1, 1), 2, 5, 2, 4),      # n = 8: one staging slot per tile, K padded to 64
+    (130, 3, (1, 1, 2, 0), 1, 4, 2, 4),
+    (256, 6, (2, 0, 1, 1), 2, 5, 4, 4),      # n = 16
+    (384, 4, (2, 2, 1, 1), 3, 12, 4, 4),
+    (200, 7, (2, 0, 0, 0), 2, 1, 4, 4),      # mixed tiles at n = 16: the CUDA-core lambda form
 ])
-def test_adjoint_tensor_core_reverse_step(torch_cuda, orc, nx, nz, bc, nph, K):
-    """n = 32: the reverse step runs on the tensor cores over single-class
-    128-site tiles (the rest on the CUDA cores), in the transposed-stream
-    form; gradients and dL/dS0 against the oracle adjoint."""
-    w = W.random_medium(nx, nz, 4, 8, seed=nx + nz, bc=bc, n_phase=nph, steps=9, surv_mode=1)
+def test_adjoint_tensor_core_reverse_step(torch_cuda, orc, nx, nz, bc, nph, K, nzen, naz):
+    """n in {8, 16, 32}: the reverse step runs on the tensor cores over
+    single-class 128-site tiles in the transposed-stream form (at n = 32 the
+    mixed tiles on a CUDA-core variant of that form; at n = 8 and 16 a medium
+    with mixed tiles keeps the CUDA-core lambda form); gradients and dL/dS0
+    against the oracle adjoint."""
+    w = W.random_medium(nx, nz, nzen, naz, seed=nx + nz, bc=bc, n_phase=nph, steps=9, surv_mode=1)
     w.tau = np.minimum(w.tau, 0.9)
     w.phase_index = (np.arange(nz)[:, None] % nph * np.ones((1, nx))).astype(np.uint8)
     P = oracle_problem(orc, w)
