@@ -7,16 +7,30 @@
 // with M = N = 4n and the sites as the reduction dimension K.
 //
 // Persistent kernel, one CTA per SM, each reducing a contiguous slice of
-// 64-site chunks.  The threads copy beta mu and S (coalesced, cp.async) into
-// a staging slot two chunks ahead, so the loads of chunks ch + 1 and ch + 2
-// are in flight while chunk ch is converted.  Conversion splits each value into bf16 hi + lo and writes
-// four K-major, 128-byte-swizzled operand tiles (rows = table index r or k,
-// K = the chunk's 64 sites); one thread then issues three tcgen05 MMAs per
-// 16-site step (hi.hi, hi.lo, lo.hi: float32-class products) into the
-// class's TMEM accumulator.  A chunk whose
-// sites mix classes is reduced once per class present with the other
-// classes' sites zeroed in A.  At the end each CTA adds its accumulators into
-// its own float64 slot (no atomics); the slots are summed after the sweep.
+// 32-site chunks, with warp roles:
+//   warps 0-15  converters: per chunk and class present (a pass), each warp
+//               takes whole (operand, direction) rows of the staged chunk, one
+//               site per lane (conflict-free shared-memory reads), splits the
+//               four Stokes components into bf16 hi + lo, transposes the 8 x 8
+//               blocks of (site, component-part) values across each group of
+//               eight lanes with shuffles, and stores 16-byte units of the two
+//               K-major, 128-byte-swizzled operand tiles, A (rows = table
+//               index r) and B (rows = k); each row holds the chunk's 32 sites
+//               as hi (K 0..31) and then lo (K 32..63)
+//   warp  16    producer: TMA loads of the chunk's rows of beta mu (or mu) and
+//               S and of its coefficients into a ring of staging slots
+//   warp  17    MMA issuer: the hi.hi, hi.lo and lo.hi products (two K = 16
+//               steps each, float32-class) into the class's TMEM accumulator
+// The operand tiles are double-buffered, so the conversion of one pass
+// overlaps the MMAs of the previous one.  The class set of each chunk comes
+// from a mask built once per call (k_adj_chunk_masks); a chunk whose sites mix
+// classes is reduced once per class present with the other classes' sites
+// zeroed in A.  At the end each CTA stores its float32 accumulators (plain
+// stores, zeros for a class it did not see) into its own partial, and a second
+// kernel adds the partials of all CTAs, in a fixed order, into a running sum
+// kept as float32 pairs (no atomics, so the result is reproducible; float64
+// arithmetic, which the per-CTA float64 slots of an earlier form used, costs
+// about 30 us per step on this GPU).
 //
 // Needs 4n <= 128 and n_phase * 4n <= 512 TMEM columns; other shapes use the
 // CUDA-core kernel.  Every wait is bounded (about 2 s): on timeout the CTA
@@ -27,6 +41,7 @@
 #include <algorithm>
 
 #include "rtlb_internal.h"
+#include "tc.h"
 #include "tc_ptx.cuh"
 
 namespace rtlb {
@@ -34,123 +49,178 @@ namespace {
 
 using namespace tcptx;
 
-constexpr int kChunk = 64;                       // sites per K chunk: one 128-byte bf16 row
+constexpr int kChunk = 32;                       // sites per K chunk: hi and lo fill one 128-byte bf16 row
 constexpr int kRows = 128;                       // operand rows (table index; zero beyond 4n)
-constexpr int kTT = 256;                         // threads
+constexpr int kConvWarps = 16;
+constexpr int kProdWarp = 16, kMmaWarp = 17;
+constexpr int kTT = 18 * 32;                     // threads
+constexpr int kSlots = 4;                        // staging slots
 constexpr uint32_t kTile = kRows * 128;          // one operand tile, 16 KB
-constexpr uint32_t kBuf = 4 * kTile;             // A hi, A lo, B hi, B lo
+constexpr uint32_t kBuf = 2 * kTile;             // A and B
+constexpr uint32_t kRowBytes = kChunk * 16;      // one direction of one operand in a staging slot
+constexpr uint32_t kStageS = 32 * kRowBytes;     // S rows follow the (up to) 32 beta mu rows
+constexpr uint32_t kStageCoef = 2 * kStageS;     // coefficients {alpha_hi, alpha_lo, beta, e} of the 32 sites
+constexpr uint32_t kStage = kStageCoef + kChunk * 16;
+constexpr uint32_t kStageAligned = (kStage + 1023) / 1024 * 1024;
 constexpr int kErrTableTimeout = 16;
 
-// hi + lo bf16 split of eight values: two 16-byte rows of packed pairs
-__device__ __forceinline__ void split8(const float v[8], uint4 &hi, uint4 &lo)
-{
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        h[k] = pack_bf16(v[2 * k], v[2 * k + 1]);
-        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&h[k]));
-        l[k] = pack_bf16(v[2 * k] - f.x, v[2 * k + 1] - f.y);
-    }
-    hi = make_uint4(h[0], h[1], h[2], h[3]);
-    lo = make_uint4(l[0], l[1], l[2], l[3]);
-}
-
-// Stores the 16-byte group `sg` (sites 8 sg .. 8 sg + 7) of row r of a
-// K-major SW128 tile.
-__device__ __forceinline__ void put_row(uint8_t *tile, int r, int sg, uint4 v)
-{
-    *reinterpret_cast<uint4 *>(tile + r * 128 + (((uint32_t)sg ^ (uint32_t)(r & 7)) << 4)) = v;
-}
-
-// Per-thread asynchronous copies (cp.async) into shared memory; `bytes` = 0
-// writes zeros (sites past the lattice).
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src, uint32_t bytes)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src, uint32_t bytes)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// Staging slot of one chunk: beta mu (or mu, scaled here by beta) and S as
-// [direction][site] rows of 64 float4 (1 KB per direction), then the chunk's
-// emission e[64], beta[64] and classes.
-// Within each 128-byte group of eight sites the 16-byte entries are permuted
-// (entry i of group g sits at position i ^ g), so that both the coalesced
-// copies (one group of eight sites per eight threads) and the conversion
-// reads (one group per thread) spread over all banks.
-constexpr uint32_t kRowBytes = kChunk * 16;
-constexpr uint32_t kStageS = (kTT / 8) * kRowBytes;            // S rows follow the 32 beta mu rows
-constexpr uint32_t kStageData = 2 * kStageS;
-constexpr uint32_t kStageE = kStageData;                         // e[64] floats
-constexpr uint32_t kStageBeta = kStageE + kChunk * 4;             // beta[64] floats
-constexpr uint32_t kStageCls = kStageBeta + kChunk * 4;           // cls[64] bytes
-constexpr uint32_t kStage = kStageCls + kChunk;
-constexpr uint32_t kStageAligned = (kStage + 127) / 128 * 128;
-
-__device__ __forceinline__ uint32_t stage_pos(int site) { return (uint32_t)((site & ~7) | ((site ^ (site >> 3)) & 7)) * 16u; }
-
-// Writes rows 4d .. 4d + 3 (hi and lo tiles) from the staged row of direction
-// d, sites 8 sg .. 8 sg + 7; `e` (or null) is added to I, `scale` (or null)
-// multiplies every component; sites of classes other than `only` are zeroed
-// when only >= 0.
-__device__ __forceinline__ void put_rows(const uint8_t *row, const float *e, const float *scale, const uint8_t *cl,
-                                         int only, int d, int sg, uint8_t *hi_tile, uint8_t *lo_tile)
-{
-    float v[4][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        float4 x = *reinterpret_cast<const float4 *>(row + stage_pos(8 * sg + i));
-        if (e) x.x += e[8 * sg + i];
-        const float keep = ((only < 0 || cl[8 * sg + i] == only) ? 1.f : 0.f) * (scale ? scale[8 * sg + i] : 1.f);
-        v[0][i] = x.x * keep;
-        v[1][i] = x.y * keep;
-        v[2][i] = x.z * keep;
-        v[3][i] = x.w * keep;
-    }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        uint4 h, l;
-        split8(v[c], h, l);
-        put_row(hi_tile, 4 * d + c, sg, h);
-        put_row(lo_tile, 4 * d + c, sg, l);
-    }
-}
+// L2 prefetch of the beta mu and S rows of the next run of this many chunks
+// (0 = none), issued once per run.  Measured on the 1024 x 256, n = 32
+// workload (table kernel alone): 0 / 2 / 4 / 8 chunks gave 130.2 / 131.1 /
+// 132.0 / 133.4 us, so none by default.
+#ifndef RTLB_TABLE_PREFETCH_CHUNKS
+#define RTLB_TABLE_PREFETCH_CHUNKS 0
+#endif
 
 __device__ int g_table_tc_err;
 
+__global__ void k_adj_chunk_masks(const uint8_t *__restrict__ cls, int nsites, uint32_t *__restrict__ masks)
+{
+    const int nchunks = (nsites + kChunk - 1) / kChunk;
+    for (int ch = blockIdx.x * blockDim.x + threadIdx.x; ch < nchunks; ch += gridDim.x * blockDim.x) {
+        uint32_t m = 0u;
+        const int end = min(nsites, (ch + 1) * kChunk);
+        for (int s = ch * kChunk; s < end; ++s) m |= 1u << cls[s];
+        masks[ch] = m;
+    }
+}
+
+// Error-free float32 addition (TwoSum): s + err == a + b exactly.
+__device__ __forceinline__ float two_sum(float a, float b, float &err)
+{
+    const float s = a + b;
+    const float bp = s - a;
+    err = (a - (s - bp)) + (b - bp);
+    return s;
+}
+
+// acc (hi at [0, len), lo at [len, 2 len)) += sum over the partials p of
+// part[p][j].  Float64 arithmetic is slow on this GPU, so the sums are kept
+// as float32 pairs (hi + lo, TwoSum on every addition: about twice float32's
+// precision).  A block takes 64 consecutive j (16 float4 columns); its 16
+// slices of threads each sum every 16th partial (independent float4 loads)
+// and the slices are combined in a fixed order, so the result does not
+// depend on timing.  len is a multiple of 64 (n_phase * 4n * 4n, 4n >= 32).
+constexpr int kFoldCols = 16, kFoldSlices = 16;
+__global__ void __launch_bounds__(kFoldCols * kFoldSlices)
+    k_adj_fold_partials(const float *__restrict__ part, int nparts, int len, float *__restrict__ acc)
+{
+    __shared__ float hi_s[kFoldSlices][kFoldCols * 4], lo_s[kFoldSlices][kFoldCols * 4];
+    const int col = threadIdx.x % kFoldCols, slice = threadIdx.x / kFoldCols;
+    for (int j0 = blockIdx.x * kFoldCols * 4; j0 < len; j0 += gridDim.x * kFoldCols * 4) {
+        const int j = j0 + 4 * col;
+        float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int p = slice; p < nparts; p += kFoldSlices) {
+            const float4 v = *reinterpret_cast<const float4 *>(part + (size_t)p * len + j);
+            const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float e;
+                h[k] = two_sum(h[k], x[k], e);
+                l[k] += e;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            hi_s[slice][4 * col + k] = h[k];
+            lo_s[slice][4 * col + k] = l[k];
+        }
+        __syncthreads();
+        if (threadIdx.x < kFoldCols * 4) {
+            const int jj = j0 + threadIdx.x;
+            float H = acc[jj], L = acc[len + jj];
+            for (int sl = 0; sl < kFoldSlices; ++sl) {
+                float e;
+                H = two_sum(H, hi_s[sl][threadIdx.x], e);
+                L += e + lo_s[sl][threadIdx.x];
+            }
+            acc[jj] = H;
+            acc[len + jj] = L;
+        }
+        __syncthreads();
+    }
+}
+
+// out[j] += hi[j] + lo[j] in float64 (once per call).
+__global__ void k_adj_table_finish(const float *__restrict__ acc, int len, double *__restrict__ out)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < len; j += gridDim.x * blockDim.x)
+        out[j] += (double)acc[j] + (double)acc[len + j];
+}
+
+// One exchange step of the 8 x 8 transpose across the eight lanes of a group:
+// lane bit `m` decides which word of the pair (lo_w, hi_w) this lane hands to
+// its partner (lane ^ m) and which it replaces.
+__device__ __forceinline__ void xpose_words(uint32_t &lo_w, uint32_t &hi_w, int m, bool up)
+{
+    const uint32_t send = up ? lo_w : hi_w;
+    const uint32_t got = __shfl_xor_sync(0xffffffffu, send, m);
+    if (up) lo_w = got;
+    else hi_w = got;
+}
+
+// Transposes the 8 x 8 matrix of 16-bit values held by the eight lanes
+// j = 0..7 of each group (lane j: v_j[0..7], packed two per word, w[i] =
+// v[2i] | v[2i + 1] << 16) so that lane k ends with (v_0[k], ..., v_7[k]).
+__device__ __forceinline__ void xpose8x8(uint32_t w[4], int lane)
+{
+    const int j = lane & 7;
+    // elements 4..7 <-> partner's 0..3 (lane bit 2)
+    xpose_words(w[0], w[2], 4, (j & 4) != 0);
+    xpose_words(w[1], w[3], 4, (j & 4) != 0);
+    // elements (2,3) <-> partner's (0,1) within each half (lane bit 1)
+    xpose_words(w[0], w[1], 2, (j & 2) != 0);
+    xpose_words(w[2], w[3], 2, (j & 2) != 0);
+    // odd <-> even element within each word (lane bit 0): the lane with bit 0
+    // clear keeps its low half and takes the partner's low half into its high
+    // half; the other keeps its high half and takes the partner's high half
+    // into its low half (byte selectors of __byte_perm)
+    const bool up = (j & 1) != 0;
+    const uint32_t sel_send = up ? 0x0010u : 0x0032u, sel_keep = up ? 0x3254u : 0x5410u;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t got = __shfl_xor_sync(0xffffffffu, __byte_perm(w[i], 0u, sel_send), 1);
+        w[i] = __byte_perm(w[i], got, sel_keep);
+    }
+}
+
 __global__ void __launch_bounds__(kTT, 1)
-    k_adj_table_tc(const float4 *__restrict__ beta_mu, const float4 *__restrict__ S, const float4 *__restrict__ coef,
-                   const uint8_t *__restrict__ cls, double *__restrict__ slots, int nsites, int n, int n_phase,
-                   uint32_t tcols, int beta_scale)
+    k_adj_table_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmS,
+                   const __grid_constant__ CUtensorMap tmC, const uint8_t *__restrict__ cls,
+                   const uint32_t *__restrict__ chunk_mask, float *__restrict__ part, int nsites, int n,
+                   int n_phase, uint32_t tcols, int beta_scale)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    uint8_t *Ahi = smem, *Alo = smem + kTile, *Bhi = smem + 2 * kTile, *Blo = smem + 3 * kTile;   // one operand buffer
-    uint8_t *stage = smem + kBuf;                                                              // [2] staging slots
-    uint64_t *done = reinterpret_cast<uint64_t *>(stage + 2 * kStageAligned);                  // MMAs completed
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    uint8_t *ops = smem;                                                 // [2] x (A, B) operand tiles
+    uint8_t *stage = smem + 2 * kBuf;                                    // [kSlots] staging slots
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stage + kSlots * kStageAligned);
+    uint64_t *st_full = bars;                  // [kSlots] TMA bytes landed
+    uint64_t *st_empty = st_full + kSlots;     // [kSlots] every converter warp is done with the slot
+    uint64_t *op_full = st_empty + kSlots;     // [2] every converter warp wrote its rows of the buffer
+    uint64_t *done = op_full + 2;              // [2] the MMAs reading the buffer completed
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N4 = 4 * n;
+    int *err = &g_table_tc_err;
 
     // operand tiles start at zero: rows 4n .. 127 of A are never written
-    for (uint32_t o = (uint32_t)tid * 16u; o < kBuf; o += kTT * 16u)
+    for (uint32_t o = (uint32_t)tid * 16u; o < 2 * kBuf; o += kTT * 16u)
         *reinterpret_cast<uint4 *>(smem + o) = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
-        mbar_init(smem_u32(done), 1);
+        for (int k = 0; k < kSlots; ++k) {
+            mbar_init(smem_u32(&st_full[k]), 1);
+            mbar_init(smem_u32(&st_empty[k]), kConvWarps);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&op_full[b]), kConvWarps);
+            mbar_init(smem_u32(&done[b]), 1);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(smem_u32(tmem_slot), tcols);
+    if (warp == kMmaWarp) tmem_alloc(smem_u32(tmem_slot), tcols);
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
@@ -160,136 +230,190 @@ __global__ void __launch_bounds__(kTT, 1)
     const int nchunks = (nsites + kChunk - 1) / kChunk;
     const int c_begin = (int)((long long)nchunks * blockIdx.x / gridDim.x);
     const int c_end = (int)((long long)nchunks * (blockIdx.x + 1) / gridDim.x);
-    const int d = tid >> 3, sg = tid & 7;          // conversion item: direction d, sites 8 sg .. 8 sg + 7
-    const bool loader = d < n;
-    const uint32_t idesc = idesc_bf16(kRows, N4);
-
-    // copies of chunk ch into staging slot `slot` (one commit group per call)
-    auto issue = [&](int ch, int slot) {
-        if (ch < c_end) {
-            const uint32_t base = smem_u32(stage + slot * kStageAligned);
-            if (loader) {   // group j of direction d: site 8 j + sg by thread (d, sg), 4 full lines per warp
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int site = ch * kChunk + 8 * j + sg;
-                    const bool in = site < nsites;
-                    const size_t off = in ? (size_t)d * nsites + site : 0;
-                    const uint32_t dst = base + d * kRowBytes + stage_pos(8 * j + sg);
-                    cp_async16(dst, beta_mu + off, in ? 16u : 0u);
-                    cp_async16(dst + kStageS, S + off, in ? 16u : 0u);
-                }
-            }
-            const int site0 = ch * kChunk + 8 * sg;
-            if (d == 0) {   // emission (coef.w) and classes of sites 8 sg .. 8 sg + 7
-                const float *ew = reinterpret_cast<const float *>(coef) + 3;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int site = site0 + i;
-                    const bool in = site < nsites;
-                    cp_async4(base + kStageE + (8 * sg + i) * 4, ew + 4 * (size_t)(in ? site : 0), in ? 4u : 0u);
-                    if (beta_scale)
-                        cp_async4(base + kStageBeta + (8 * sg + i) * 4, ew - 1 + 4 * (size_t)(in ? site : 0), in ? 4u : 0u);
-                }
-                const int left = nsites - site0;   // class bytes present in this group (rest zero-filled)
-                const uint32_t nb = left <= 0 ? 0u : (left >= 8 ? 8u : (uint32_t)left);
-                cp_async8(base + kStageCls + 8 * sg, cls + (nb ? site0 : 0), nb);
-            }
-        }
-        cp_async_commit();
-    };
-
-    issue(c_begin, 0);
-    issue(c_begin + 1, 1);
-    uint32_t cnt = 0;                              // commits issued (same in every thread)
-    unsigned seen = 0u;                            // classes with an accumulator (same in every thread)
+    const uint32_t stage_tx = 2u * (uint32_t)n * kRowBytes + kChunk * 16u;
+    unsigned seen = 0u;                            // classes with an accumulator (MMA thread and, at the end, everyone)
     bool ok = true;
-    auto ops_free = [&]() -> bool {                // the last pass's MMAs completed; vote = barrier
-        const bool w = cnt == 0u || mbar_wait(smem_u32(done), (cnt - 1u) & 1u, abort_flag, &g_table_tc_err,
-                                              kErrTableTimeout);
-        return __syncthreads_and(w) != 0;
-    };
 
-    for (int ch = c_begin, it = 0; ch < c_end && ok; ++ch, ++it) {
-        const int slot = it & 1;
-        uint8_t *st = stage + slot * kStageAligned;
-        const uint8_t *mine = st + d * kRowBytes;
-        const float *e = reinterpret_cast<const float *>(st + kStageE);
-        const float *bt = beta_scale ? reinterpret_cast<const float *>(st + kStageBeta) : nullptr;
-        const uint8_t *cl = st + kStageCls;
-        const int site0 = ch * kChunk;
-        cp_async_wait1();                          // own copies of this chunk (the next chunk's may be pending)
-        unsigned mask = 0u;
-        for (int c = 0; c < n_phase; ++c)          // the votes also publish every thread's copies to the block
-            if (__syncthreads_or(tid < kChunk && site0 + tid < nsites && cl[tid] == c)) mask |= 1u << c;
-        const bool single = (mask & (mask - 1u)) == 0u;
-        bool first = true;
-        for (int c = 0; c < n_phase; ++c) {
-            if (!(mask & (1u << c))) continue;
-            if (!(ok = ops_free())) break;
-            if (loader) {
-                if (first) put_rows(mine + kStageS, e, nullptr, cl, -1, d, sg, Bhi, Blo);   // S~ = S + e
-                put_rows(mine, nullptr, bt, cl, single ? -1 : c, d, sg, Ahi, Alo);        // beta mu (this class)
-            }
-            fence_proxy_async();
-            tc_fence_before();
-            __syncthreads();
-            if (tid == 0) {
-                tc_fence_after();
-                const uint32_t acc = tmem + (uint32_t)(c * N4);
-                uint32_t accum = (seen >> c) & 1u;
-#pragma unroll
-                for (int kk = 0; kk < kChunk / 16; ++kk) {
-                    const uint64_t ah = sw128_desc(smem_u32(Ahi + kk * 32)), al = sw128_desc(smem_u32(Alo + kk * 32));
-                    const uint64_t bh = sw128_desc(smem_u32(Bhi + kk * 32)), bl = sw128_desc(smem_u32(Blo + kk * 32));
-                    mma_bf16(acc, ah, bh, idesc, accum);
-                    mma_bf16(acc, ah, bl, idesc, 1u);
-                    mma_bf16(acc, al, bh, idesc, 1u);
-                    accum = 1u;
+    if (warp == kProdWarp) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            int it = 0;
+            for (int ch = c_begin; ch < c_end && ok; ++ch, ++it) {
+                const int slot = it % kSlots;
+                if (it >= kSlots)
+                    ok = mbar_wait(smem_u32(&st_empty[slot]), ((it / kSlots) - 1) & 1, abort_flag, err, kErrTableTimeout);
+                if (!ok) break;
+                const uint32_t fb = smem_u32(&st_full[slot]);
+                const uint32_t base = smem_u32(stage + slot * kStageAligned);
+                mbar_expect_tx(fb, stage_tx);
+                tma_load_2d(base, &tmA, fb, 4 * ch * kChunk, 0);
+                tma_load_2d(base + kStageS, &tmS, fb, 4 * ch * kChunk, 0);
+                tma_load_2d(base + kStageCoef, &tmC, fb, 0, ch * kChunk);
+                if (RTLB_TABLE_PREFETCH_CHUNKS > 0 && it % RTLB_TABLE_PREFETCH_CHUNKS == 0) {
+                    // the next run of chunks into L2 together: each direction's
+                    // rows of beta mu and S then come from DRAM as runs of
+                    // RTLB_TABLE_PREFETCH_CHUNKS x 512 bytes
+                    for (int k = RTLB_TABLE_PREFETCH_CHUNKS; k < 2 * RTLB_TABLE_PREFETCH_CHUNKS; ++k)
+                        if (ch + k < c_end) {
+                            tma_prefetch_2d(&tmA, 4 * (ch + k) * kChunk, 0);
+                            tma_prefetch_2d(&tmS, 4 * (ch + k) * kChunk, 0);
+                        }
                 }
-                mma_commit(smem_u32(done));
             }
-            ++cnt;
-            seen |= 1u << c;
-            first = false;
+            // every load issued has landed before the CTA leaves (bounded)
+            for (int k = 0; k < kSlots && k < it; ++k) {
+                const int i2 = it - 1 - k, slot = i2 % kSlots;
+                const unsigned long long t0 = global_ns();
+                while (!mbar_try(smem_u32(&st_full[slot]), (i2 / kSlots) & 1) && global_ns() - t0 < kTimeoutNs) {
+                }
+            }
         }
-        // every thread has read its staged values and e[] / cl[] of this slot
-        __syncthreads();
-        issue(ch + 2, slot);
-    }
-    cp_async_wait0();
-    // every MMA issued has completed (bounded) before TMEM is read and freed
-    bool drained = true;
-    if (cnt > 0u) {
-        const unsigned long long t0 = global_ns();
-        while (!mbar_try(smem_u32(done), (cnt - 1u) & 1u) && global_ns() - t0 < kTimeoutNs) {
+    } else if (warp == kMmaWarp) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(kRows, N4);
+            uint32_t pass = 0;
+            unsigned mask_next = c_begin < c_end ? chunk_mask[c_begin] : 0u;
+            for (int ch = c_begin; ch < c_end && ok; ++ch) {
+                const unsigned mask = mask_next;
+                if (ch + 1 < c_end) mask_next = chunk_mask[ch + 1];
+                for (int c = 0; c < n_phase && ok; ++c) {
+                    if (!(mask & (1u << c))) continue;
+                    const int b = (int)(pass & 1u);
+                    ok = mbar_wait(smem_u32(&op_full[b]), (pass >> 1) & 1u, abort_flag, err, kErrTableTimeout);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t acc = tmem + (uint32_t)(c * N4);
+                    uint32_t accum = (seen >> c) & 1u;
+                    const uint64_t a0 = sw128_desc(smem_u32(ops + b * kBuf)), b0 = sw128_desc(smem_u32(ops + b * kBuf + kTile));
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        // +32 bytes per K = 16 step; the lo half of a row starts 64 bytes in
+                        const uint64_t ah = a0 + 2 * kk, al = a0 + 4 + 2 * kk, bh = b0 + 2 * kk, bl = b0 + 4 + 2 * kk;
+                        mma_bf16(acc, ah, bh, idesc, accum);
+                        mma_bf16(acc, ah, bl, idesc, 1u);
+                        mma_bf16(acc, al, bh, idesc, 1u);
+                        accum = 1u;
+                    }
+                    mma_commit(smem_u32(&done[b]));
+                    seen |= 1u << c;
+                    ++pass;
+                }
+            }
+            // every MMA issued has completed before TMEM is read and freed
+            if (pass > 0u) {
+                const int b = (int)((pass - 1u) & 1u);
+                const uint32_t par = ((pass - 1u) >> 1) & 1u;
+                const unsigned long long t0 = global_ns();
+                while (!mbar_try(smem_u32(&done[b]), par) && global_ns() - t0 < kTimeoutNs) {
+                }
+                if (!mbar_try(smem_u32(&done[b]), par)) ok = false;
+            }
         }
-        drained = mbar_try(smem_u32(done), (cnt - 1u) & 1u);
+    } else {
+        // ----------------------------------------------------------- converter
+        uint32_t pass = 0;
+        const int tasks = 2 * n;                   // (operand, direction) rows per pass
+        const int g = lane >> 3;                   // this lane's group of eight sites
+        int it = 0;
+        unsigned mask_next = c_begin < c_end ? chunk_mask[c_begin] : 0u;
+        for (int ch = c_begin; ch < c_end && ok; ++ch, ++it) {
+            const int slot = it % kSlots;
+            const unsigned mask = mask_next;
+            if (ch + 1 < c_end) mask_next = chunk_mask[ch + 1];
+            const bool single = (mask & (mask - 1u)) == 0u;
+            const int site = ch * kChunk + lane;
+            const int my_cls = (!single && site < nsites) ? (int)__ldg(cls + site) : -1;
+            ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&st_full[slot]), (it / kSlots) & 1, abort_flag, err,
+                                                   kErrTableTimeout));
+            if (!ok) break;
+            const uint8_t *st = stage + slot * kStageAligned;
+            const float4 cf = *reinterpret_cast<const float4 *>(st + kStageCoef + lane * 16);   // {., ., beta, e}
+            for (int c = 0; c < n_phase && ok; ++c) {
+                if (!(mask & (1u << c))) continue;
+                const int b = (int)(pass & 1u);
+                // the MMAs of the pass two before this one (same buffer) completed
+                if (pass >= 2u)
+                    ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&done[b]), ((pass >> 1) & 1u) ^ 1u, abort_flag,
+                                                           err, kErrTableTimeout));
+                if (!ok) break;
+                uint8_t *A = ops + b * kBuf;
+                const float keep = (single || my_cls == c) ? (beta_scale ? cf.z : 1.f) : 0.f;
+                // up to four (operand, direction) rows per warp (2n <= 64 rows,
+                // 16 warps), unrolled so their shuffle chains interleave
+#pragma unroll
+                for (int jt = 0; jt < 4; ++jt) {
+                    const int t = warp + kConvWarps * jt;
+                    if (t >= tasks) break;
+                    const int o = t >= n ? 1 : 0, d = t - o * n;
+                    float4 x = *reinterpret_cast<const float4 *>(st + o * kStageS + d * kRowBytes + lane * 16);
+                    if (o == 0) {
+                        x.x *= keep;
+                        x.y *= keep;
+                        x.z *= keep;
+                        x.w *= keep;
+                    } else {
+                        x.x += cf.w;                                   // S~: emission on I
+                    }
+                    // elements 0..3: hi of components 0..3, elements 4..7: lo
+                    uint32_t w[4];
+                    w[0] = pack_bf16(x.x, x.y);
+                    w[1] = pack_bf16(x.z, x.w);
+                    w[2] = pack_bf16(x.x - __uint_as_float(w[0] << 16), x.y - __uint_as_float(w[0] & 0xFFFF0000u));
+                    w[3] = pack_bf16(x.z - __uint_as_float(w[1] << 16), x.w - __uint_as_float(w[1] & 0xFFFF0000u));
+                    // lane k of the group now gets element k (component k % 4,
+                    // hi for k < 4, lo otherwise) of sites 8 g .. 8 g + 7
+                    xpose8x8(w, lane);
+                    const int k = lane & 7, comp = k & 3, part = k >> 2;
+                    const int r = 4 * d + comp;
+                    const int u = (part ? 4 + g : g) ^ (r & 7);
+                    *reinterpret_cast<uint4 *>(A + (uint32_t)o * kTile + (uint32_t)r * 128u + ((uint32_t)u << 4)) =
+                        make_uint4(w[0], w[1], w[2], w[3]);
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&op_full[b]));
+                seen |= 1u << c;
+                ++pass;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&st_empty[slot]));
+        }
     }
-    ok = __syncthreads_and(ok && drained) != 0;
+
+    // the MMA thread drained its MMAs; everyone agrees on the outcome
+    const bool all_ok = __syncthreads_and(ok) != 0;
     tc_fence_after();
-    if (ok) {
-        // warps 0-3 and 4-7 read the same lanes (rows r), each half of the columns
-        const int q = warp & 3, half = warp >> 2;
+    if (all_ok && warp < kConvWarps) {
+        // warps w, w + 4, w + 8, w + 12 read the same lanes (rows r), each a
+        // quarter of the columns (16 at least)
+        const int q = warp & 3, qp = warp >> 2;
         const int r = q * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        const int cw = N4 / 4 >= 16 ? N4 / 4 : 16;        // columns per quarter
         for (int c = 0; c < n_phase; ++c) {
-            if (!(seen & (1u << c))) continue;
-            double *slot = slots + ((size_t)blockIdx.x * n_phase + c) * (size_t)N4 * N4;
-            for (int col = half * (N4 / 2); col < (half + 1) * (N4 / 2); col += 16) {
+            float *dst = part + ((size_t)blockIdx.x * n_phase + c) * (size_t)N4 * N4;
+            for (int col = qp * cw; col < (qp + 1) * cw && col < N4; col += 16) {
                 float v[16];
-                tmem_ld16(tmem + lane_base + (uint32_t)(c * N4 + col), v);
-                if (r < N4) {
+                if (seen & (1u << c)) {
+                    tmem_ld16(tmem + lane_base + (uint32_t)(c * N4 + col), v);
+                } else {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) slot[(size_t)r * N4 + col + j] += (double)v[j];
+                    for (int j = 0; j < 16; ++j) v[j] = 0.f;
+                }
+                if (r < N4) {
+                    float4 *o4 = reinterpret_cast<float4 *>(dst + (size_t)r * N4 + col);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) o4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                 }
             }
         }
-    } else if (tid == 0) {
+    } else if (!all_ok && tid == 0) {
         atomicOr(&g_table_tc_err, kErrTableTimeout);
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, tcols);
+    if (warp == kMmaWarp) tmem_dealloc(tmem, tcols);
 }
 
 }  // namespace
@@ -300,12 +424,27 @@ bool adjoint_table_tc_supported(int n, int n_phase)
     return (N4 == 32 || N4 == 64 || N4 == 128) && n_phase * N4 <= 512;
 }
 
+cudaError_t launch_adjoint_chunk_masks(const uint8_t *cls, int nsites, uint32_t *masks, cudaStream_t s)
+{
+    const int nchunks = (nsites + kChunk - 1) / kChunk;
+    k_adj_chunk_masks<<<std::min((nchunks + 255) / 256, 148 * 8), 256, 0, s>>>(cls, nsites, masks);
+    return cudaGetLastError();
+}
+
+size_t adjoint_chunk_masks_bytes(int nsites) { return (size_t)((nsites + kChunk - 1) / kChunk) * sizeof(uint32_t); }
+
 cudaError_t launch_adjoint_table_tc(const AdjointParams &p, double *slots, int nslots, cudaStream_t s)
 {
+    if (!p.chunk_mask || !p.table_part || !p.table_acc || p.n > 32) return cudaErrorInvalidValue;
     const int N4 = 4 * p.n, nsites = p.nx * p.nz;
     uint32_t tcols = 32;
     while (tcols < (uint32_t)(p.n_phase * N4)) tcols <<= 1;
-    const size_t smem = (size_t)kBuf + 2 * (size_t)kStageAligned + 64 + 1024;
+    CUtensorMap tmA, tmS, tmC;
+    if (!tc_encode_f32_2d(&tmA, p.beta_mu, (uint64_t)nsites * 4, (uint64_t)p.n, kChunk * 4, (uint32_t)p.n) ||
+        !tc_encode_f32_2d(&tmS, p.S, (uint64_t)nsites * 4, (uint64_t)p.n, kChunk * 4, (uint32_t)p.n) ||
+        !tc_encode_f32_2d(&tmC, reinterpret_cast<const float *>(p.coef), 4, (uint64_t)nsites, 4, kChunk))
+        return cudaErrorInvalidValue;
+    const size_t smem = 2 * (size_t)kBuf + kSlots * (size_t)kStageAligned + 128 + 1024;
     static bool attr = false;
     if (!attr) {
         const cudaError_t e = cudaFuncSetAttribute(k_adj_table_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -313,9 +452,20 @@ cudaError_t launch_adjoint_table_tc(const AdjointParams &p, double *slots, int n
         attr = true;
     }
     const int grid = std::min(nslots, (nsites + kChunk - 1) / kChunk);
-    k_adj_table_tc<<<grid, kTT, smem, s>>>(reinterpret_cast<const float4 *>(p.beta_mu),
-                                          reinterpret_cast<const float4 *>(p.S), p.coef, p.cls, slots, nsites, p.n,
-                                          p.n_phase, tcols, p.beta_scale);
+    k_adj_table_tc<<<grid, kTT, smem, s>>>(tmA, tmS, tmC, p.cls, p.chunk_mask, p.table_part, nsites, p.n, p.n_phase,
+                                          tcols, p.beta_scale);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the partials of this launch into the running float32-pair sum
+    const int len = p.n_phase * N4 * N4;
+    k_adj_fold_partials<<<std::min(len / (kFoldCols * 4), 148 * 8), kFoldCols * kFoldSlices, 0, s>>>(p.table_part, grid,
+                                                                                                      len, p.table_acc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_table_tc_finish(const float *acc, int len, double *slot0, cudaStream_t s)
+{
+    k_adj_table_finish<<<std::min((len + 255) / 256, 148 * 4), 256, 0, s>>>(acc, len, slot0);
     return cudaGetLastError();
 }
 

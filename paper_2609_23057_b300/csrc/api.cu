@@ -670,6 +670,9 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
         {&w.gtd, stage_t ? ns * sizeof(float) : 0},
         {&w.gad, stage_a ? ns * sizeof(float) : 0},
         {&w.gS, stage_S ? bytes : 0},
+        {&w.cmask, adjoint_chunk_masks_bytes((int)ns)},
+        {&w.tpart, adjoint_table_tc_supported(c->n, c->n_phase) ? (size_t)nslots * glen * sizeof(float) : 0},
+        {&w.tacc, adjoint_table_tc_supported(c->n, c->n_phase) ? 2 * glen * sizeof(float) : 0},
     };
     auto grow = [&]() -> cudaError_t {
         for (const auto &b : need) {
@@ -744,6 +747,10 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
     AK(cudaMemsetAsync(ga, 0, 2 * ns * sizeof(double), s), "g_alpha init");
     AK(cudaMemsetAsync(gb, 0, 2 * ns * sizeof(double), s), "g_beta init");
     AK(cudaMemsetAsync(slots, 0, (size_t)nslots * glen * sizeof(double), s), "slots init");
+    const bool table_tc = adjoint_table_tc_supported(c->n, c->n_phase);
+    if (table_tc) AK(cudaMemsetAsync(w.tacc.p, 0, 2 * glen * sizeof(float), s), "table sum init");
+    const uint32_t *cmask = w.cmask.as<uint32_t>();
+    AK(launch_adjoint_chunk_masks(c->d_cls, (int)ns, w.cmask.as<uint32_t>(), s), "chunk class masks");
     int lc = 0;
     if (nu_form) {
         // transposed-stream form: lam[lc] holds nu^t = T^T lambda^{t+1}; each
@@ -802,6 +809,9 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
                 ap.dirT = a.dirT.as<int>();
                 ap.bcbitsT = bcbitsT;
                 ap.push = push ? 1 : 0;
+                ap.chunk_mask = cmask;
+                ap.table_part = w.tpart.as<float>();
+                ap.table_acc = w.tacc.as<float>();
                 AK(launch_adjoint_step_nu_mixed(ap, a.n_mixed, s), "adjoint step (mixed tiles)");
                 AK(launch_adjoint_table(ap, slots, s), "adjoint table gradient");
                 lc ^= 1;
@@ -841,6 +851,9 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
             for (int k = 0; k < 4; ++k) ap.bc[k] = c->bc[k];
             ap.g_alpha = ga;
             ap.g_beta = gb;
+            ap.chunk_mask = cmask;
+            ap.table_part = w.tpart.as<float>();
+            ap.table_acc = w.tacc.as<float>();
             AK(launch_adjoint_step(ap, slots, s), "adjoint step");
             lc ^= 1;
         }
@@ -865,6 +878,7 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
             AK(cudaMemcpyAsync(grad_albedo, gad, ns * sizeof(float), cudaMemcpyDeviceToHost, s), "grad_albedo");
     }
     if (grad_Z) {
+        if (table_tc) AK(launch_adjoint_table_tc_finish(w.tacc.as<float>(), (int)glen, slots, s), "table gradient sum");
         AK(launch_adjoint_fold(slots, nslots, glen, G, s), "table gradient");
         AK(cudaMemcpyAsync(grad_Z, G, glen * sizeof(double), cudaMemcpyDeviceToHost, s), "grad_Z");
     }

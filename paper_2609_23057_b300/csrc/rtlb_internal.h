@@ -62,6 +62,14 @@ struct AdjointParams {
     int bcbitsT = 0;
     int push = 1;
     int beta_scale = 0;
+    // class mask of each 32-site chunk (bit c: a site of class c), for the
+    // tensor-core table gradient (launch_adjoint_chunk_masks)
+    const uint32_t *chunk_mask = nullptr;
+    // float32 partial of each CTA of the tensor-core table gradient
+    // ([adjoint_table_slots()][n_phase][4n][4n]) and the running sum over the
+    // steps as float32 pairs (hi [n_phase][4n][4n], then lo)
+    float *table_part = nullptr;
+    float *table_acc = nullptr;
 };
 
 bool adjoint_supported(int n);
@@ -81,6 +89,10 @@ cudaError_t launch_adjoint_seed_nu(float *nu, const float *dL_dout, const int *d
 // tensor-core table gradient (adj_table_tc.cu): 4n <= 128, n_phase * 4n <= 512
 bool adjoint_table_tc_supported(int n, int n_phase);
 cudaError_t launch_adjoint_table_tc(const AdjointParams &p, double *slots, int nslots, cudaStream_t s);
+cudaError_t launch_adjoint_chunk_masks(const uint8_t *cls, int nsites, uint32_t *masks, cudaStream_t s);
+// slot0[j] += hi[j] + lo[j] (float64) from the running sum of the tensor-core table gradient
+cudaError_t launch_adjoint_table_tc_finish(const float *acc, int len, double *slot0, cudaStream_t s);
+size_t adjoint_chunk_masks_bytes(int nsites);
 int adjoint_table_tc_take_error();
 
 // ---- kernels (launchers return the launch error) ----
@@ -122,14 +134,14 @@ struct DevBuf {
 // rtlb_adjoint's device workspace (checkpoints, scratch states, adjoint
 // states, accumulators and staging), kept in the context between calls.
 struct AdjWork {
-    DevBuf ck, seg, lam, bm, ga, gb, slots, G, tapT, dl, gtd, gad, gS;
+    DevBuf ck, seg, lam, bm, ga, gb, slots, G, tapT, dl, gtd, gad, gS, cmask, tpart, tacc;
     void release()
     {
-        for (DevBuf *b : {&ck, &seg, &lam, &bm, &ga, &gb, &slots, &G, &tapT, &dl, &gtd, &gad, &gS}) b->release();
+        for (DevBuf *b : {&ck, &seg, &lam, &bm, &ga, &gb, &slots, &G, &tapT, &dl, &gtd, &gad, &gS, &cmask, &tpart, &tacc}) b->release();
     }
 };
 
-// Tensor-core reverse step state (4n = 128), built from the medium on the
+// Tensor-core reverse step state (4n in {32, 64, 128}), built from the medium on the
 // first rtlb_adjoint after each rtlb_set_medium: Z^T as bf16 hi and lo with
 // their tensor maps, single-class and mixed 128-site tile lists, and the
 // negated streaming offsets.

@@ -1161,6 +1161,20 @@ rtlb_status tc_check_error(rtlb_ctx *c, cudaStream_t s)
 
 bool tc_encode_state_map(CUtensorMap *m, const float *S, size_t nsites, int n) { return encode_state_map(m, S, nsites, n); }
 
+bool tc_encode_f32_2d(CUtensorMap *m, const float *base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                      uint32_t box_outer)
+{
+    auto fn = encode_fn();
+    if (!fn || inner % 4 != 0) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    cuuint64_t strides[1] = {(cuuint64_t)inner * 4};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool tc_encode_table_map(CUtensorMap *m, const __nv_bfloat16 *Z, int N4, int KP, int n_phase, int box_rows)
 {
     return encode_z_map(m, Z, N4, KP, n_phase, box_rows);

@@ -53,6 +53,10 @@ int adjoint_tc_stages(int n);   // 0 where the form does not exist (n not in {8,
 cudaError_t launch_adjoint_step_tc(const CUtensorMap &tmNu, const CUtensorMap &tmZhi, const CUtensorMap &tmZlo,
                                    const AdjTcLaunch &a, cudaStream_t s);
 int adjoint_step_tc_take_error();
+// float32 2D tensor map (rows of `inner` floats, `outer` rows, row stride
+// inner * 4 bytes), boxes of box_inner x box_outer, no swizzle, zero fill
+bool tc_encode_f32_2d(CUtensorMap *m, const float *base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                      uint32_t box_outer);
 // bf16 table [n_phase][N4][KP] tensor map with boxes of 64 columns x box_rows rows
 bool tc_encode_table_map(CUtensorMap *m, const __nv_bfloat16 *Z, int N4, int KP, int n_phase, int box_rows);
 
