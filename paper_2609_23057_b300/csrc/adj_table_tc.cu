@@ -11,12 +11,12 @@
 //   warps 0-15  converters: per chunk and class present (a pass), each warp
 //               takes whole (operand, direction) rows of the staged chunk, one
 //               site per lane (conflict-free shared-memory reads), splits the
-//               four Stokes components into bf16 hi + lo, transposes the 8 x 8
-//               blocks of (site, component-part) values across each group of
-//               eight lanes with shuffles, and stores 16-byte units of the two
-//               K-major, 128-byte-swizzled operand tiles, A (rows = table
-//               index r) and B (rows = k); each row holds the chunk's 32 sites
-//               as hi (K 0..31) and then lo (K 32..63)
+//               four Stokes components into bf16 hi + lo and stores them as
+//               8-byte pieces of two MN-major, 128-byte-swizzled operand
+//               tiles, A (M = table index r) and B (N = k): a site is a K
+//               index, its four components four consecutive M (N) values, so
+//               no transpose is needed.  K holds the chunk's 32 sites as hi
+//               (K 0..31) and then lo (K 32..63).
 //   warp  16    producer: TMA loads of the chunk's rows of beta mu (or mu) and
 //               S and of its coefficients into a ring of staging slots
 //   warp  17    MMA issuer: the hi.hi, hi.lo and lo.hi products (two K = 16
@@ -148,40 +148,22 @@ __global__ void k_adj_table_finish(const float *__restrict__ acc, int len, doubl
         out[j] += (double)acc[j] + (double)acc[len + j];
 }
 
-// One exchange step of the 8 x 8 transpose across the eight lanes of a group:
-// lane bit `m` decides which word of the pair (lo_w, hi_w) this lane hands to
-// its partner (lane ^ m) and which it replaces.
-__device__ __forceinline__ void xpose_words(uint32_t &lo_w, uint32_t &hi_w, int m, bool up)
+// MN-major, 128-byte-swizzled operand tile of 128 MN values x 64 K values
+// (bf16): K groups of 8 (2048 bytes each) hold two atoms of 64 MN values (8 K
+// rows of 128 bytes, the 16-byte chunks of row k XOR k % 8).  Byte offset of
+// the four MN values 4 d .. 4 d + 3 at K index k.
+__device__ __forceinline__ uint32_t mn_off4(int d, int k)
 {
-    const uint32_t send = up ? lo_w : hi_w;
-    const uint32_t got = __shfl_xor_sync(0xffffffffu, send, m);
-    if (up) lo_w = got;
-    else hi_w = got;
+    return (uint32_t)(k >> 3) * 2048u + (uint32_t)(d >> 4) * 1024u + (uint32_t)(k & 7) * 128u +
+           ((uint32_t)(((d & 15) >> 1) ^ (k & 7)) << 4) + ((uint32_t)(d & 1) << 3);
 }
 
-// Transposes the 8 x 8 matrix of 16-bit values held by the eight lanes
-// j = 0..7 of each group (lane j: v_j[0..7], packed two per word, w[i] =
-// v[2i] | v[2i + 1] << 16) so that lane k ends with (v_0[k], ..., v_7[k]).
-__device__ __forceinline__ void xpose8x8(uint32_t w[4], int lane)
+// Descriptor of such a tile: leading byte offset 1024 (next MN atom), stride
+// byte offset 2048 (next K group of 8), 128-byte swizzle.
+__device__ __forceinline__ uint64_t mn_desc(uint32_t saddr)
 {
-    const int j = lane & 7;
-    // elements 4..7 <-> partner's 0..3 (lane bit 2)
-    xpose_words(w[0], w[2], 4, (j & 4) != 0);
-    xpose_words(w[1], w[3], 4, (j & 4) != 0);
-    // elements (2,3) <-> partner's (0,1) within each half (lane bit 1)
-    xpose_words(w[0], w[1], 2, (j & 2) != 0);
-    xpose_words(w[2], w[3], 2, (j & 2) != 0);
-    // odd <-> even element within each word (lane bit 0): the lane with bit 0
-    // clear keeps its low half and takes the partner's low half into its high
-    // half; the other keeps its high half and takes the partner's high half
-    // into its low half (byte selectors of __byte_perm)
-    const bool up = (j & 1) != 0;
-    const uint32_t sel_send = up ? 0x0010u : 0x0032u, sel_keep = up ? 0x3254u : 0x5410u;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const uint32_t got = __shfl_xor_sync(0xffffffffu, __byte_perm(w[i], 0u, sel_send), 1);
-        w[i] = __byte_perm(w[i], got, sel_keep);
-    }
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(1024 >> 4) << 16) | ((uint64_t)(2048 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
 __global__ void __launch_bounds__(kTT, 1)
@@ -271,7 +253,8 @@ __global__ void __launch_bounds__(kTT, 1)
     } else if (warp == kMmaWarp) {
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(kRows, N4);
+            // both operands MN-major (transpose bits 15 and 16)
+            const uint32_t idesc = idesc_bf16(kRows, N4) | (1u << 15) | (1u << 16);
             uint32_t pass = 0;
             unsigned mask_next = c_begin < c_end ? chunk_mask[c_begin] : 0u;
             for (int ch = c_begin; ch < c_end && ok; ++ch) {
@@ -285,11 +268,12 @@ __global__ void __launch_bounds__(kTT, 1)
                     tc_fence_after();
                     const uint32_t acc = tmem + (uint32_t)(c * N4);
                     uint32_t accum = (seen >> c) & 1u;
-                    const uint64_t a0 = sw128_desc(smem_u32(ops + b * kBuf)), b0 = sw128_desc(smem_u32(ops + b * kBuf + kTile));
+                    const uint64_t a0 = mn_desc(smem_u32(ops + b * kBuf)), b0 = mn_desc(smem_u32(ops + b * kBuf + kTile));
 #pragma unroll
                     for (int kk = 0; kk < 2; ++kk) {
-                        // +32 bytes per K = 16 step; the lo half of a row starts 64 bytes in
-                        const uint64_t ah = a0 + 2 * kk, al = a0 + 4 + 2 * kk, bh = b0 + 2 * kk, bl = b0 + 4 + 2 * kk;
+                        // 4096 bytes (two K groups) per K = 16 step; the lo half starts at K = 32 (8192 bytes)
+                        const uint64_t ah = a0 + 256 * kk, al = a0 + 512 + 256 * kk, bh = b0 + 256 * kk,
+                                       bl = b0 + 512 + 256 * kk;
                         mma_bf16(acc, ah, bh, idesc, accum);
                         mma_bf16(acc, ah, bl, idesc, 1u);
                         mma_bf16(acc, al, bh, idesc, 1u);
@@ -314,7 +298,6 @@ __global__ void __launch_bounds__(kTT, 1)
         // ----------------------------------------------------------- converter
         uint32_t pass = 0;
         const int tasks = 2 * n;                   // (operand, direction) rows per pass
-        const int g = lane >> 3;                   // this lane's group of eight sites
         int it = 0;
         unsigned mask_next = c_begin < c_end ? chunk_mask[c_begin] : 0u;
         for (int ch = c_begin; ch < c_end && ok; ++ch, ++it) {
@@ -340,7 +323,7 @@ __global__ void __launch_bounds__(kTT, 1)
                 uint8_t *A = ops + b * kBuf;
                 const float keep = (single || my_cls == c) ? (beta_scale ? cf.z : 1.f) : 0.f;
                 // up to four (operand, direction) rows per warp (2n <= 64 rows,
-                // 16 warps), unrolled so their shuffle chains interleave
+                // 16 warps)
 #pragma unroll
                 for (int jt = 0; jt < 4; ++jt) {
                     const int t = warp + kConvWarps * jt;
@@ -355,20 +338,13 @@ __global__ void __launch_bounds__(kTT, 1)
                     } else {
                         x.x += cf.w;                                   // S~: emission on I
                     }
-                    // elements 0..3: hi of components 0..3, elements 4..7: lo
-                    uint32_t w[4];
-                    w[0] = pack_bf16(x.x, x.y);
-                    w[1] = pack_bf16(x.z, x.w);
-                    w[2] = pack_bf16(x.x - __uint_as_float(w[0] << 16), x.y - __uint_as_float(w[0] & 0xFFFF0000u));
-                    w[3] = pack_bf16(x.z - __uint_as_float(w[1] << 16), x.w - __uint_as_float(w[1] & 0xFFFF0000u));
-                    // lane k of the group now gets element k (component k % 4,
-                    // hi for k < 4, lo otherwise) of sites 8 g .. 8 g + 7
-                    xpose8x8(w, lane);
-                    const int k = lane & 7, comp = k & 3, part = k >> 2;
-                    const int r = 4 * d + comp;
-                    const int u = (part ? 4 + g : g) ^ (r & 7);
-                    *reinterpret_cast<uint4 *>(A + (uint32_t)o * kTile + (uint32_t)r * 128u + ((uint32_t)u << 4)) =
-                        make_uint4(w[0], w[1], w[2], w[3]);
+                    const uint32_t hi0 = pack_bf16(x.x, x.y), hi1 = pack_bf16(x.z, x.w);
+                    const uint32_t lo0 = pack_bf16(x.x - __uint_as_float(hi0 << 16), x.y - __uint_as_float(hi0 & 0xFFFF0000u));
+                    const uint32_t lo1 = pack_bf16(x.z - __uint_as_float(hi1 << 16), x.w - __uint_as_float(hi1 & 0xFFFF0000u));
+                    uint8_t *tile = A + (uint32_t)o * kTile;
+                    const uint32_t off = mn_off4(d, lane);                 // K = site (hi)
+                    *reinterpret_cast<uint2 *>(tile + off) = make_uint2(hi0, hi1);
+                    *reinterpret_cast<uint2 *>(tile + off + 4u * 2048u) = make_uint2(lo0, lo1);   // K = 32 + site (lo)
                 }
                 fence_proxy_async();
                 __syncwarp();
