@@ -396,7 +396,7 @@ def adjoint_ratio(steps: int, headline: str):
     fwd["tf32x3"] = a.elapsed_time(b)
     s.close()
     seed = torch.randn((w.nx, w.n, 4), device="cuda")
-    for K, prec in ((50, "fp32"), (1, "fp32"), (50, "tf32x3")):
+    for K, prec in ((50, "fp32"), (1, "fp32"), (50, "tf32x3"), (1, "tf32x3")):
         s = solver_for(w, prec)
         # warm-up: the same call, which also sizes the workspace the context
         # keeps between adjoint calls (the timed call allocates nothing)
