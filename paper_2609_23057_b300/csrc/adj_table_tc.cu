@@ -148,6 +148,24 @@ __global__ void k_adj_table_finish(const float *__restrict__ acc, int len, doubl
         out[j] += (double)acc[j] + (double)acc[len + j];
 }
 
+// TMA load of a chunk's rows of beta mu (or nu) or S.  With
+// RTLB_TABLE_LOAD_KEEP the lines keep normal L2 priority (the reverse step
+// that follows reads the same data), otherwise they are marked evict-first.
+#ifndef RTLB_TABLE_LOAD_KEEP
+#define RTLB_TABLE_LOAD_KEEP 1
+#endif
+__device__ __forceinline__ void load_rows(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x)
+{
+#if RTLB_TABLE_LOAD_KEEP
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(0)
+        : "memory");
+#else
+    tma_load_2d(dst, map, bar, x, 0);
+#endif
+}
+
 // MN-major, 128-byte-swizzled operand tile of 128 MN values x 64 K values
 // (bf16): K groups of 8 (2048 bytes each) hold two atoms of 64 MN values (8 K
 // rows of 128 bytes, the 16-byte chunks of row k XOR k % 8).  Byte offset of
@@ -228,8 +246,8 @@ __global__ void __launch_bounds__(kTT, 1)
                 const uint32_t fb = smem_u32(&st_full[slot]);
                 const uint32_t base = smem_u32(stage + slot * kStageAligned);
                 mbar_expect_tx(fb, stage_tx);
-                tma_load_2d(base, &tmA, fb, 4 * ch * kChunk, 0);
-                tma_load_2d(base + kStageS, &tmS, fb, 4 * ch * kChunk, 0);
+                load_rows(base, &tmA, fb, 4 * ch * kChunk);
+                load_rows(base + kStageS, &tmS, fb, 4 * ch * kChunk);
                 tma_load_2d(base + kStageCoef, &tmC, fb, 0, ch * kChunk);
                 if (RTLB_TABLE_PREFETCH_CHUNKS > 0 && it % RTLB_TABLE_PREFETCH_CHUNKS == 0) {
                     // the next run of chunks into L2 together: each direction's

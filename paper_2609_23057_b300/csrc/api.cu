@@ -17,6 +17,15 @@
 
 using namespace rtlb;
 
+// Order of the two reverse-sweep kernels of a step in the transposed-stream
+// form: 1 = table gradient first (it reads the reverse step's inputs only).
+// Measured with the table kernel's loads at normal L2 priority, 300 steps of
+// the 1024 x 256, n = 32 adjoint with every state kept: 73.4 ms first, 74.0 ms
+// after (74.5 ms after with evict-first loads).
+#ifndef RTLB_ADJ_TABLE_FIRST
+#define RTLB_ADJ_TABLE_FIRST 1
+#endif
+
 namespace rtlb {
 
 cudaError_t DevBuf::ensure(size_t bytes)
@@ -770,24 +779,6 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
             for (int j = 0; j + 1 < len; ++j) AK(fp32_step_into(c, state(j), state(j + 1), s), "adjoint recompute");
             for (int j = len - 1; j >= 0; --j) {
                 const bool push = g * K + j > 0;
-                if (a.n_pure > 0) {
-                    AdjTcLaunch tl;
-                    tl.S = state(j);
-                    tl.coef = c->d_coef;
-                    tl.dirT = a.dirT.as<int>();
-                    tl.bcbitsT = bcbitsT;
-                    tl.nu_out = lam + (size_t)(lc ^ 1) * L;
-                    tl.g_alpha = ga;
-                    tl.g_beta = gb;
-                    tl.tiles = a.pure.as<int>();
-                    tl.n_tiles = a.n_pure;
-                    tl.nx = c->nx;
-                    tl.nz = c->nz;
-                    tl.n = c->n;
-                    tl.push = push ? 1 : 0;
-                    tl.sm_count = sm_count;
-                    AK(launch_adjoint_step_tc(tmNu[lc], a.tmZhi, a.tmZlo, tl, s), "adjoint step (tensor cores)");
-                }
                 AdjointParams ap;
                 ap.lam_next = lam + (size_t)lc * L;
                 ap.lam_out = lam + (size_t)(lc ^ 1) * L;
@@ -812,8 +803,30 @@ rtlb_status rtlb_adjoint(rtlb_ctx *c, int32_t nsteps, int32_t checkpoint_every, 
                 ap.chunk_mask = cmask;
                 ap.table_part = w.tpart.as<float>();
                 ap.table_acc = w.tacc.as<float>();
+                // the table gradient reads nu^t and S^t, the reverse step's
+                // inputs, and nothing it writes: run first, it leaves part of
+                // both in L2 for the reverse step
+                if (RTLB_ADJ_TABLE_FIRST) AK(launch_adjoint_table(ap, slots, s), "adjoint table gradient");
+                if (a.n_pure > 0) {
+                    AdjTcLaunch tl;
+                    tl.S = state(j);
+                    tl.coef = c->d_coef;
+                    tl.dirT = a.dirT.as<int>();
+                    tl.bcbitsT = bcbitsT;
+                    tl.nu_out = lam + (size_t)(lc ^ 1) * L;
+                    tl.g_alpha = ga;
+                    tl.g_beta = gb;
+                    tl.tiles = a.pure.as<int>();
+                    tl.n_tiles = a.n_pure;
+                    tl.nx = c->nx;
+                    tl.nz = c->nz;
+                    tl.n = c->n;
+                    tl.push = push ? 1 : 0;
+                    tl.sm_count = sm_count;
+                    AK(launch_adjoint_step_tc(tmNu[lc], a.tmZhi, a.tmZlo, tl, s), "adjoint step (tensor cores)");
+                }
                 AK(launch_adjoint_step_nu_mixed(ap, a.n_mixed, s), "adjoint step (mixed tiles)");
-                AK(launch_adjoint_table(ap, slots, s), "adjoint table gradient");
+                if (!RTLB_ADJ_TABLE_FIRST) AK(launch_adjoint_table(ap, slots, s), "adjoint table gradient");
                 lc ^= 1;
             }
         }
