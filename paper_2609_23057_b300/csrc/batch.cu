@@ -310,7 +310,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int b = i & 1;
             const int site = tile * kTileM + r;
             const int z = site / nx, x = site - z * nx;
-            const bool interior = site < nsites && x > 0 && x < nx - 1 && z > 0 && z < nz - 1;
+            // warp-uniform: a warp with any boundary site pushes all its sites through
+            // the general routine (one path instead of two divergent ones)
+            const bool interior = __all_sync(0xffffffffu, site < nsites && x > 0 && x < nx - 1 && z > 0 && z < nz - 1);
             float *S_new = f.S_new;
             const int *dir = f.dir;
             ok = __all_sync(0xffffffffu,

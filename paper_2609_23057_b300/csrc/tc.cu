@@ -321,7 +321,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int b = i & 1;
             const int site = tile * kTileM + r;
             const int z = site / p.nx, x = site - z * p.nx;
-            const bool interior = site < nsites && x > 0 && x < p.nx - 1 && z > 0 && z < p.nz - 1;
+            // warp-uniform: a warp with any boundary site pushes all its sites through
+            // the general routine (one path instead of two divergent ones)
+            const bool interior = __all_sync(0xffffffffu, site < nsites && x > 0 && x < p.nx - 1 && z > 0 && z < p.nz - 1);
             ok = __all_sync(0xffffffffu,
                             mbar_wait(smem_u32(&acc_full[b]), (i >> 1) & 1, abort_flag, p.err, kErrTimeoutEpilogue));
             if (!ok) break;
@@ -611,7 +613,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             const int b = i & 1;
             const int site = tile * kTileM + r;
             const int z = site / p.nx, x = site - z * p.nx;
-            const bool interior = site < nsites && x > 0 && x < p.nx - 1 && z > 0 && z < p.nz - 1;
+            // warp-uniform: a warp with any boundary site pushes all its sites through
+            // the general routine (one path instead of two divergent ones)
+            const bool interior = __all_sync(0xffffffffu, site < nsites && x > 0 && x < p.nx - 1 && z > 0 && z < p.nz - 1);
             ok = __all_sync(0xffffffffu,
                             mbar_wait(smem_u32(&acc_full[b]), (i >> 1) & 1, abort_flag, p.err, kErrTimeoutEpilogue));
             if (!ok) break;
