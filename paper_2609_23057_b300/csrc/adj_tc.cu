@@ -306,9 +306,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int site = tile * kTileM + r;
             const bool valid = site < nsites;
             const int z = site / p.nx, x = site - z * p.nx;
-            // warp-uniform: a warp with any boundary site pushes all its sites through
-            // the general routine (one path instead of two divergent ones)
-            const bool interior = __all_sync(0xffffffffu, valid && x > 0 && x < p.nx - 1 && z > 0 && z < p.nz - 1);
+            const bool interior = valid && x > 0 && x < p.nx - 1 && z > 0 && z < p.nz - 1;
             const float4 cf = valid ? __ldg(p.coef + site) : make_float4(0.f, 0.f, 0.f, 0.f);
             const double ga0 = valid ? ga[site] : 0.0, gb0 = valid ? gb[site] : 0.0;
             // the next tile's S (this thread's directions) on its way into L2
@@ -354,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     } else if (interior) {
                         out[(size_t)d * nsites + site + s_cx[d] + (long long)s_cz[d] * p.nx] = val;
                     } else {
-                        push_store(p.dirT, nullptr, p.bcbitsT, p.nu_out, p.nx, p.nz, n, site, d, val);
+                        push_store_xz(p.dirT, nullptr, p.bcbitsT, p.nu_out, p.nx, p.nz, n, site, x, z, d, val);
                     }
                 }
             }

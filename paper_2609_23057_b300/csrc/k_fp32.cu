@@ -40,9 +40,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-__device__ __forceinline__ void store_out(const StepParams &p, int site, int d, float4 v)
+__device__ __forceinline__ void store_out(const StepParams &p, int site, int x, int z, int d, float4 v)
 {
-    push_store(p.dir, p.inflow, pack_bc(p.bc), p.S_new, p.nx, p.nz, p.n, site, d, v);
+    push_store_xz(p.dir, p.inflow, pack_bc(p.bc), p.S_new, p.nx, p.nz, p.n, site, x, z, d, v);
 }
 
 template <int N4>
@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
     for (int i = 0; i < TS; ++i) {
         const int s = site_of(i), site = site0 + s;
         if (site >= nsites) continue;
+        const int z = site / p.nx, x = site - z * p.nx;
         const float al = s_alpha[s], alo = s_alo[s], be = s_beta[s];
 #pragma unroll
         for (int jd = 0; jd < 2; ++jd) {
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
                 const float sv = As[(col + k) * SITES + s];
                 o[k] = fmaf(al, sv, fmaf(alo, sv, be * acc[i][4 * jd + k]));
             }
-            store_out(p, site, d, make_float4(o[0], o[1], o[2], o[3]));
+            store_out(p, site, x, z, d, make_float4(o[0], o[1], o[2], o[3]));
         }
     }
 }
@@ -230,7 +231,8 @@ __global__ void __launch_bounds__(128) k_step_fp32_generic(StepParams p)
     v.y = fmaf(cf.x, own.y, fmaf(cf.y, own.y, cf.z * y[1]));
     v.z = fmaf(cf.x, own.z, fmaf(cf.y, own.z, cf.z * y[2]));
     v.w = fmaf(cf.x, own.w, fmaf(cf.y, own.w, cf.z * y[3]));
-    store_out(p, site, o, v);
+    const int z = site / p.nx;
+    store_out(p, site, site - z * p.nx, z, o, v);
 }
 
 template <int N4>

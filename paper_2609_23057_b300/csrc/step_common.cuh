@@ -19,12 +19,13 @@ __host__ __device__ __forceinline__ int pack_bc(const int bc[4])
 }
 __device__ __forceinline__ int bc_of(int bcbits, int side) { return (bcbits >> (2 * side)) & 3; }
 
-__device__ __forceinline__ void push_store(const int *__restrict__ dir, const float *__restrict__ inflow,
-                                           int bcbits, float *__restrict__ S_new, int nx, int nz,
-                                           int n, int site, int d, float4 v)
+// The push of one post-collision Stokes vector of site (x, z) along
+// direction d (with the site's coordinates already known).
+__device__ __forceinline__ void push_store_xz(const int *__restrict__ dir, const float *__restrict__ inflow,
+                                              int bcbits, float *__restrict__ S_new, int nx, int nz,
+                                              int n, int site, int x, int z, int d, float4 v)
 {
     const size_t nsites = (size_t)nx * nz;
-    const int z = site / nx, x = site - z * nx;
     const int cx = dir[d], cz = dir[n + d];
     const bool per_x = bc_of(bcbits, RTLB_SIDE_LEFT) == RTLB_BC_PERIODIC;
     const bool per_z = bc_of(bcbits, RTLB_SIDE_TOP) == RTLB_BC_PERIODIC;
@@ -46,6 +47,14 @@ __device__ __forceinline__ void push_store(const int *__restrict__ dir, const fl
         if (bc_of(bcbits, side) == RTLB_BC_INFLOW) gv = reinterpret_cast<const float4 *>(inflow)[side * n + d];
         out[site] = gv;
     }
+}
+
+__device__ __forceinline__ void push_store(const int *__restrict__ dir, const float *__restrict__ inflow,
+                                           int bcbits, float *__restrict__ S_new, int nx, int nz,
+                                           int n, int site, int d, float4 v)
+{
+    const int z = site / nx, x = site - z * nx;
+    push_store_xz(dir, inflow, bcbits, S_new, nx, nz, n, site, x, z, d, v);
 }
 
 }  // namespace rtlb

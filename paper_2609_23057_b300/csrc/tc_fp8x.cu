@@ -455,9 +455,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int tile = p.tiles[t_begin + i] & 0xFFFFFF;
             const int site = tile * kTileM + r;
             const int z = site / p.nx, x = site - z * p.nx;
-            // warp-uniform: a warp with any boundary site pushes all its sites through
-            // the general routine (one path instead of two divergent ones)
-            const bool interior = __all_sync(0xffffffffu, site < nsites && x > 0 && x < p.nx - 1 && z > 0 && z < p.nz - 1);
+            const bool interior = site < nsites && x > 0 && x < p.nx - 1 && z > 0 && z < p.nz - 1;
             ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(acc_full), i & 1, abort_flag, p.err, kErrTimeoutEpilogue));
             if (!ok) break;
             tc_fence_after();
@@ -489,7 +487,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int k = 0; k < 16; ++k)
                         if (k < step)
-                            push_store(p.dir, p.inflow, p.bcbits, p.S_new, p.nx, p.nz, n, site, d0 + k,
+                            push_store_xz(p.dir, p.inflow, p.bcbits, p.S_new, p.nx, p.nz, n, site, x, z, d0 + k,
                                        make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
                 }
             }
