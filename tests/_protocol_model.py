@@ -729,6 +729,83 @@ def tf32_step(items, stages, seed, gate_ring=True, slow=None):
     return M.steps
 
 
+def table_step(masks, stages, seed, gate_done=True, slow=None):
+    """The adjoint's tensor-core table gradient: `masks` lists the class mask
+    of each 32-site chunk a CTA reduces.  A producer thread fills a ring of
+    `stages` staging slots (st_full by transaction bytes; it waits on
+    st_empty, count 16, before reusing a slot); sixteen converter warps take
+    each chunk's passes (one per class present), write operand buffer
+    pass % 2 after the MMAs of the pass two before it completed (done), and
+    report on op_full (count 16); the MMA thread waits op_full, issues and
+    commits done; every converter warp releases the slot after the chunk's
+    last pass.  gate_done=False drops the converters' wait on done (a planted
+    flaw)."""
+    M = Machine(seed, slow)
+    W = 16
+    st_full = [Barrier(f"st_full[{k}]", 1) for k in range(stages)]
+    st_empty = [Barrier(f"st_empty[{k}]", W) for k in range(stages)]
+    op_full = [Barrier(f"op_full[{b}]", W) for b in range(2)]
+    done = [Barrier(f"done[{b}]", 1) for b in range(2)]
+    stage = [None] * stages
+    ops = {}                               # (buffer, warp) -> (pass, state)
+    passes = [(ch, c) for ch, m in enumerate(masks) for c in range(4) if m >> c & 1]
+
+    def producer():
+        for it, _ in enumerate(masks):
+            k = it % stages
+            if it >= stages:
+                yield Wait(st_empty[k], it // stages - 1, "producer")
+            st_full[k].expect_tx(1)
+
+            def land(k=k, it=it):
+                stage[k] = it
+                st_full[k].complete_tx(1)
+            M.tma_load(land)
+
+    def converter(w):
+        who = f"converter{w}"
+        p = 0
+        for it, m in enumerate(masks):
+            k = it % stages
+            yield Wait(st_full[k], it // stages, who)
+            for c in range(4):
+                if not m >> c & 1:
+                    continue
+                b = p & 1
+                if p >= 2 and gate_done:
+                    yield Wait(done[b], (p >> 1) - 1, who)
+                if stage[k] != it:
+                    raise ProtocolError(f"{who} pass {p}: staging slot {k} holds chunk {stage[k]}, {it} needed")
+                cell = ops.get((b, w))
+                if cell is not None and cell[1] != "used":
+                    raise ProtocolError(f"{who} pass {p}: operand buffer {b} still holds unread pass {cell[0]}")
+                ops[(b, w)] = [p, "written"]
+                op_full[b].arrive()
+                p += 1
+            st_empty[k].arrive()
+
+    def mma():
+        for p, (ch, c) in enumerate(passes):
+            b = p & 1
+            yield Wait(op_full[b], p >> 1, "mma")
+
+            def read(p=p, b=b):
+                for w in range(W):
+                    cell = ops.get((b, w))
+                    if cell is None or cell != [p, "written"]:
+                        raise ProtocolError(f"MMA pass {p}: operand buffer {b} part {w} is {cell}")
+                    cell[1] = "used"
+            M.issue_mma(read)
+            M.commit(done[b])
+
+    M.add_role("producer", producer())
+    M.add_role("mma", mma())
+    for w in range(W):
+        M.add_role(f"conv{w}", converter(w))
+    M.run()
+    return M.steps
+
+
 def pair_step(keys, stages, seed, n=64, gate_acc_empty=True, slow=None):
     """The CTA-pair kernel (cta_group::2, bf16 state operand and split table):
     each entry of `keys` is one pair of tiles (one per CTA) of the same table

@@ -122,3 +122,24 @@ def test_tf32_model_sees_ungated_ring():
     with pytest.raises(P.ProtocolError, match="ring slot"):
         for seed in range(5):
             P.tf32_step([(32, 0)] * 4, 2, seed, gate_ring=False)
+
+
+@pytest.mark.parametrize("stages", [2, 4])
+def test_table_gradient_is_race_free(stages):
+    """The adjoint's tensor-core table gradient: staging ring, double-buffered
+    operands, one pass per class present in a chunk (mixed chunks make two);
+    also with one role lagging far behind."""
+    masks = [1, 1, 3, 2, 2, 3, 1, 2, 1, 1]
+    for seed in range(6):
+        P.table_step(masks, stages, seed)
+    for slow in ("conv3", "mma", "producer"):
+        P.table_step(masks, stages, 0, slow={slow: 0.01})
+
+
+def test_table_gradient_model_sees_ungated_buffer():
+    """Converters that overwrite an operand buffer without waiting for the
+    MMAs of the pass two before it: with the MMA thread lagging, the model
+    must report the overwrite."""
+    with pytest.raises(P.ProtocolError, match="operand buffer"):
+        for seed in range(10):
+            P.table_step([1] * 8, 4, seed, gate_done=False, slow={"mma": 0.01})
