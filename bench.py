@@ -453,30 +453,36 @@ def batch_throughput(steps: int, count: int = 256):
     return out
 
 
-def bilinear_throughput(precision: str, steps: int, nearest_ms: float, peaks, src):
-    """The same workload with semi-Lagrangian bilinear streaming (Eq. 34):
-    an in-place collision pass, then the four-tap gather kernel."""
+def bilinear_throughput(precision: str, steps: int, nearest_ms: float, peaks, src, w=None):
+    """A workload with semi-Lagrangian bilinear streaming (Eq. 34), by default
+    the headline one.  In the gather form (the bf16 tensor-core steps at
+    n <= 32) each step gathers the previous step's post-collision field while
+    loading, one pass over the state like the nearest scheme; the other forms
+    (n = 64 included) run a collision pass and the four-tap gather kernel."""
     import torch
     from paper_2609_23057_b300.solver import solver_for
-    w = W.precision(seed=1, steps=steps)
+    w = w or W.precision(seed=1, steps=steps)
     w.scheme = "bilinear"
     s = solver_for(w, precision)
     s.step(3)
     torch.cuda.synchronize()
     per, tot = _time_steps(torch, s, torch.cuda.current_stream(), steps)
+    gather = s.gather_form
+    mixed = s.mixed_tiles
     s.close()
     del s
     torch.cuda.empty_cache()
     sdu = w.sites * w.n
     ms = tot / len(per)
-    gather_ms = ms - nearest_ms
-    gbs = 32.0 * sdu / (gather_ms * 1e-3) / 1e9 if gather_ms > 0 else None
+    gbs = (32.0 + 16.0 / w.n) * sdu / (ms * 1e-3) / 1e9
     return {"workload": w.name + "_bilinear", "precision": precision, "value": sdu * len(per) / (tot * 1e-3),
-            "unit": UNIT, "ms_per_step": ms, "steps": len(per), "gpu_launches_per_step": 2,
-            "gather_ms_estimate": gather_ms,
-            "gather_roofline": {"bound": "hbm", "achieved": gbs, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-                                "frac": None if gbs is None else gbs / float(peaks["hbm_gbs"]),
-                                "note": "32 B per site-direction over (bilinear step - nearest step) time"}}
+            "unit": UNIT, "ms_per_step": ms, "steps": len(per), "form": "gather" if gather else "two-pass",
+            "gpu_launches_per_step": (1 if gather else 2) + (1 if mixed else 0),
+            "over_nearest": None if nearest_ms is None else ms / nearest_ms,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                         "frac": gbs / float(peaks["hbm_gbs"]),
+                         "note": "one pass's (32 + 16/n) B per site-direction (the least a step moves) over "
+                                 "the step time; the two-pass form moves twice that"}}
 
 
 def run_ours(args):
@@ -598,6 +604,9 @@ def run_ours(args):
         if ws == 1 and args.bilinear_steps > 0 and args.nx == 2048 and args.nz == 2048:
             line["bilinear"] = _leg(bilinear_throughput, args.precision, args.bilinear_steps, t_max / args.steps, peaks,
                                     src)
+            # the gather form: 2048^2 at n = 32 (bf16x2 runs it on one CTA per tile)
+            line["bilinear_n32"] = _leg(bilinear_throughput, args.precision, args.bilinear_steps, None, peaks, src,
+                                        W.cloud("lattice2048_n32", 2048, 2048, 4, 8, 1, args.bilinear_steps))
         if ws == 1 and args.batch_steps > 0:
             line["batch"] = _leg(batch_throughput, args.batch_steps, args.batch_channels)
         if ws == 1 and args.adjoint_steps > 0:

@@ -185,7 +185,12 @@ rtlb_status rtlb_get_state(rtlb_ctx *ctx, float *S_out, void *stream);
 
 /* Advance nsteps >= 0 steps: per step and site, emission, absorption,
  * scattering (the 4n x 4n contraction), then streaming of every direction to
- * its neighbour.  The stored state is the paper's S^t (after streaming). */
+ * its neighbour.  The stored state is the paper's S^t (after streaming); in
+ * the gather form of BILINEAR streaming (rtlb_get_form) the context holds the
+ * last step's post-collision field and streams it when a reader needs S^t
+ * (rtlb_get_state, the readouts, the residual: one extra pass, done once per
+ * step taken) or when the next step loads it.  rtlb_set_boundary completes a
+ * pending streaming with the old boundary first. */
 rtlb_status rtlb_step(rtlb_ctx *ctx, int32_t nsteps, void *stream);
 
 /* Step until the residual max|S^{t+1} - S^t| / max|S^{t+1}| (float64 on the
@@ -258,6 +263,21 @@ rtlb_status rtlb_total_intensity(rtlb_ctx *ctx, double *total, void *stream);
 
 /* Steps taken since the last rtlb_set_state (or creation). */
 int64_t rtlb_steps_done(const rtlb_ctx *ctx);
+
+/* How the context's steps run, as decided by rtlb_set_medium (all zero before
+ * it): tensor_core = 1 for the tcgen05 step kernels (0: CUDA cores, float32);
+ * cta_pair = 1 for the CTA-pair form (bf16x2 at n = 64); gather_form = 1 when
+ * BILINEAR streaming is gathered while the next step loads its operand (one
+ * pass over the state per step: the BF16, BF16X2 and BF16X3 tensor-core steps
+ * at n in {16, 32} with nx % 128 == 0 -- other forms run a collision pass and
+ * a gather pass; the state a reader sees is the same to the bit);
+ * mixed_tiles = the 128-site tiles that mix phase classes (or are left
+ * unpaired) and run on the CUDA-core kernel; stages = staging slots of the
+ * tensor-core kernel.  RTLB_E_ARG for NULL. */
+typedef struct {
+    int32_t tensor_core, cta_pair, gather_form, mixed_tiles, stages;
+} rtlb_form;
+rtlb_status rtlb_get_form(const rtlb_ctx *ctx, rtlb_form *out);
 
 const char *rtlb_last_error(const rtlb_ctx *ctx);
 void rtlb_destroy(rtlb_ctx *ctx);

@@ -30,7 +30,7 @@ EXPORTS = [
     "rtlb_residual_noalloc", "rtlb_adjoint", "rtlb_phase_conserve_intensity",
     "rtlb_batch_create", "rtlb_batch_configure", "rtlb_batch_balance", "rtlb_batch_step", "rtlb_batch_check",
     "rtlb_batch_last_error", "rtlb_batch_destroy", "rtlb_stream_taps", "rtlb_release_workspace",
-    "rtlb_dop_out", "rtlb_phase_hg_grad", "rtlb_test_stall_next_step",
+    "rtlb_dop_out", "rtlb_phase_hg_grad", "rtlb_test_stall_next_step", "rtlb_get_form",
 ]
 
 
@@ -46,6 +46,11 @@ class Directions(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("survival", C.c_int32), ("absorption", C.c_int32),
                 ("streaming", C.c_int32), ("plane", C.c_int32)]
+
+
+class Form(C.Structure):
+    _fields_ = [("tensor_core", C.c_int32), ("cta_pair", C.c_int32), ("gather_form", C.c_int32),
+                ("mixed_tiles", C.c_int32), ("stages", C.c_int32)]
 
 
 class RtlbError(RuntimeError):
@@ -103,6 +108,7 @@ def lib() -> C.CDLL:
     L.rtlb_dop_out.argtypes = [vp, i32, vp, vp]
     L.rtlb_phase_hg_grad.argtypes = [C.POINTER(Directions), C.c_double, C.c_double, vp, dp]
     L.rtlb_test_stall_next_step.argtypes = [vp]
+    L.rtlb_get_form.argtypes = [vp, C.POINTER(Form)]
     for name in EXPORTS:
         f = getattr(L, name)
         if f.restype is C.c_int:     # ctypes default: status codes are int32

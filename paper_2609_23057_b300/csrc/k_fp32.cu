@@ -11,7 +11,9 @@
 // site, and also writes the ghost value (zero or inflow) into its own entries
 // whose upstream cell lies outside a non-periodic side -- those entries have
 // no other writer.  The state is direction-major [d][site][4], so a warp's
-// loads of one direction are contiguous 16-byte vectors.
+// loads of one direction are contiguous 16-byte vectors.  With bilinear
+// streaming in the gather form the kernel stores P at the site itself and the
+// next step's load forms S~ from four taps of it (step_common.cuh).
 #include "rtlb_internal.h"
 #include "step_common.cuh"
 
@@ -27,8 +29,10 @@ struct Cfg {
     static constexpr int SITES = SG * TS;                // sites per CTA
     static constexpr int KC = 16;                        // k rows per B chunk
     // S~ tile, two Z^T chunks (the next one is copied in while the current one
-    // is used), four per-site words
-    static constexpr size_t SMEM = (size_t)N4 * SITES * 4 + (size_t)2 * KC * N4 * 4 + (size_t)SITES * 16;
+    // is used), four per-site words, the bilinear taps of the gather form
+    // (n = N4 / 4 directions x 12 words)
+    static constexpr size_t SMEM = (size_t)N4 * SITES * 4 + (size_t)2 * KC * N4 * 4 + (size_t)SITES * 16 +
+                                   (size_t)(N4 / 4) * 48;
 };
 
 __device__ __forceinline__ void cp_async16(float *dst, const float *src)
@@ -57,6 +61,8 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
     float *s_alo = s_alpha + SITES;          // [SITES]  alpha lo
     float *s_beta = s_alo + SITES;           // [SITES]
     int *s_cls = reinterpret_cast<int *>(s_beta + SITES);
+    int *s_to = s_cls + SITES;                                   // [n][8] tap offsets (gather form)
+    float *s_tw = reinterpret_cast<float *>(s_to + 8 * (N4 / 4)); // [n][4] tap weights
     __shared__ unsigned s_mask;
 
     const int n = p.n;
@@ -74,6 +80,11 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
     const int nsites_all = p.nx * p.nz;
     const int tid = threadIdx.x;
     if (tid == 0) s_mask = 0u;
+    if (p.taps_o)
+        for (int k = tid; k < 12 * n; k += 256) {
+            if (k < 8 * n) s_to[k] = p.taps_o[k];
+            else s_tw[k - 8 * n] = p.taps_w[k - 8 * n];
+        }
     __syncthreads();
 
     // coefficients and classes of the tile
@@ -94,14 +105,23 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
     }
     if (my_mask) atomicOr(&s_mask, my_mask);
 
-    // S~ tile, transposed to k-major; emission added to I (Eq. 6/8)
+    // S~ tile, transposed to k-major; emission added to I (Eq. 6/8).  In the
+    // gather form S~ is the bilinear sum of the previous step's P.
     const float4 *S4 = reinterpret_cast<const float4 *>(p.S);
+    const int bcbits = pack_bc(p.bc);
     for (int idx = tid; idx < n * SITES; idx += 256) {
         const int d = idx / SITES, s = idx - d * SITES;
         const int site = site0 + s;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (site < nsites) {
-            v = S4[(size_t)d * nsites_all + site];
+            if (p.taps_o) {
+                const int z = site / p.nx;
+                v = gather_bilinear(load_taps<true>(s_to, s_tw, d), S4 + (size_t)d * nsites_all,
+                                    reinterpret_cast<const float4 *>(p.inflow), bcbits, p.nx, p.nz, n, d, site,
+                                    site - z * p.nx, z);
+            } else {
+                v = S4[(size_t)d * nsites_all + site];
+            }
             v.x += p.coef[site].w;
         }
         As[(4 * d + 0) * SITES + s] = v.x;
@@ -216,8 +236,12 @@ __global__ void __launch_bounds__(128) k_step_fp32_generic(StepParams p)
     const float4 *S4 = reinterpret_cast<const float4 *>(p.S);
     float y[4] = {0.f, 0.f, 0.f, 0.f};
     float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int zs = site / p.nx;
     for (int d = 0; d < p.n; ++d) {
-        float4 v = S4[(size_t)d * nsites + site];
+        float4 v = p.taps_o ? gather_bilinear(load_taps(p.taps_o, p.taps_w, d), S4 + (size_t)d * nsites,
+                                              reinterpret_cast<const float4 *>(p.inflow), pack_bc(p.bc), p.nx, p.nz,
+                                              p.n, d, site, site - zs * p.nx, zs)
+                            : S4[(size_t)d * nsites + site];
         v.x += cf.w;
         if (d == o) own = v;
         const float sv[4] = {v.x, v.y, v.z, v.w};
@@ -231,8 +255,7 @@ __global__ void __launch_bounds__(128) k_step_fp32_generic(StepParams p)
     v.y = fmaf(cf.x, own.y, fmaf(cf.y, own.y, cf.z * y[1]));
     v.z = fmaf(cf.x, own.z, fmaf(cf.y, own.z, cf.z * y[2]));
     v.w = fmaf(cf.x, own.w, fmaf(cf.y, own.w, cf.z * y[3]));
-    const int z = site / p.nx;
-    store_out(p, site, site - z * p.nx, z, o, v);
+    store_out(p, site, site - zs * p.nx, zs, o, v);
 }
 
 template <int N4>

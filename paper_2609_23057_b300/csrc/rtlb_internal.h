@@ -39,6 +39,11 @@ struct StepParams {
     // optional: restrict the step to listed tiles of tile_span sites
     const int *tile_list = nullptr;
     int n_tiles = 0, tile_span = 0;
+    // optional (bilinear streaming, gather form): S holds the post-collision
+    // field P of the step before, and the operand S~ is gathered from its four
+    // taps while loading (taps_o [n][8] int, taps_w [n][4] float)
+    const int *taps_o = nullptr;
+    const float *taps_w = nullptr;
 };
 
 // Everything one adjoint step needs (see adjoint.cu).
@@ -201,6 +206,13 @@ struct rtlb_ctx {
 
     int64_t steps = 0;
     bool has_prev = false;
+    // bilinear streaming in the gather form: each step reads the previous
+    // step's post-collision field P and gathers its streaming while loading,
+    // so the streaming of the last step is deferred -- S[cur] then holds that
+    // step's P, and the state S^t is its gather (api.cu: state_view, settle)
+    bool deferred = false;
+    bool prev_deferred = false;   // the same for S[cur ^ 1] (the residual's previous state)
+    bool view_valid = false;      // d_post holds the gather of S[cur]
     std::string err;
 
     size_t nsites() const { return (size_t)nx * nz; }

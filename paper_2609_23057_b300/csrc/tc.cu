@@ -36,6 +36,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <tuple>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -73,6 +74,12 @@ struct TcState {
     CUtensorMap tmZhi{}, tmZlo{}, tmS[2]{};
     bool tmS_ready[2] = {false, false};
     const float *tmS_ptr[2] = {nullptr, nullptr};
+    // gather form (bilinear streaming on CTA pairs): window maps of both state
+    // buffers; tiles ordered down 256-site column strips
+    bool gather = false;
+    GatherTaps gtaps{};
+    CUtensorMap tmG[2]{};
+    const float *tmG_ptr[2] = {nullptr, nullptr};
     int sm_count = 0;
     int stages = 0;
     size_t smem = 0;
@@ -81,11 +88,15 @@ struct TcState {
 
 // MODE 1: bf16 operands; 2: bf16 state operand, table as bf16 hi + lo (two
 // MMAs); 3: both operands hi + lo (three MMAs).
-template <int MODE>
+template <int MODE, bool GATHER>
 __global__ void __launch_bounds__(kThreads, 1)
     k_step_tc(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmZhi,
-              const __grid_constant__ CUtensorMap tmZlo, TcParams p, int N4, int stages)
+              const __grid_constant__ CUtensorMap tmZlo, TcParams p, int N4, int stages,
+              const __grid_constant__ GatherTaps gt)
 {
+    // GATHER: tmS is the windows' map (see encode_gather_map), the staging
+    // slots hold four directions' windows and the converters form S~ from them
+    constexpr uint32_t stage_bytes = GATHER ? kGatherStageBytes : (uint32_t)kStageBytes;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023u)) & 1023u);
     constexpr bool ZLO = MODE >= 2, ALO = MODE == 3;
@@ -101,7 +112,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t *sA = sZlo + (ZLO ? C * z_chunk : 0);
     uint8_t *sAlo = sA + C * a_chunk;
     uint8_t *sStage = sAlo + (ALO ? C * a_chunk : 0);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sStage + (size_t)stages * kStageBytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sStage + (size_t)stages * stage_bytes);
     uint64_t *st_full = bars;
     uint64_t *st_empty = st_full + stages;
     uint64_t *a_empty = st_empty + stages;     // [C]
@@ -111,7 +122,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *z_full = acc_empty + 2;          // [1]
     uint64_t *drain = z_full + 1;              // [1]
     uint64_t *z_free = drain + 1;              // [1]  the resident table's last MMAs completed
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(z_free + 1);
+    uint64_t *fill_bar = z_free + 1;           // [2]  gather form: a converter group's ghost fill done
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fill_bar + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     int8_t *s_cx = reinterpret_cast<int8_t *>(tmem_slot + 2);   // [n]
     int8_t *s_cz = s_cx + kMaxDirs;                              // [n]
@@ -141,6 +153,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_init(smem_u32(z_full), 1);
         mbar_init(smem_u32(drain), 1);
         mbar_init(smem_u32(z_free), 1);
+        mbar_init(smem_u32(&fill_bar[0]), 4);
+        mbar_init(smem_u32(&fill_bar[1]), 4);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -184,15 +198,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                     prev_cls = cls;
                 }
                 // keep the next tiles' state on its way into L2
-                for (int ahead = (i == 0 ? 1 : RTLB_TC_PREFETCH_TILES); ahead <= RTLB_TC_PREFETCH_TILES; ++ahead) {
+                for (int ahead = (i == 0 ? 1 : RTLB_TC_PREFETCH_TILES); !GATHER && ahead <= RTLB_TC_PREFETCH_TILES;
+                     ++ahead) {
                     if (i + ahead >= T) break;
                     const int nt = p.tiles[t_begin + i + ahead] & 0xFFFFFF;
                     for (int j = 0; j < groups; ++j)
                         for (int h = 0; h < kTileM / kHalfSites; ++h)
                             tma_prefetch_2d(&tmS, 4 * (nt * kTileM + h * kHalfSites), j * kDirsPerStage);
                 }
-                for (int j = 0; j < groups && ok; ++j) {
-                    const int gr = j & 1;
+                const int nslots = GATHER ? n / kGatherDirs : groups;
+                for (int j = 0; j < nslots && ok; ++j) {
+                    // gather form: slots 4c + 2 grp + {0, 1} go to group grp
+                    const int gr = GATHER ? (j >> 1) & 1 : j & 1;
                     const uint32_t local = gq[gr]++;
                     const int s = ring_slot(gr, local, stages / 2);
                     ok = mbar_wait(smem_u32(&st_empty[s]), ((local / (uint32_t)(stages / 2)) & 1) ^ 1, abort_flag, p.err,
@@ -200,6 +217,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!ok) break;
                     if (stall && i == 0 && j == 0) continue;   // test hook: this load is never issued
                     const uint32_t fb = smem_u32(&st_full[s]);
+                    if (GATHER) {
+                        mbar_expect_tx(fb, kGatherStageTx);
+                        gather_slot_loads(&tmS, gt, p.nx, tile * kTileM, j, smem_u32(sStage + (size_t)s * stage_bytes), fb);
+                        continue;
+                    }
                     mbar_expect_tx(fb, kStageBytes);
                     for (int h = 0; h < kTileM / kHalfSites; ++h)
                         tma_load_2d(smem_u32(sStage + (size_t)s * kStageBytes + h * (kStageBytes / 2)), &tmS, fb,
@@ -279,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int grp = (warp - kConvWarp0) >> 2;  // staging-slot group
         const int r = q * 32 + lane;               // site row = TMEM lane
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        uint32_t gq = 0;
+        uint32_t gq = 0, fq = 0;   // staging slots consumed; ghost fills (gather form)
         bool ok = true;
         // tile entries two ahead, coefficients one ahead (see load_coef)
         int e_next = T > 0 ? p.tiles[t_begin] : 0, e_after = T > 1 ? p.tiles[t_begin + 1] : 0;
@@ -298,8 +320,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!ok) break;
             tc_fence_after();
             const uint32_t acc = tmem + lane_base + (uint32_t)((sepE ? 2 * N4 : 0) + b * N4);   // E, else D
-            ok = convert_tile<ALO>(cf, p.fwd + (size_t)(entry >> 24) * n, r, lane, grp, n, groups, stages, gq, i, acc, sA,
-                                   sAlo, sStage, st_full, st_empty, a_empty, a_chunk, abort_flag, p.err);
+            if (GATHER) {
+                const int site = (entry & 0xFFFFFF) * kTileM + r, z = site / p.nx, x = site - z * p.nx;
+                const GatherGeom g{p.nx, p.nz, p.bcbits, reinterpret_cast<const float4 *>(p.P),
+                                   reinterpret_cast<const float4 *>(p.inflow)};
+                ok = convert_tile_gather<ALO>(cf, p.fwd + (size_t)(entry >> 24) * n, r, lane, grp, n, stages, gq, i, acc,
+                                              sA, sAlo, sStage, st_full, st_empty, a_empty, fill_bar, fq, a_chunk, g, gt,
+                                              !gather_interior_tile(gt, p.bcbits, p.nx, p.nz, x - r, z), x, z,
+                                              abort_flag, p.err);
+            } else {
+                ok = convert_tile<ALO>(cf, p.fwd + (size_t)(entry >> 24) * n, r, lane, grp, n, groups, stages, gq, i,
+                                       acc, sA, sAlo, sStage, st_full, st_empty, a_empty, a_chunk, abort_flag, p.err);
+            }
             if (!ok) break;
             tmem_wait_st();
             fence_proxy_async();
@@ -378,10 +410,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 // even CTA with a single remote (cluster-scope release) arrive, which keeps
 // that microsecond-long release off the converters' path.  Its producer
 // forwards the completion of its half of the table the same way.
+template <bool GATHER>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     k_step_tc_pair(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmZhi,
-                   const __grid_constant__ CUtensorMap tmZlo, TcParams p, int N4, int stages)
+                   const __grid_constant__ CUtensorMap tmZlo, TcParams p, int N4, int stages,
+                   const __grid_constant__ GatherTaps gt)
 {
+    // GATHER: tmS is the windows' map (see encode_gather_map), the staging
+    // slots hold four directions' windows and the converters form S~ from them
+    constexpr uint32_t stage_bytes = GATHER ? kGatherStageBytes : (uint32_t)kStageBytes;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t rank = cluster_rank();
@@ -398,7 +435,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     uint8_t *sZlo = sZ + C * z_chunk;
     uint8_t *sA = sZlo + C * z_chunk;
     uint8_t *sStage = sA + C * a_chunk;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sStage + (size_t)stages * kStageBytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sStage + (size_t)stages * stage_bytes);
     uint64_t *st_full = bars;
     uint64_t *st_empty = st_full + stages;
     uint64_t *a_empty = st_empty + stages;     // [C]   multicast commit from the even CTA
@@ -409,7 +446,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     uint64_t *drain = z_full + 1;              // [1]   multicast commit
     uint64_t *z_free = drain + 1;              // [1]   multicast commit: the resident table is no longer read
     uint64_t *t_local = z_free + 1;            // [2]   odd CTA: its 4 converter warps, forwarded to the even CTA
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(t_local + 2);
+    uint64_t *fill_bar = t_local + 2;          // [2]   gather form: a converter group's ghost fill done
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fill_bar + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     int8_t *s_cx = reinterpret_cast<int8_t *>(tmem_slot + 2);
     int8_t *s_cz = s_cx + kMaxDirs;
@@ -432,6 +470,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         mbar_init(smem_u32(z_full), leader ? 2 : 1);
         mbar_init(smem_u32(drain), 1);
         mbar_init(smem_u32(z_free), 1);
+        mbar_init(smem_u32(&fill_bar[0]), 4);
+        mbar_init(smem_u32(&fill_bar[1]), 4);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -480,8 +520,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     ++zl;
                     prev_cls = cls;
                 }
-                for (int j = 0; j < groups && ok; ++j) {
-                    const int gr = j & 1;
+                const int nslots = GATHER ? n / kGatherDirs : groups;
+                for (int j = 0; j < nslots && ok; ++j) {
+                    // gather form: slots 4c + 2 grp + {0, 1} go to group grp
+                    const int gr = GATHER ? (j >> 1) & 1 : j & 1;
                     const uint32_t local = gq[gr]++;
                     const int s = ring_slot(gr, local, stages / 2);
                     ok = mbar_wait(smem_u32(&st_empty[s]), ((local / (uint32_t)(stages / 2)) & 1) ^ 1, abort_flag, p.err,
@@ -489,6 +531,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     if (!ok) break;
                     if (stall && i == 0 && j == 0) continue;   // test hook: this load is never issued
                     const uint32_t fb = smem_u32(&st_full[s]);
+                    if (GATHER) {
+                        // direction d's window: rows z - n0z - 1 and z - n0z, sites
+                        // x0 - n0x - 1 ... x0 - n0x + 127 (zero outside the lattice)
+                        mbar_expect_tx(fb, kGatherStageTx);
+                        gather_slot_loads(&tmS, gt, p.nx, tile * kTileM, j, smem_u32(sStage + (size_t)s * stage_bytes), fb);
+                        continue;
+                    }
                     mbar_expect_tx(fb, kStageBytes);
                     for (int h = 0; h < kTileM / kHalfSites; ++h)
                         tma_load_2d(smem_u32(sStage + (size_t)s * kStageBytes + h * (kStageBytes / 2)), &tmS, fb,
@@ -571,7 +620,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         const int grp = (warp - kConvWarp0) >> 2;
         const int r = q * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        uint32_t gq = 0;
+        uint32_t gq = 0, fq = 0;   // staging slots consumed; ghost fills (gather form)
         bool ok = true;
         // coefficients and classes fetched a tile ahead (see load_coef)
         float4 cf_next = T > 0 ? load_coef(p.coef, my_tile(0) * kTileM + r, nsites) : float4{};
@@ -589,8 +638,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             if (!ok) break;
             tc_fence_after();
             const uint32_t acc = tmem + lane_base + (uint32_t)(b * N4);
-            ok = convert_tile<false>(cf, p.fwd + (size_t)cls * n, r, lane, grp, n, groups, stages, gq, i, acc, sA, sA, sStage,
-                                     st_full, st_empty, a_empty, a_chunk, abort_flag, p.err);
+            if (GATHER) {
+                const int site = my_tile(i) * kTileM + r, z = site / p.nx, x = site - z * p.nx;
+                const GatherGeom g{p.nx, p.nz, p.bcbits, reinterpret_cast<const float4 *>(p.P),
+                                   reinterpret_cast<const float4 *>(p.inflow)};
+                ok = convert_tile_gather<false>(cf, p.fwd + (size_t)cls * n, r, lane, grp, n, stages, gq, i, acc, sA, sA,
+                                                sStage, st_full, st_empty, a_empty, fill_bar, fq, a_chunk, g, gt,
+                                                !gather_interior_tile(gt, p.bcbits, p.nx, p.nz, x - r, z), x, z,
+                                                abort_flag, p.err);
+            } else {
+                ok = convert_tile<false>(cf, p.fwd + (size_t)cls * n, r, lane, grp, n, groups, stages, gq, i, acc, sA, sA,
+                                         sStage, st_full, st_empty, a_empty, a_chunk, abort_flag, p.err);
+            }
             if (!ok) break;
             tmem_wait_st();
             fence_proxy_async();
@@ -689,6 +748,22 @@ bool encode_state_map(CUtensorMap *m, const float *S, size_t nsites, int n)
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Windows of the gather form: 4D view (the 8 floats of a pair of sites, site
+// pair, row z, direction d) of the direction-major state (nx even), boxes of
+// 65 site pairs x 2 rows, zero outside the lattice.
+bool encode_gather_map(CUtensorMap *m, const float *S, int nx, int nz, int n)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[4] = {8, (cuuint64_t)nx / 2, (cuuint64_t)nz, (cuuint64_t)n};
+    cuuint64_t strides[3] = {32, (cuuint64_t)nx * 16, (cuuint64_t)nx * nz * 16};
+    cuuint32_t box[4] = {8, (cuuint32_t)kGatherCols / 2, 2, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(S), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool encode_z_map(CUtensorMap *m, const __nv_bfloat16 *Z, int N4, int KP, int n_phase, int box_rows)
 {
     auto fn = encode_fn();
@@ -774,19 +849,20 @@ void free_tables(TcState *t)
     t->n_pure = t->n_mixed = 0;
 }
 
-size_t smem_bytes(int N4, int mode, int stages)
+size_t smem_bytes(int N4, int mode, int stages, bool gather = false)
 {
     const int C = (N4 + 63) / 64;
     size_t b = (size_t)C * N4 * 128 * (mode >= 2 ? 2 : 1) + (size_t)C * kTileM * 128 * (mode == 3 ? 2 : 1) +
-               (size_t)stages * kStageBytes + (size_t)(2 * stages + C + 9) * 8 + 16 + 2 * kMaxDirs;
+               (size_t)stages * (gather ? kGatherStageBytes : (uint32_t)kStageBytes) + (size_t)(2 * stages + C + 11) * 8 + 16 + 2 * kMaxDirs;
     return b + 1024;  // alignment slack
 }
 
-size_t smem_bytes_pair(int N4, int stages)
+size_t smem_bytes_pair(int N4, int stages, bool gather = false)
 {
     const int C = (N4 + 63) / 64;
-    size_t b = (size_t)C * (N4 / 2) * 128 * 2 + (size_t)C * kTileM * 128 + (size_t)stages * kStageBytes +
-               (size_t)(2 * stages + C + 11) * 8 + 16 + 2 * kMaxDirs;
+    size_t b = (size_t)C * (N4 / 2) * 128 * 2 + (size_t)C * kTileM * 128 +
+               (size_t)stages * (gather ? kGatherStageBytes : (uint32_t)kStageBytes) +
+               (size_t)(2 * stages + C + 13) * 8 + 16 + 2 * kMaxDirs;
     return b + 1024;
 }
 
@@ -804,13 +880,14 @@ int mode_of(int precision)
 
 // Largest even stage count that fits (0 = does not fit); even because each
 // of the two converter groups owns half of the staging slots.
-int fit_stages(int N4, int mode, bool pair)
+int fit_stages(int N4, int mode, bool pair, bool gather = false)
 {
     for (int st = RTLB_TC_MAX_STAGES & ~1; st >= 2; st -= 2)
-        if ((pair ? smem_bytes_pair(N4, st)
+        if ((pair ? smem_bytes_pair(N4, st, gather)
                   : (mode == 4 ? tc_fp8_smem_bytes(N4, st)
                                : (mode == 5 ? tc_tf32_smem_bytes(N4, st)
-                                            : (mode == 6 ? tc_fp8x_smem_bytes(N4, st) : smem_bytes(N4, mode, st))))) <=
+                                            : (mode == 6 ? tc_fp8x_smem_bytes(N4, st)
+                                                         : smem_bytes(N4, mode, st, gather))))) <=
             (size_t)kSmemLimit)
             return st;
     return 0;
@@ -839,11 +916,36 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
         return RTLB_E_UNSUPPORTED;
     }
     const int N4 = 4 * c->n, KP = ((N4 + 63) / 64) * 64, C = KP / 64;
-    bool pair = false;
+    bool pair = false, gather = false;
     int stages = fit_stages(N4, mode, false);
     if (stages == 0 && mode == 2) {
         pair = true;
         stages = fit_stages(N4, mode, true);
+    }
+    // bilinear streaming is gathered while loading (the bf16 forms) where
+    // tiles are row segments and the windows' staging fits
+    GatherTaps gtaps{};
+    bool taps_ok = c->opt.streaming == RTLB_STREAM_BILINEAR && c->n <= kTcMaxDirs;
+    for (int d = 0; taps_ok && d < c->n; ++d) {
+        const int *o = &c->tap_o[8 * (size_t)d];
+        for (int k = 0; k < 4; ++k)
+            if (o[k] != o[0] + (k & 1) || o[4 + k] != o[4] + (k >> 1) || std::abs(o[0]) > 100 || std::abs(o[4]) > 100)
+                taps_ok = false;
+        const float *w = &c->tap_w[4 * (size_t)d];
+        gtaps.w[d] = make_float4(w[0], w[1], w[2], w[3]);
+        gtaps.n0x[d] = (int8_t)o[0];
+        gtaps.n0z[d] = (int8_t)o[4];
+        gtaps.reach_x = std::max(gtaps.reach_x, std::max(std::abs(o[0]), std::abs(o[0] + 1)));
+        gtaps.reach_z = std::max(gtaps.reach_z, std::max(std::abs(o[4]), std::abs(o[4] + 1)));
+    }
+    if (stages > 0 && mode <= 3 && taps_ok && c->nx % kTileM == 0 && c->n % 16 == 0) {
+        // at least two staging slots per converter group (four directions
+        // each) in flight: with one, each slot's load latency shows in full
+        const int gst = fit_stages(N4, mode, pair, true);
+        if (gst >= 4) {
+            gather = true;
+            stages = gst;
+        }
     }
     if (stages == 0) {
         c->err = "this precision form does not fit in shared memory for this n";
@@ -972,7 +1074,20 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
         if (same) pure.push_back(tile | ((int)cls[a] << 24));
         else mixed.push_back(tile);
     }
-    std::stable_sort(pure.begin(), pure.end(), [](int x, int y) { return (x >> 24) < (y >> 24); });
+    if (gather) {
+        // by class, then down strips of 256 sites (two tiles, one per CTA of a
+        // pair): a CTA's next tile is the one below, so one of the two window
+        // rows it reads was read for the tile before and is still in L2
+        const int nx = c->nx;
+        auto key = [nx](int e) {
+            const long long site0 = (long long)(e & 0xFFFFFF) * kTileM;
+            const long long z = site0 / nx, x0 = site0 - z * nx;
+            return std::make_tuple(e >> 24, x0 / (2 * kTileM), z, x0);
+        };
+        std::stable_sort(pure.begin(), pure.end(), [&](int x, int y) { return key(x) < key(y); });
+    } else {
+        std::stable_sort(pure.begin(), pure.end(), [](int x, int y) { return (x >> 24) < (y >> 24); });
+    }
     if (pair) {
         // consecutive single-class tiles of the same class form a pair; a
         // tile left alone in its class runs on the CUDA-core kernel
@@ -1040,10 +1155,14 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
     t->n_pure = pair ? (int)pure.size() / 2 : (int)pure.size();
     t->n_mixed = (int)mixed.size();
     t->stages = stages;
-    t->smem = pair ? smem_bytes_pair(N4, stages)
+    t->gather = gather;
+    t->gtaps = gtaps;
+    t->tmG_ptr[0] = t->tmG_ptr[1] = nullptr;
+    t->smem = pair ? smem_bytes_pair(N4, stages, gather)
                    : (mode == 4 ? tc_fp8_smem_bytes(N4, stages)
                                 : (mode == 6 ? tc_fp8x_smem_bytes(N4, stages)
-                                             : (tf32 ? tc_tf32_smem_bytes(N4, stages) : smem_bytes(N4, mode, stages))));
+                                             : (tf32 ? tc_tf32_smem_bytes(N4, stages)
+                                                     : smem_bytes(N4, mode, stages, gather))));
     return RTLB_OK;
 }
 
@@ -1055,7 +1174,21 @@ rtlb_status tc_step(rtlb_ctx *c, const StepParams &p, cudaStream_t s)
         return RTLB_E_STATE;
     }
     const int which = (p.S == c->S[0]) ? 0 : 1;
-    if (!t->tmS_ready[which] || t->tmS_ptr[which] != p.S) {
+    const bool gather = p.taps_o != nullptr;
+    if (gather) {
+        if (!t->gather) {
+            c->err = "this tensor-core form has no gather (bilinear) load";
+            return RTLB_E_STATE;
+        }
+        if (t->tmG_ptr[which] != p.S) {
+            if (!encode_gather_map(&t->tmG[which], p.S, c->nx, c->nz, c->n)) {
+                c->err = "tensor map encoding for the gather windows failed";
+                return RTLB_E_CUDA;
+            }
+            t->tmG_ptr[which] = p.S;
+        }
+    }
+    if (!gather && (!t->tmS_ready[which] || t->tmS_ptr[which] != p.S)) {
         if (!encode_state_map(&t->tmS[which], p.S, c->nsites(), c->n)) {
             c->err = "tensor map encoding for the state failed";
             return RTLB_E_CUDA;
@@ -1079,6 +1212,7 @@ rtlb_status tc_step(rtlb_ctx *c, const StepParams &p, cudaStream_t s)
         tp.err = t->d_err;
         tp.stall = t->stall_next;
         t->stall_next = 0;
+        if (gather) tp.P = p.S;
         cudaError_t e = cudaSuccess;
         if (t->mode == 4) {
             e = launch_step_tc_fp8(t->tmS[which], t->tmZhi, tp, t->d_sfb, t->N4, t->stages, t->n_phase,
@@ -1091,19 +1225,22 @@ rtlb_status tc_step(rtlb_ctx *c, const StepParams &p, cudaStream_t s)
                                     std::min(t->sm_count, t->n_pure), s);
         } else if (t->pair) {
             const int grid = 2 * std::min(t->sm_count / 2, t->n_pure);
-            e = cudaFuncSetAttribute(k_step_tc_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem);
+            auto kern = gather ? k_step_tc_pair<true> : k_step_tc_pair<false>;
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem);
             if (e == cudaSuccess)
-                k_step_tc_pair<<<grid, kThreads, t->smem, s>>>(t->tmS[which], t->tmZhi, t->tmZlo, tp, t->N4, t->stages);
+                kern<<<grid, kThreads, t->smem, s>>>(gather ? t->tmG[which] : t->tmS[which], t->tmZhi, t->tmZlo, tp,
+                                                     t->N4, t->stages, t->gtaps);
         } else {
             const int grid = std::min(t->sm_count, t->n_pure);
             auto launch = [&](auto kern) {
                 e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem);
                 if (e == cudaSuccess)
-                    kern<<<grid, kThreads, t->smem, s>>>(t->tmS[which], t->tmZhi, t->tmZlo, tp, t->N4, t->stages);
+                    kern<<<grid, kThreads, t->smem, s>>>(gather ? t->tmG[which] : t->tmS[which], t->tmZhi, t->tmZlo, tp,
+                                                         t->N4, t->stages, t->gtaps);
             };
-            if (t->mode == 3) launch(k_step_tc<3>);
-            else if (t->mode == 2) launch(k_step_tc<2>);
-            else launch(k_step_tc<1>);
+            if (t->mode == 3) launch(gather ? k_step_tc<3, true> : k_step_tc<3, false>);
+            else if (t->mode == 2) launch(gather ? k_step_tc<2, true> : k_step_tc<2, false>);
+            else launch(gather ? k_step_tc<1, true> : k_step_tc<1, false>);
         }
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) {
@@ -1203,6 +1340,21 @@ void tc_mixed_list(const rtlb_ctx *c, const int **list, int *count)
     const TcState *t = static_cast<const TcState *>(c->tc);
     *list = t ? t->d_mixed : nullptr;
     *count = t ? t->n_mixed : 0;
+}
+
+bool tc_gather(const rtlb_ctx *c)
+{
+    const TcState *t = c ? static_cast<const TcState *>(c->tc) : nullptr;
+    return t && t->gather;
+}
+
+bool tc_form(const rtlb_ctx *c, int *pair, int *stages)
+{
+    const TcState *t = c ? static_cast<const TcState *>(c->tc) : nullptr;
+    if (!t || (!t->d_Zhi && !t->d_Z8 && !t->d_Zt_hi)) return false;
+    *pair = t->pair ? 1 : 0;
+    *stages = t->stages;
+    return true;
 }
 
 int tc_mixed_tiles(const rtlb_ctx *c)

@@ -26,6 +26,13 @@ rtlb_status tc_check_error(rtlb_ctx *c, cudaStream_t s);
 // tables exist, RTLB_E_UNSUPPORTED for the FP8 kernel.
 rtlb_status tc_arm_stall(rtlb_ctx *c);
 int tc_mixed_tiles(const rtlb_ctx *c);
+// True when the prepared form gathers bilinear streaming while loading (the
+// bf16, bf16x2 and bf16x3 forms with nx % 128 == 0, n % 16 == 0 and room for
+// four staging slots: n in {16, 32}): tc_step then takes StepParams with taps
+// (S = the previous step's P).
+bool tc_gather(const rtlb_ctx *c);
+// Pair form and stage count of the prepared tensor-core form (false when none).
+bool tc_form(const rtlb_ctx *c, int *pair, int *stages);
 void tc_release(rtlb_ctx *c);
 
 // Tensor-core reverse step of the adjoint (adj_tc.cu), 4n in {32, 64, 128}: reads

@@ -4,6 +4,7 @@
 #pragma once
 #include <cuda_fp8.h>
 
+#include "step_common.cuh"
 #include "tc_ptx.cuh"
 
 namespace rtlb {
@@ -23,7 +24,25 @@ constexpr int kDirsPerStage = 8;                    // directions per state chun
 constexpr int kStageBytes = kDirsPerStage * kTileM * 16;
 constexpr int kHalfSites = 64;                      // sites per TMA box row (256 floats)
 constexpr int kSmemLimit = 232448;                  // max dynamic smem per block
+// gather form (bilinear streaming): a staging slot holds four directions, each
+// the window of the previous step's P that a 128-site row tile's taps read --
+// two lattice rows of 129 sites, copied as one TMA box of {2 sites x 4 floats,
+// 65 site pairs, 2 rows} from an even site (130 sites), at a 128-byte aligned
+// pitch.  Measured at 2048^2, n = 32: 1.41 ms per step against 1.75 ms for
+// three boxes of 43 sites x 2 rows per direction.
+constexpr int kGatherDirs = 4;
+constexpr int kGatherCols = kTileM + 2;                     // 130 sites from the even site at or below the first
+constexpr uint32_t kGatherBoxBytes = 2u * kGatherCols * 16u;
+constexpr uint32_t kGatherDirBytes = (kGatherBoxBytes + 127u) & ~127u;
+constexpr uint32_t kGatherStageBytes = kGatherDirs * kGatherDirBytes;
+constexpr uint32_t kGatherStageTx = kGatherDirs * kGatherBoxBytes;   // bytes the TMA delivers per slot
 
+// Byte offset of window row `row`, column `col` (0..128 from the first site
+// the taps read, which sits `odd` sites after the box's even first site).
+__device__ __forceinline__ uint32_t gather_window_offset(int row, int col, int odd)
+{
+    return (uint32_t)row * (kGatherCols * 16u) + (uint32_t)(col + odd) * 16u;
+}
 
 // Arguments of the tensor-core step kernels.
 struct TcParams {
@@ -41,7 +60,35 @@ struct TcParams {
     // its first staging slot unissued (nothing is then in flight for it), so
     // its converters' wait runs out and the launch reports a timeout
     int stall = 0;
+    // gather form only: the previous step's P (direction-major, read at the
+    // lattice edge, where taps take the ghost rule)
+    const float *P = nullptr;
 };
+
+// Bilinear taps of every direction for the gather form, passed as a kernel
+// parameter (__grid_constant__) so that the warp-uniform reads hit the
+// constant cache: direction d reads P at (x - n0x[d] - bx, z - n0z[d] - bz)
+// with weight w[d][bx + 2 bz] (the tap order of Eq. 34's stencil product).
+constexpr int kTcMaxDirs = 64;
+struct GatherTaps {
+    float4 w[kTcMaxDirs];
+    int8_t n0x[kTcMaxDirs], n0z[kTcMaxDirs];
+    int reach_x = 0, reach_z = 0;   // largest |tap offset| over the directions, per axis
+};
+
+// Whether the window values serve every tap of the row tile starting at
+// (x0, z) as they are: taps inside the lattice, or beyond a vacuum side,
+// whose ghost value (zero) is what the TMA fills outside the lattice -- a
+// source beyond two sides takes the top / bottom side's rule, and a tile
+// within reach of any other side fails the test.  Uniform over the CTA.
+__device__ __forceinline__ bool gather_interior_tile(const GatherTaps &gt, int bcbits, int nx, int nz, int x0, int z)
+{
+    const bool left = bc_of(bcbits, RTLB_SIDE_LEFT) != RTLB_BC_VACUUM && x0 < gt.reach_x;
+    const bool right = bc_of(bcbits, RTLB_SIDE_RIGHT) != RTLB_BC_VACUUM && x0 + kTileM - 1 + gt.reach_x >= nx;
+    const bool bottom = bc_of(bcbits, RTLB_SIDE_BOTTOM) != RTLB_BC_VACUUM && z < gt.reach_z;
+    const bool top = bc_of(bcbits, RTLB_SIDE_TOP) != RTLB_BC_VACUUM && z + gt.reach_z >= nz;
+    return !(left || right || bottom || top);
+}
 
 enum ErrCode { kErrTimeoutProducer = 1, kErrTimeoutConverter = 2, kErrTimeoutMma = 4, kErrTimeoutEpilogue = 8 };
 
@@ -150,6 +197,168 @@ __device__ __forceinline__ bool convert_tile(const float4 cf, const float *fwd, 
         }
     }
     return true;
+}
+
+struct GatherGeom {
+    int nx, nz, bcbits;
+    const float4 *P, *inflow;   // the previous step's P; inflow [4][n]
+};
+
+// Gather form of convert_tile (bilinear streaming, Eq. 33-38).  The step's
+// input is the previous step's post-collision field P; S~ of (site, d) is the
+// four-tap sum of P, formed here from the two-row window that the producer
+// staged for direction d (tap (bx, bz) at window row 1 - bz, column
+// r + 1 - bx) -- the same sum, in the same order, as the two-pass form's
+// gather kernel.  Outside the lattice the TMA fills zeros, the ghost value of
+// a vacuum side; in a tile within reach of another side (`edge`) the group
+// first writes the ghost values (inflow, or the periodic image) into the
+// window's entries outside the lattice and meets on fill_bar[grp].  The taps
+// come from `gt` (forward taps: n0 and n0 + 1 per axis).  Each 64-wide K chunk
+// c (16 directions) comes in four slots of four directions; group grp takes
+// slots 4c + 2 grp and 4c + 2 grp + 1 (its directions 16c + 8 grp ... + 7, the
+// same as in convert_tile), so the A rows it writes are the same.  Requires
+// n % 16 == 0 and tiles that are row segments (nx % 128 == 0); x, z: the
+// coordinates of this thread's site; fq: this group's count of fill_bar
+// phases.
+template <bool ALO>
+__device__ __forceinline__ bool convert_tile_gather(const float4 cf, const float *fwd, int r, int lane, int grp, int n,
+                                                    int stages, uint32_t &gq, int i, uint32_t acc, uint8_t *sA,
+                                                    uint8_t *sAlo, uint8_t *sStage, uint64_t *st_full,
+                                                    uint64_t *st_empty, uint64_t *a_empty, uint64_t *fill_bar,
+                                                    uint32_t &fq, uint32_t a_chunk, const GatherGeom g,
+                                                    const GatherTaps &gt, bool edge, int x, int z,
+                                                    volatile int *abort_flag, int *err)
+{
+    const int C = n / 16;
+    const int ring = stages / 2;
+    const size_t nsites = (size_t)g.nx * g.nz;
+    for (int c = 0; c < C; ++c) {
+        const int d_beg = 16 * c + 8 * grp;
+        uint4 packed[4], packed_lo[4];
+        float fw[8];
+#pragma unroll
+        for (int k = 0; k < 8; k += 4) {
+            const float4 f = __ldg(reinterpret_cast<const float4 *>(fwd + d_beg + k));
+            fw[k] = f.x;
+            fw[k + 1] = f.y;
+            fw[k + 2] = f.z;
+            fw[k + 3] = f.w;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t local = gq++;
+            const int s = ring_slot(grp, local, ring);
+            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&st_full[s]), (local / (uint32_t)ring) & 1, abort_flag, err,
+                                                   kErrTimeoutConverter)))
+                return false;
+            uint8_t *stg = sStage + (size_t)s * kGatherStageBytes;
+            if (edge) {
+                // ghost values into the four windows' entries outside the lattice
+                const int x0 = x - r;
+#pragma unroll 1
+                for (int e = 0; e < kGatherDirs; ++e) {
+                    const int d = d_beg + 4 * h + e;
+                    const int xs0 = x0 - gt.n0x[d] - 1, xe = xs0 - (xs0 & 1), zs0 = z - gt.n0z[d] - 1;
+                    float4 *win = reinterpret_cast<float4 *>(stg + e * kGatherDirBytes);
+#pragma unroll 1
+                    for (int idx = r; idx < 2 * kGatherCols; idx += kTileM) {
+                        const int row = idx / kGatherCols, xs = xe + idx - row * kGatherCols, zs = zs0 + row;
+                        if (xs < 0 || xs >= g.nx || zs < 0 || zs >= g.nz)
+                            win[idx] = source_or_ghost(g.P + (size_t)d * nsites, g.inflow, g.bcbits, g.nx, g.nz, n, d, xs,
+                                                       zs);
+                    }
+                }
+                fence_proxy_async();                        // before the next TMA into this slot
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&fill_bar[grp]));
+                if (!__all_sync(0xffffffffu,
+                                mbar_wait(smem_u32(&fill_bar[grp]), (fq++) & 1, abort_flag, err, kErrTimeoutConverter)))
+                    return false;
+            }
+#pragma unroll
+            for (int dp = 0; dp < 2; ++dp) {
+                const int dl = 4 * h + 2 * dp;              // within this group's eight directions
+                float4 v[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int d = d_beg + dl + e;
+                    const float4 w4 = gt.w[d];
+                    const int n0x = gt.n0x[d];
+                    const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+                    const uint8_t *win = stg + (2 * dp + e) * kGatherDirBytes;
+                    const int odd = (x - r - n0x - 1) & 1;   // the window's first site is odd
+                    // tap (bx, bz): window row 1 - bz, column r + 1 - bx; the
+                    // loads are unconditional (in the window), the sums skip
+                    // zero weights
+                    float4 tv[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        tv[k] = *reinterpret_cast<const float4 *>(win +
+                                                                  gather_window_offset(1 - (k >> 1), r + 1 - (k & 1), odd));
+                    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (w[k] != 0.f) axpy4(a, w[k], tv[k]);
+                    v[e] = a;
+                }
+                v[0].x += cf.w;                             // emission (I only)
+                v[1].x += cf.w;
+                const float sv[8] = {v[0].x, v[0].y, v[0].z, v[0].w, v[1].x, v[1].y, v[1].z, v[1].w};
+                const float g0 = fmaf(cf.z, fw[dl], cf.y), g1 = fmaf(cf.z, fw[dl + 1], cf.y);
+                float init[8], bs[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    init[k] = fmaf(cf.x, sv[k], (k < 4 ? g0 : g1) * sv[k]);
+                    bs[k] = cf.z * sv[k];
+                }
+                tmem_st8(acc + 4 * (d_beg + dl), init);
+                uint4 hi;
+                hi.x = pack_bf16(bs[0], bs[1]);
+                hi.y = pack_bf16(bs[2], bs[3]);
+                hi.z = pack_bf16(bs[4], bs[5]);
+                hi.w = pack_bf16(bs[6], bs[7]);
+                packed[dl >> 1] = hi;
+                if (ALO) {
+                    const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&hi);
+                    uint32_t *lw = reinterpret_cast<uint32_t *>(&packed_lo[dl >> 1]);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float2 f = __bfloat1622float2(h2[k]);
+                        lw[k] = pack_bf16(bs[2 * k] - f.x, bs[2 * k + 1] - f.y);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&st_empty[s]));
+        }
+        if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&a_empty[c]), (i & 1) ^ 1, abort_flag, err, kErrTimeoutConverter)))
+            return false;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t gi = 4u * (uint32_t)grp + (uint32_t)k;
+            const uint32_t off = c * a_chunk + r * 128u + ((gi ^ (uint32_t)(r & 7)) << 4);
+            *reinterpret_cast<uint4 *>(sA + off) = packed[k];
+            if (ALO) *reinterpret_cast<uint4 *>(sAlo + off) = packed_lo[k];
+        }
+    }
+    return true;
+}
+
+// Producer side of the gather form: issues the windows of staging slot j of
+// the tile whose first site is site0 -- directions 4j ... 4j + 3, one box
+// each, from the even site at or below the first site the taps read (x0 is
+// even: nx % 128 == 0).  (An L2 prefetch of the windows a few slots ahead
+// measured slower at every distance tried, 4 to 12 slots.)
+__device__ __forceinline__ void gather_slot_loads(const CUtensorMap *tm, const GatherTaps &gt, int nx, int site0, int j,
+                                                  uint32_t dst, uint32_t bar)
+{
+    const int z = site0 / nx, x0 = site0 - z * nx;
+#pragma unroll
+    for (int e = 0; e < kGatherDirs; ++e) {
+        const int d = kGatherDirs * j + e;
+        const int xs = x0 - gt.n0x[d] - 1;
+        tma_load_4d(dst + e * kGatherDirBytes, tm, bar, 0, (xs - (xs & 1)) / 2, z - gt.n0z[d] - 1, d);
+    }
 }
 
 // UE8M0 exponent of a block whose largest |value| is amax (float32): the

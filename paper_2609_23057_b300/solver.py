@@ -273,6 +273,21 @@ class Solver:
     def steps_done(self) -> int:
         return int(lib().rtlb_steps_done(self._ctx))
 
+    def form(self) -> dict:
+        """How the steps run (rtlb_get_form): tensor_core, cta_pair,
+        gather_form, mixed_tiles, stages."""
+        f = _lib.Form()
+        self._check(lib().rtlb_get_form(self._ctx, C.byref(f)))
+        return {k: int(getattr(f, k)) for k, _ in f._fields_}
+
+    @property
+    def gather_form(self) -> bool:
+        return bool(self.form()["gather_form"])
+
+    @property
+    def mixed_tiles(self) -> int:
+        return self.form()["mixed_tiles"]
+
 
 def solver_for(w, precision: str = "fp32") -> Solver:
     """Solver set up for a workloads.Workload (medium, tables, boundaries)."""

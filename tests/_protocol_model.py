@@ -806,7 +806,7 @@ def table_step(masks, stages, seed, gate_done=True, slow=None):
     return M.steps
 
 
-def pair_step(keys, stages, seed, n=64, gate_acc_empty=True, slow=None):
+def pair_step(keys, stages, seed, n=64, gate_acc_empty=True, slow=None, gather=False, gather_ring_flaw=False):
     """The CTA-pair kernel (cta_group::2, bf16 state operand and split table):
     each entry of `keys` is one pair of tiles (one per CTA) of the same table
     key.  Per CTA: a producer (its half of the table and its own tile's
@@ -818,7 +818,12 @@ def pair_step(keys, stages, seed, n=64, gate_acc_empty=True, slow=None):
     odd producer forwards the completion of its table half to the even z_full
     (count 2).  gate_acc_empty=False lets the converters write a tile's
     accumulator init without waiting for the epilogue of two tiles before (a
-    planted flaw)."""
+    planted flaw).  gather: the bilinear gather form, whose staging slots hold
+    four directions each (n / 4 per tile); slot j goes to group (j >> 1) & 1,
+    and group grp takes slots 4c + 2 grp and 4c + 2 grp + 1 of chunk c
+    (together its eight directions of the chunk).  gather_ring_flaw: the
+    producer keeps the eight-direction form's group of a slot (j & 1), a
+    planted flaw."""
     M = Machine(seed, slow)
     T = len(keys)
     G, C, ring = _groups(n), _chunks(n), stages // 2
@@ -858,8 +863,8 @@ def pair_step(keys, stages, seed, n=64, gate_acc_empty=True, slow=None):
                     z_full[0].arrive()                      # forward to the even CTA
                 zl += 1
                 prev = key
-            for j in range(G):
-                gr = j & 1
+            for j in range(n // 4 if gather else G):
+                gr = (j >> 1) & 1 if gather and not gather_ring_flaw else j & 1
                 local = gq[gr]
                 gq[gr] += 1
                 s = gr * ring + local % ring
@@ -879,18 +884,21 @@ def pair_step(keys, stages, seed, n=64, gate_acc_empty=True, slow=None):
             if gate_acc_empty:
                 yield Wait(acc_empty[(r, b)], (i >> 1) - 1, who)
             for c in range(C):
-                j = 2 * c + grp
-                local = gq
-                gq += 1
-                s = grp * ring + local % ring
-                yield Wait(st_full[(r, s)], local // ring, who)
-                if stage[(r, s)] != (i, j):
-                    raise ProtocolError(f"{who} tile {i} slot {j}: staging holds {stage[(r, s)]}")
-                cell = acc.get((r, b, j, q))
-                if cell is not None and cell[0] != "free":
-                    raise ProtocolError(f"{who} tile {i}: accumulator {b} slot {j} still {cell[0]}")
-                acc[(r, b, j, q)] = ["init", i, 0]
-                st_empty[(r, s)].arrive()
+                j = 2 * c + grp                             # eight-direction group of the accumulator
+                for h in range(2 if gather else 1):
+                    sj = 4 * c + 2 * grp + h if gather else j
+                    local = gq
+                    gq += 1
+                    s = grp * ring + local % ring
+                    yield Wait(st_full[(r, s)], local // ring, who)
+                    if stage[(r, s)] != (i, sj):
+                        raise ProtocolError(f"{who} tile {i} slot {sj}: staging holds {stage[(r, s)]}")
+                    if h == 0:
+                        cell = acc.get((r, b, j, q))
+                        if cell is not None and cell[0] != "free":
+                            raise ProtocolError(f"{who} tile {i}: accumulator {b} slot {j} still {cell[0]}")
+                        acc[(r, b, j, q)] = ["init", i, 0]
+                    st_empty[(r, s)].arrive()
                 yield Wait(a_empty[(r, c)], i - 1, who)
                 A[(r, c, grp, q)] = i
             (t_ready[b] if r == 0 else t_local[b]).arrive()

@@ -164,6 +164,79 @@ def test_full_size_sampled_sites(torch_cuda, orc, prec):
             assert abs_err_dop(g, r) < 1e-5, (z, x)
 
 
+def _settle_each_step(s, w):
+    """Re-set one boundary to its own kind: the library then ends the
+    deferred streaming of the last step with the gather kernel, so the next
+    step loads a state, as in the two-pass form."""
+    inflow = None if w.inflow is None else w.inflow[0]
+    s.set_boundary(0, w.bc[0], inflow if w.bc[0] == 2 else None)
+
+
+@pytest.mark.parametrize("prec,nzen,naz,mixed,bc", [("bf16", 4, 4, False, (2, 0, 1, 1)),
+                                                     ("bf16x2", 4, 8, True, (2, 0, 1, 1)),
+                                                     ("bf16x3", 4, 8, False, (2, 2, 0, 0)),
+                                                     ("bf16", 4, 8, True, (0, 0, 0, 0))])
+def test_gather_form_equals_two_pass(torch_cuda, prec, nzen, naz, mixed, bc):
+    """The gather form (each step gathers the previous step's P while
+    loading: the tensor-core bf16 forms at n in {16, 32} with nx % 128 == 0)
+    against the two-pass form (collision pass, then the gather kernel) on the
+    same inputs: identical bits for the state, the readouts, the residual and
+    a following adjoint.  Boundaries: top inflow, periodic x, vacuum bottom
+    (ghost values written into the staged windows), inflow top and bottom,
+    all vacuum (the TMA's zero fill); `mixed` puts a class boundary inside
+    tiles (those tiles run on the CUDA-core kernel, also gathering)."""
+    from paper_2609_23057_b300.solver import solver_for
+    w = W.random_medium(256, 7, nzen, naz, seed=nzen * naz + 5, bc=bc, n_phase=2, steps=5)
+    if mixed:
+        w.phase_index = ((np.arange(w.nx)[None, :] >= 100) * np.ones((w.nz, 1))).astype(np.uint8)
+    else:
+        w.phase_index = (np.arange(w.nz)[:, None] % 2 * np.ones((1, w.nx))).astype(np.uint8)
+    w.scheme, w.plane = "bilinear", "xz"
+    S0 = torch_cuda.from_numpy(W.random_state(w.nz, w.nx, w.n, seed=2, dtype=np.float32)).cuda()
+    seed = torch_cuda.from_numpy(np.random.default_rng(8).standard_normal((w.nx, w.n, 4)).astype(np.float32)).cuda()
+    res = []
+    for settle in (False, True):
+        s = solver_for(w, prec)
+        assert s.gather_form
+        assert (s.mixed_tiles > 0) == mixed
+        s.set_state(S0)
+        for _ in range(w.steps):
+            s.step(1)
+            if settle:
+                _settle_each_step(s, w)
+        st = s.get_state().cpu().numpy()
+        top = s.radiance_out(0).cpu().numpy()
+        dop = s.dop_out(0).cpu().numpy()
+        r = s.last_residual()
+        tot = s.total_intensity()
+        s.step(2)
+        st2 = s.get_state().cpu().numpy()
+        gt, ga, gZ, _ = s.adjoint(3, seed, checkpoint_every=2)
+        res.append((st, top, dop, r, tot, st2, gt.cpu().numpy(), ga.cpu().numpy(), gZ))
+        s.close()
+    a, b = res
+    for k in range(len(a)):
+        assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), k
+
+
+def test_run_to_steady_gather_form(torch_cuda, orc):
+    """run_to_steady through the gather form (residual between two gathered
+    states, bf16x3 at n = 16) against the oracle: the same step count within
+    one, the final state within the form's bound."""
+    from paper_2609_23057_b300.solver import solver_for
+    w = W.random_medium(128, 12, 4, 4, seed=77, bc=(2, 0, 1, 1), n_phase=1, steps=1)
+    w.scheme, w.plane = "bilinear", "xz"
+    P = oracle_problem(orc, w)
+    s = solver_for(w, "bf16x3")
+    assert s.gather_form
+    taken, r, ok = s.run_to_steady(1e-6, 2000, check_every=1)
+    got = s.get_state().cpu().numpy().astype(np.float64)
+    s.close()
+    ref, rtaken, _ = P.run_to_steady(P.zero_state(), 1e-6, 2000)
+    assert ok and abs(taken - rtaken) <= 0.02 * rtaken + 1
+    assert rel_err_I(got, ref) < TOL_TC["bf16x3"]
+
+
 def test_batch_rejects_bilinear_channels(torch_cuda):
     from paper_2609_23057_b300 import _lib
     from paper_2609_23057_b300.solver import Batch, solver_for

@@ -73,6 +73,26 @@ def test_cta_pair_step_is_race_free(stages):
             P.pair_step([0, 0, 1, 1, 0, 0], stages, seed, slow={slow: 0.01})
 
 
+@pytest.mark.parametrize("stages", [2, 4])
+def test_cta_pair_gather_form_is_race_free(stages):
+    """The CTA-pair kernel in the bilinear gather form: four-direction
+    staging slots, two per converter group and chunk; also with one role
+    lagging far behind."""
+    for seed in range(10):
+        P.pair_step([0, 0, 0, 1, 1, 0, 0], stages, seed, gather=True)
+    for slow in ("epi0", "conv1", "producer1", "mma"):
+        for seed in range(4):
+            P.pair_step([0, 0, 1, 1, 0], stages, seed, slow={slow: 0.01}, gather=True)
+
+
+def test_cta_pair_gather_model_sees_wrong_ring():
+    """A producer that hands the gather form's slots to the groups of the
+    eight-direction form (j & 1) feeds a group slots of the other group's
+    directions: the model must report it."""
+    with pytest.raises(P.ProtocolError):
+        P.pair_step([0, 0, 1], 2, 0, gather=True, gather_ring_flaw=True)
+
+
 def test_cta_pair_model_sees_unreleased_accumulator():
     """Converters that write a tile's accumulator init before the epilogue
     of two tiles earlier has read that buffer: with the epilogue lagging, the
