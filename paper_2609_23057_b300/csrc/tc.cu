@@ -74,8 +74,8 @@ struct TcState {
     CUtensorMap tmZhi{}, tmZlo{}, tmS[2]{};
     bool tmS_ready[2] = {false, false};
     const float *tmS_ptr[2] = {nullptr, nullptr};
-    // gather form (bilinear streaming on CTA pairs): window maps of both state
-    // buffers; tiles ordered down 256-site column strips
+    // gather form (bilinear streaming, single-CTA bf16 forms): window maps of
+    // both state buffers, the taps; tiles ordered down 256-site column strips
     bool gather = false;
     GatherTaps gtaps{};
     CUtensorMap tmG[2]{};
@@ -410,15 +410,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 // even CTA with a single remote (cluster-scope release) arrive, which keeps
 // that microsecond-long release off the converters' path.  Its producer
 // forwards the completion of its half of the table the same way.
-template <bool GATHER>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     k_step_tc_pair(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ CUtensorMap tmZhi,
-                   const __grid_constant__ CUtensorMap tmZlo, TcParams p, int N4, int stages,
-                   const __grid_constant__ GatherTaps gt)
+                   const __grid_constant__ CUtensorMap tmZlo, TcParams p, int N4, int stages)
 {
-    // GATHER: tmS is the windows' map (see encode_gather_map), the staging
-    // slots hold four directions' windows and the converters form S~ from them
-    constexpr uint32_t stage_bytes = GATHER ? kGatherStageBytes : (uint32_t)kStageBytes;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t rank = cluster_rank();
@@ -435,7 +430,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     uint8_t *sZlo = sZ + C * z_chunk;
     uint8_t *sA = sZlo + C * z_chunk;
     uint8_t *sStage = sA + C * a_chunk;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sStage + (size_t)stages * stage_bytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sStage + (size_t)stages * kStageBytes);
     uint64_t *st_full = bars;
     uint64_t *st_empty = st_full + stages;
     uint64_t *a_empty = st_empty + stages;     // [C]   multicast commit from the even CTA
@@ -446,8 +441,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     uint64_t *drain = z_full + 1;              // [1]   multicast commit
     uint64_t *z_free = drain + 1;              // [1]   multicast commit: the resident table is no longer read
     uint64_t *t_local = z_free + 1;            // [2]   odd CTA: its 4 converter warps, forwarded to the even CTA
-    uint64_t *fill_bar = t_local + 2;          // [2]   gather form: a converter group's ghost fill done
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fill_bar + 2);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(t_local + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     int8_t *s_cx = reinterpret_cast<int8_t *>(tmem_slot + 2);
     int8_t *s_cz = s_cx + kMaxDirs;
@@ -470,8 +464,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         mbar_init(smem_u32(z_full), leader ? 2 : 1);
         mbar_init(smem_u32(drain), 1);
         mbar_init(smem_u32(z_free), 1);
-        mbar_init(smem_u32(&fill_bar[0]), 4);
-        mbar_init(smem_u32(&fill_bar[1]), 4);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -520,10 +512,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     ++zl;
                     prev_cls = cls;
                 }
-                const int nslots = GATHER ? n / kGatherDirs : groups;
-                for (int j = 0; j < nslots && ok; ++j) {
-                    // gather form: slots 4c + 2 grp + {0, 1} go to group grp
-                    const int gr = GATHER ? (j >> 1) & 1 : j & 1;
+                for (int j = 0; j < groups && ok; ++j) {
+                    const int gr = j & 1;
                     const uint32_t local = gq[gr]++;
                     const int s = ring_slot(gr, local, stages / 2);
                     ok = mbar_wait(smem_u32(&st_empty[s]), ((local / (uint32_t)(stages / 2)) & 1) ^ 1, abort_flag, p.err,
@@ -531,13 +521,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     if (!ok) break;
                     if (stall && i == 0 && j == 0) continue;   // test hook: this load is never issued
                     const uint32_t fb = smem_u32(&st_full[s]);
-                    if (GATHER) {
-                        // direction d's window: rows z - n0z - 1 and z - n0z, sites
-                        // x0 - n0x - 1 ... x0 - n0x + 127 (zero outside the lattice)
-                        mbar_expect_tx(fb, kGatherStageTx);
-                        gather_slot_loads(&tmS, gt, p.nx, tile * kTileM, j, smem_u32(sStage + (size_t)s * stage_bytes), fb);
-                        continue;
-                    }
                     mbar_expect_tx(fb, kStageBytes);
                     for (int h = 0; h < kTileM / kHalfSites; ++h)
                         tma_load_2d(smem_u32(sStage + (size_t)s * kStageBytes + h * (kStageBytes / 2)), &tmS, fb,
@@ -620,7 +603,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         const int grp = (warp - kConvWarp0) >> 2;
         const int r = q * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        uint32_t gq = 0, fq = 0;   // staging slots consumed; ghost fills (gather form)
+        uint32_t gq = 0;
         bool ok = true;
         // coefficients and classes fetched a tile ahead (see load_coef)
         float4 cf_next = T > 0 ? load_coef(p.coef, my_tile(0) * kTileM + r, nsites) : float4{};
@@ -638,18 +621,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             if (!ok) break;
             tc_fence_after();
             const uint32_t acc = tmem + lane_base + (uint32_t)(b * N4);
-            if (GATHER) {
-                const int site = my_tile(i) * kTileM + r, z = site / p.nx, x = site - z * p.nx;
-                const GatherGeom g{p.nx, p.nz, p.bcbits, reinterpret_cast<const float4 *>(p.P),
-                                   reinterpret_cast<const float4 *>(p.inflow)};
-                ok = convert_tile_gather<false>(cf, p.fwd + (size_t)cls * n, r, lane, grp, n, stages, gq, i, acc, sA, sA,
-                                                sStage, st_full, st_empty, a_empty, fill_bar, fq, a_chunk, g, gt,
-                                                !gather_interior_tile(gt, p.bcbits, p.nx, p.nz, x - r, z), x, z,
-                                                abort_flag, p.err);
-            } else {
-                ok = convert_tile<false>(cf, p.fwd + (size_t)cls * n, r, lane, grp, n, groups, stages, gq, i, acc, sA, sA,
-                                         sStage, st_full, st_empty, a_empty, a_chunk, abort_flag, p.err);
-            }
+            ok = convert_tile<false>(cf, p.fwd + (size_t)cls * n, r, lane, grp, n, groups, stages, gq, i, acc, sA, sA,
+                                     sStage, st_full, st_empty, a_empty, a_chunk, abort_flag, p.err);
             if (!ok) break;
             tmem_wait_st();
             fence_proxy_async();
@@ -857,12 +830,11 @@ size_t smem_bytes(int N4, int mode, int stages, bool gather = false)
     return b + 1024;  // alignment slack
 }
 
-size_t smem_bytes_pair(int N4, int stages, bool gather = false)
+size_t smem_bytes_pair(int N4, int stages)
 {
     const int C = (N4 + 63) / 64;
-    size_t b = (size_t)C * (N4 / 2) * 128 * 2 + (size_t)C * kTileM * 128 +
-               (size_t)stages * (gather ? kGatherStageBytes : (uint32_t)kStageBytes) +
-               (size_t)(2 * stages + C + 13) * 8 + 16 + 2 * kMaxDirs;
+    size_t b = (size_t)C * (N4 / 2) * 128 * 2 + (size_t)C * kTileM * 128 + (size_t)stages * kStageBytes +
+               (size_t)(2 * stages + C + 11) * 8 + 16 + 2 * kMaxDirs;
     return b + 1024;
 }
 
@@ -883,7 +855,7 @@ int mode_of(int precision)
 int fit_stages(int N4, int mode, bool pair, bool gather = false)
 {
     for (int st = RTLB_TC_MAX_STAGES & ~1; st >= 2; st -= 2)
-        if ((pair ? smem_bytes_pair(N4, st, gather)
+        if ((pair ? (gather ? ~(size_t)0 : smem_bytes_pair(N4, st))   // no gather form on CTA pairs
                   : (mode == 4 ? tc_fp8_smem_bytes(N4, st)
                                : (mode == 5 ? tc_tf32_smem_bytes(N4, st)
                                             : (mode == 6 ? tc_fp8x_smem_bytes(N4, st)
@@ -1158,7 +1130,7 @@ rtlb_status tc_prepare(rtlb_ctx *c, const double *tables, int n_phase, const uin
     t->gather = gather;
     t->gtaps = gtaps;
     t->tmG_ptr[0] = t->tmG_ptr[1] = nullptr;
-    t->smem = pair ? smem_bytes_pair(N4, stages, gather)
+    t->smem = pair ? smem_bytes_pair(N4, stages)
                    : (mode == 4 ? tc_fp8_smem_bytes(N4, stages)
                                 : (mode == 6 ? tc_fp8x_smem_bytes(N4, stages)
                                              : (tf32 ? tc_tf32_smem_bytes(N4, stages)
@@ -1225,11 +1197,9 @@ rtlb_status tc_step(rtlb_ctx *c, const StepParams &p, cudaStream_t s)
                                     std::min(t->sm_count, t->n_pure), s);
         } else if (t->pair) {
             const int grid = 2 * std::min(t->sm_count / 2, t->n_pure);
-            auto kern = gather ? k_step_tc_pair<true> : k_step_tc_pair<false>;
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem);
+            e = cudaFuncSetAttribute(k_step_tc_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t->smem);
             if (e == cudaSuccess)
-                kern<<<grid, kThreads, t->smem, s>>>(gather ? t->tmG[which] : t->tmS[which], t->tmZhi, t->tmZlo, tp,
-                                                     t->N4, t->stages, t->gtaps);
+                k_step_tc_pair<<<grid, kThreads, t->smem, s>>>(t->tmS[which], t->tmZhi, t->tmZlo, tp, t->N4, t->stages);
         } else {
             const int grid = std::min(t->sm_count, t->n_pure);
             auto launch = [&](auto kern) {
