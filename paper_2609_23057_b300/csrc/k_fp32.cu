@@ -29,10 +29,10 @@ struct Cfg {
     static constexpr int SITES = SG * TS;                // sites per CTA
     static constexpr int KC = 16;                        // k rows per B chunk
     // S~ tile, two Z^T chunks (the next one is copied in while the current one
-    // is used), four per-site words, the bilinear taps of the gather form
+    // is used), four per-site words; the gather form adds the bilinear taps
     // (n = N4 / 4 directions x 12 words)
-    static constexpr size_t SMEM = (size_t)N4 * SITES * 4 + (size_t)2 * KC * N4 * 4 + (size_t)SITES * 16 +
-                                   (size_t)(N4 / 4) * 48;
+    static constexpr size_t SMEM = (size_t)N4 * SITES * 4 + (size_t)2 * KC * N4 * 4 + (size_t)SITES * 16;
+    static constexpr size_t SMEM_GATHER = SMEM + (size_t)(N4 / 4) * 48;
 };
 
 __device__ __forceinline__ void cp_async16(float *dst, const float *src)
@@ -49,7 +49,10 @@ __device__ __forceinline__ void store_out(const StepParams &p, int site, int x, 
     push_store_xz(p.dir, p.inflow, pack_bc(p.bc), p.S_new, p.nx, p.nz, p.n, site, x, z, d, v);
 }
 
-template <int N4>
+// GATHER: S holds the previous step's P and the tile load gathers S~ from
+// the taps (the mixed tiles of a tensor-core gather form); a template
+// parameter so that the plain step's load loop stays as it is.
+template <int N4, bool GATHER>
 __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
 {
     using C = Cfg<N4>;
@@ -80,7 +83,7 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
     const int nsites_all = p.nx * p.nz;
     const int tid = threadIdx.x;
     if (tid == 0) s_mask = 0u;
-    if (p.taps_o)
+    if (GATHER)
         for (int k = tid; k < 12 * n; k += 256) {
             if (k < 8 * n) s_to[k] = p.taps_o[k];
             else s_tw[k - 8 * n] = p.taps_w[k - 8 * n];
@@ -114,7 +117,7 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
         const int site = site0 + s;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (site < nsites) {
-            if (p.taps_o) {
+            if (GATHER) {
                 const int z = site / p.nx;
                 v = gather_bilinear(load_taps<true>(s_to, s_tw, d), S4 + (size_t)d * nsites_all,
                                     reinterpret_cast<const float4 *>(p.inflow), bcbits, p.nx, p.nz, n, d, site,
@@ -224,6 +227,7 @@ __global__ void __launch_bounds__(256, 2) k_step_fp32_tiled(StepParams p)
 
 // Any n: one thread per (site, outgoing direction); Z^T read through the
 // read-only cache (the whole warp shares one direction and usually one class).
+template <bool GATHER>
 __global__ void __launch_bounds__(128) k_step_fp32_generic(StepParams p)
 {
     const int nsites = p.nx * p.nz;
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(128) k_step_fp32_generic(StepParams p)
     float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
     const int zs = site / p.nx;
     for (int d = 0; d < p.n; ++d) {
-        float4 v = p.taps_o ? gather_bilinear(load_taps(p.taps_o, p.taps_w, d), S4 + (size_t)d * nsites,
+        float4 v = GATHER ? gather_bilinear(load_taps(p.taps_o, p.taps_w, d), S4 + (size_t)d * nsites,
                                               reinterpret_cast<const float4 *>(p.inflow), pack_bc(p.bc), p.nx, p.nz,
                                               p.n, d, site, site - zs * p.nx, zs)
                             : S4[(size_t)d * nsites + site];
@@ -258,14 +262,15 @@ __global__ void __launch_bounds__(128) k_step_fp32_generic(StepParams p)
     store_out(p, site, site - zs * p.nx, zs, o, v);
 }
 
-template <int N4>
+template <int N4, bool GATHER>
 cudaError_t launch_tiled(const StepParams &p, cudaStream_t s)
 {
     using C = Cfg<N4>;
+    constexpr size_t smem = GATHER ? C::SMEM_GATHER : C::SMEM;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_fp32_tiled<N4>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(k_step_fp32_tiled<N4, GATHER>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -277,26 +282,32 @@ cudaError_t launch_tiled(const StepParams &p, cudaStream_t s)
         grid = (p.nx * p.nz + C::SITES - 1) / C::SITES;
     }
     if (grid == 0) return cudaSuccess;
-    k_step_fp32_tiled<N4><<<grid, 256, C::SMEM, s>>>(p);
+    k_step_fp32_tiled<N4, GATHER><<<grid, 256, smem, s>>>(p);
     return cudaGetLastError();
+}
+
+template <bool GATHER>
+cudaError_t launch_fp32(const StepParams &p, cudaStream_t s)
+{
+    switch (4 * p.n) {
+    case 32: return launch_tiled<32, GATHER>(p, s);
+    case 64: return launch_tiled<64, GATHER>(p, s);
+    case 128: return launch_tiled<128, GATHER>(p, s);
+    case 256: return launch_tiled<256, GATHER>(p, s);
+    default: {
+        const int nsites = p.nx * p.nz;
+        dim3 grid((nsites + 127) / 128, p.n);
+        k_step_fp32_generic<GATHER><<<grid, 128, 0, s>>>(p);
+        return cudaGetLastError();
+    }
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_step_fp32(const StepParams &p, cudaStream_t s)
 {
-    switch (4 * p.n) {
-    case 32: return launch_tiled<32>(p, s);
-    case 64: return launch_tiled<64>(p, s);
-    case 128: return launch_tiled<128>(p, s);
-    case 256: return launch_tiled<256>(p, s);
-    default: {
-        const int nsites = p.nx * p.nz;
-        dim3 grid((nsites + 127) / 128, p.n);
-        k_step_fp32_generic<<<grid, 128, 0, s>>>(p);
-        return cudaGetLastError();
-    }
-    }
+    return p.taps_o ? launch_fp32<true>(p, s) : launch_fp32<false>(p, s);
 }
 
 }  // namespace rtlb
