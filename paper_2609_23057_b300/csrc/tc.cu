@@ -721,16 +721,17 @@ bool encode_state_map(CUtensorMap *m, const float *S, size_t nsites, int n)
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Windows of the gather form: 4D view (the 8 floats of a pair of sites, site
-// pair, row z, direction d) of the direction-major state (nx even), boxes of
-// 65 site pairs x 2 rows, zero outside the lattice.
+// Windows of the gather form: 4D view (the floats of kGatherSites sites, site
+// group, row z, direction d) of the direction-major state (nx % 128 == 0),
+// boxes of kGatherCols sites x 2 rows, zero outside the lattice.
 bool encode_gather_map(CUtensorMap *m, const float *S, int nx, int nz, int n)
 {
     auto fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[4] = {8, (cuuint64_t)nx / 2, (cuuint64_t)nz, (cuuint64_t)n};
-    cuuint64_t strides[3] = {32, (cuuint64_t)nx * 16, (cuuint64_t)nx * nz * 16};
-    cuuint32_t box[4] = {8, (cuuint32_t)kGatherCols / 2, 2, 1};
+    cuuint64_t dims[4] = {(cuuint64_t)(4 * kGatherSites), (cuuint64_t)(nx / kGatherSites), (cuuint64_t)nz,
+                          (cuuint64_t)n};
+    cuuint64_t strides[3] = {(cuuint64_t)(16 * kGatherSites), (cuuint64_t)nx * 16, (cuuint64_t)nx * nz * 16};
+    cuuint32_t box[4] = {(cuuint32_t)(4 * kGatherSites), (cuuint32_t)(kGatherCols / kGatherSites), 2, 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(S), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,

@@ -26,22 +26,28 @@ constexpr int kHalfSites = 64;                      // sites per TMA box row (25
 constexpr int kSmemLimit = 232448;                  // max dynamic smem per block
 // gather form (bilinear streaming): a staging slot holds four directions, each
 // the window of the previous step's P that a 128-site row tile's taps read --
-// two lattice rows of 129 sites, copied as one TMA box of {2 sites x 4 floats,
-// 65 site pairs, 2 rows} from an even site (130 sites), at a 128-byte aligned
-// pitch.  Measured at 2048^2, n = 32: 1.41 ms per step against 1.75 ms for
-// three boxes of 43 sites x 2 rows per direction.
+// two lattice rows of 129 sites, copied as one TMA box of {G sites x 4 floats,
+// kGatherCols / G site groups, 2 rows} from the first multiple of G at or
+// below the first tap, at a 128-byte aligned pitch (G =
+// RTLB_TC_GATHER_SITES).  Measured at 2048^2, n = 32 (bf16): 1.337 ms per
+// step with G = 4, 1.368 with G = 2, 1.346 with G = 8, 1.75 ms for three boxes
+// of 43 sites x 2 rows per direction.
+#ifndef RTLB_TC_GATHER_SITES
+#define RTLB_TC_GATHER_SITES 4
+#endif
 constexpr int kGatherDirs = 4;
-constexpr int kGatherCols = kTileM + 2;                     // 130 sites from the even site at or below the first
+constexpr int kGatherSites = RTLB_TC_GATHER_SITES;                 // sites per TMA box row
+constexpr int kGatherCols = (kTileM + 1 + kGatherSites - 1 + kGatherSites - 1) / kGatherSites * kGatherSites;
 constexpr uint32_t kGatherBoxBytes = 2u * kGatherCols * 16u;
 constexpr uint32_t kGatherDirBytes = (kGatherBoxBytes + 127u) & ~127u;
 constexpr uint32_t kGatherStageBytes = kGatherDirs * kGatherDirBytes;
 constexpr uint32_t kGatherStageTx = kGatherDirs * kGatherBoxBytes;   // bytes the TMA delivers per slot
 
 // Byte offset of window row `row`, column `col` (0..128 from the first site
-// the taps read, which sits `odd` sites after the box's even first site).
-__device__ __forceinline__ uint32_t gather_window_offset(int row, int col, int odd)
+// the taps read, which sits `lead` sites after the box's first site).
+__device__ __forceinline__ uint32_t gather_window_offset(int row, int col, int lead)
 {
-    return (uint32_t)row * (kGatherCols * 16u) + (uint32_t)(col + odd) * 16u;
+    return (uint32_t)row * (kGatherCols * 16u) + (uint32_t)(col + lead) * 16u;
 }
 
 // Arguments of the tensor-core step kernels.
@@ -258,7 +264,7 @@ __device__ __forceinline__ bool convert_tile_gather(const float4 cf, const float
 #pragma unroll 1
                 for (int e = 0; e < kGatherDirs; ++e) {
                     const int d = d_beg + 4 * h + e;
-                    const int xs0 = x0 - gt.n0x[d] - 1, xe = xs0 - (xs0 & 1), zs0 = z - gt.n0z[d] - 1;
+                    const int xs0 = x0 - gt.n0x[d] - 1, xe = xs0 - (xs0 & (kGatherSites - 1)), zs0 = z - gt.n0z[d] - 1;
                     float4 *win = reinterpret_cast<float4 *>(stg + e * kGatherDirBytes);
 #pragma unroll 1
                     for (int idx = r; idx < 2 * kGatherCols; idx += kTileM) {
@@ -286,7 +292,7 @@ __device__ __forceinline__ bool convert_tile_gather(const float4 cf, const float
                     const int n0x = gt.n0x[d];
                     const float w[4] = {w4.x, w4.y, w4.z, w4.w};
                     const uint8_t *win = stg + (2 * dp + e) * kGatherDirBytes;
-                    const int odd = (x - r - n0x - 1) & 1;   // the window's first site is odd
+                    const int lead = (x - r - n0x - 1) & (kGatherSites - 1);   // first tap after the box's first site
                     // tap (bx, bz): window row 1 - bz, column r + 1 - bx; the
                     // loads are unconditional (in the window), the sums skip
                     // zero weights
@@ -294,7 +300,7 @@ __device__ __forceinline__ bool convert_tile_gather(const float4 cf, const float
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
                         tv[k] = *reinterpret_cast<const float4 *>(win +
-                                                                  gather_window_offset(1 - (k >> 1), r + 1 - (k & 1), odd));
+                                                                  gather_window_offset(1 - (k >> 1), r + 1 - (k & 1), lead));
                     float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
@@ -346,8 +352,8 @@ __device__ __forceinline__ bool convert_tile_gather(const float4 cf, const float
 
 // Producer side of the gather form: issues the windows of staging slot j of
 // the tile whose first site is site0 -- directions 4j ... 4j + 3, one box
-// each, from the even site at or below the first site the taps read (x0 is
-// even: nx % 128 == 0).  (An L2 prefetch of the windows a few slots ahead
+// each, from the multiple of kGatherSites at or below the first site the taps
+// read (nx % 128 == 0).  (An L2 prefetch of the windows a few slots ahead
 // measured slower at every distance tried, 4 to 12 slots.)
 __device__ __forceinline__ void gather_slot_loads(const CUtensorMap *tm, const GatherTaps &gt, int nx, int site0, int j,
                                                   uint32_t dst, uint32_t bar)
@@ -357,7 +363,8 @@ __device__ __forceinline__ void gather_slot_loads(const CUtensorMap *tm, const G
     for (int e = 0; e < kGatherDirs; ++e) {
         const int d = kGatherDirs * j + e;
         const int xs = x0 - gt.n0x[d] - 1;
-        tma_load_4d(dst + e * kGatherDirBytes, tm, bar, 0, (xs - (xs & 1)) / 2, z - gt.n0z[d] - 1, d);
+        tma_load_4d(dst + e * kGatherDirBytes, tm, bar, 0, (xs - (xs & (kGatherSites - 1))) / kGatherSites,
+                    z - gt.n0z[d] - 1, d);
     }
 }
 
