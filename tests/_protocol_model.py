@@ -146,7 +146,8 @@ def _chunks(n):
     return (4 * n + 63) // 64            # 64-wide bf16 K chunks per tile
 
 
-def bf16_step(items, stages, seed, shared_ring=False):
+def bf16_step(items, stages, seed, shared_ring=False, gather=False, edge_tiles=(), skip_fill_wait=False,
+              gather_ring_flaw=False, slow=None):
     """The single-CTA tensor-core step (and the batch kernel, whose items may
     differ in n and table): `items` lists (n, table key) per tile in the order
     a CTA processes them.  Roles as in the kernels: one producer thread (TMA of
@@ -157,8 +158,16 @@ def bf16_step(items, stages, seed, shared_ring=False):
     commit per chunk barrier for every chunk the widest item has, then the
     accumulator barrier, then `z_free` before a key change) and eight epilogue
     warps (quadrant q, half of the directions).  shared_ring: the earlier form
-    in which both converter groups consumed one ring of `stages` slots."""
-    M = Machine(seed)
+    in which both converter groups consumed one ring of `stages` slots.
+    gather: the gather form of bilinear streaming -- staging slots of four
+    directions (n / 4 per tile), slot j to group (j >> 1) & 1, group grp
+    taking slots 4c + 2 grp and 4c + 2 grp + 1 of chunk c; in the tiles listed
+    in `edge_tiles` each of the group's four warps first writes its part of
+    the window's ghost values, arrives on the group's fill barrier (count 4)
+    and waits for it before reading the window.  skip_fill_wait: the warps
+    read without that wait; gather_ring_flaw: the producer keeps the
+    eight-direction form's group of a slot (j & 1) (planted flaws)."""
+    M = Machine(seed, slow)
     T = len(items)
     ring = stages // 2
     max_c = max(_chunks(n) for n, _ in items)
@@ -169,11 +178,13 @@ def bf16_step(items, stages, seed, shared_ring=False):
     acc_full = [Barrier(f"acc_full[{b}]", 1) for b in range(2)]
     acc_empty = [Barrier(f"acc_empty[{b}]", 8) for b in range(2)]
     z_full, z_free = Barrier("z_full", 1), Barrier("z_free", 1)
+    fill_bar = [Barrier(f"fill_bar[{g}]", 4) for g in range(2)]
     stage = [None] * stages
+    filled = {}                  # (staging slot, quadrant) -> (tile, slot) whose ghost values it holds
     A, acc, z = {}, {}, [None]
     base = [0]
     for n, _ in items:
-        base.append(base[-1] + _groups(n))
+        base.append(base[-1] + (n // 4 if gather else _groups(n)))
 
     def slot_of(i, j, grp, local):
         if shared_ring:
@@ -195,8 +206,8 @@ def bf16_step(items, stages, seed, shared_ring=False):
                     z_full.complete_tx(1)
                 M.tma_load(land_z)
                 prev = key
-            for j in range(_groups(n)):
-                gr = j & 1
+            for j in range(n // 4 if gather else _groups(n)):
+                gr = (j >> 1) & 1 if gather and not gather_ring_flaw else j & 1
                 local = gq[gr]
                 gq[gr] += 1
                 s, k = slot_of(i, j, gr, local)
@@ -210,24 +221,39 @@ def bf16_step(items, stages, seed, shared_ring=False):
 
     def converter(q, grp):
         who = f"converter(q{q},g{grp})"
-        gq = 0
+        gq = fq = 0
         for i, (n, key) in enumerate(items):
             b = i & 1
             yield Wait(acc_empty[b], (i >> 1) - 1, who)
             for c in range(_chunks(n)):
                 j = 2 * c + grp
                 mine = j < _groups(n)
-                if mine:
+                for h in range(2 if gather else 1):
+                    if not mine:
+                        break
+                    sj = 4 * c + 2 * grp + h if gather else j
                     local = gq
                     gq += 1
-                    s, k = slot_of(i, j, grp, local)
+                    s, k = slot_of(i, sj, grp, local)
                     yield Wait(st_full[s], k, who)
-                    if stage[s] != (i, j):
-                        raise ProtocolError(f"{who} tile {i} slot {j}: staging slot {s} holds {stage[s]}")
-                    cell = acc.get((b, j, q))
-                    if cell is not None and cell[0] != "free":
-                        raise ProtocolError(f"{who} tile {i}: accumulator {b} slot {j} still {cell[0]} for tile {cell[1]}")
-                    acc[(b, j, q)] = ["init", i, 0]
+                    if stage[s] != (i, sj):
+                        raise ProtocolError(f"{who} tile {i} slot {sj}: staging slot {s} holds {stage[s]}")
+                    if gather and i in edge_tiles:
+                        filled[(s, q)] = (i, sj)
+                        fill_bar[grp].arrive()
+                        if not skip_fill_wait:
+                            yield Wait(fill_bar[grp], fq, who)
+                        fq += 1
+                        for q2 in range(4):
+                            if filled.get((s, q2)) != (i, sj):
+                                raise ProtocolError(f"{who} tile {i} slot {sj}: window part {q2} of staging slot {s} "
+                                                    f"holds {filled.get((s, q2))}")
+                    if h == 0:
+                        cell = acc.get((b, j, q))
+                        if cell is not None and cell[0] != "free":
+                            raise ProtocolError(f"{who} tile {i}: accumulator {b} slot {j} still {cell[0]} "
+                                                f"for tile {cell[1]}")
+                        acc[(b, j, q)] = ["init", i, 0]
                     st_empty[s].arrive()
                 yield Wait(a_empty[c], i - 1, who)
                 if mine:
@@ -806,7 +832,7 @@ def table_step(masks, stages, seed, gate_done=True, slow=None):
     return M.steps
 
 
-def pair_step(keys, stages, seed, n=64, gate_acc_empty=True, slow=None, gather=False, gather_ring_flaw=False):
+def pair_step(keys, stages, seed, n=64, gate_acc_empty=True, slow=None):
     """The CTA-pair kernel (cta_group::2, bf16 state operand and split table):
     each entry of `keys` is one pair of tiles (one per CTA) of the same table
     key.  Per CTA: a producer (its half of the table and its own tile's
@@ -818,12 +844,7 @@ def pair_step(keys, stages, seed, n=64, gate_acc_empty=True, slow=None, gather=F
     odd producer forwards the completion of its table half to the even z_full
     (count 2).  gate_acc_empty=False lets the converters write a tile's
     accumulator init without waiting for the epilogue of two tiles before (a
-    planted flaw).  gather: the bilinear gather form, whose staging slots hold
-    four directions each (n / 4 per tile); slot j goes to group (j >> 1) & 1,
-    and group grp takes slots 4c + 2 grp and 4c + 2 grp + 1 of chunk c
-    (together its eight directions of the chunk).  gather_ring_flaw: the
-    producer keeps the eight-direction form's group of a slot (j & 1), a
-    planted flaw."""
+    planted flaw)."""
     M = Machine(seed, slow)
     T = len(keys)
     G, C, ring = _groups(n), _chunks(n), stages // 2
@@ -863,8 +884,8 @@ def pair_step(keys, stages, seed, n=64, gate_acc_empty=True, slow=None, gather=F
                     z_full[0].arrive()                      # forward to the even CTA
                 zl += 1
                 prev = key
-            for j in range(n // 4 if gather else G):
-                gr = (j >> 1) & 1 if gather and not gather_ring_flaw else j & 1
+            for j in range(G):
+                gr = j & 1
                 local = gq[gr]
                 gq[gr] += 1
                 s = gr * ring + local % ring
@@ -884,21 +905,18 @@ def pair_step(keys, stages, seed, n=64, gate_acc_empty=True, slow=None, gather=F
             if gate_acc_empty:
                 yield Wait(acc_empty[(r, b)], (i >> 1) - 1, who)
             for c in range(C):
-                j = 2 * c + grp                             # eight-direction group of the accumulator
-                for h in range(2 if gather else 1):
-                    sj = 4 * c + 2 * grp + h if gather else j
-                    local = gq
-                    gq += 1
-                    s = grp * ring + local % ring
-                    yield Wait(st_full[(r, s)], local // ring, who)
-                    if stage[(r, s)] != (i, sj):
-                        raise ProtocolError(f"{who} tile {i} slot {sj}: staging holds {stage[(r, s)]}")
-                    if h == 0:
-                        cell = acc.get((r, b, j, q))
-                        if cell is not None and cell[0] != "free":
-                            raise ProtocolError(f"{who} tile {i}: accumulator {b} slot {j} still {cell[0]}")
-                        acc[(r, b, j, q)] = ["init", i, 0]
-                    st_empty[(r, s)].arrive()
+                j = 2 * c + grp
+                local = gq
+                gq += 1
+                s = grp * ring + local % ring
+                yield Wait(st_full[(r, s)], local // ring, who)
+                if stage[(r, s)] != (i, j):
+                    raise ProtocolError(f"{who} tile {i} slot {j}: staging holds {stage[(r, s)]}")
+                cell = acc.get((r, b, j, q))
+                if cell is not None and cell[0] != "free":
+                    raise ProtocolError(f"{who} tile {i}: accumulator {b} slot {j} still {cell[0]}")
+                acc[(r, b, j, q)] = ["init", i, 0]
+                st_empty[(r, s)].arrive()
                 yield Wait(a_empty[(r, c)], i - 1, who)
                 A[(r, c, grp, q)] = i
             (t_ready[b] if r == 0 else t_local[b]).arrive()

@@ -73,24 +73,37 @@ def test_cta_pair_step_is_race_free(stages):
             P.pair_step([0, 0, 1, 1, 0, 0], stages, seed, slow={slow: 0.01})
 
 
-@pytest.mark.parametrize("stages", [2, 4])
-def test_cta_pair_gather_form_is_race_free(stages):
-    """The CTA-pair kernel in the bilinear gather form: four-direction
-    staging slots, two per converter group and chunk; also with one role
+@pytest.mark.parametrize("n", [16, 32])
+@pytest.mark.parametrize("stages", [4, 8])
+def test_gather_form_is_race_free(n, stages):
+    """The single-CTA step in the gather form of bilinear streaming:
+    four-direction slots, two per converter group and chunk, and the ghost
+    fill of edge tiles met on each group's fill barrier; also with one role
     lagging far behind."""
-    for seed in range(10):
-        P.pair_step([0, 0, 0, 1, 1, 0, 0], stages, seed, gather=True)
-    for slow in ("epi0", "conv1", "producer1", "mma"):
-        for seed in range(4):
-            P.pair_step([0, 0, 1, 1, 0], stages, seed, slow={slow: 0.01}, gather=True)
+    items = [(n, 0), (n, 0), (n, 1), (n, 1), (n, 0)]
+    for seed in range(8):
+        P.bf16_step(items, stages, seed, gather=True, edge_tiles={0, 2, 3})
+    for slow in ("conv01", "conv10", "epi", "mma", "producer"):
+        for seed in range(3):
+            P.bf16_step(items, stages, seed, gather=True, edge_tiles={1, 2}, slow={slow: 0.01})
 
 
-def test_cta_pair_gather_model_sees_wrong_ring():
+def test_gather_model_sees_unfinished_fill():
+    """Converter warps that read the window of an edge tile without waiting
+    for the group's fill barrier: with one warp of the group lagging, the
+    model must report a window part not yet filled."""
+    with pytest.raises(P.ProtocolError, match="window part"):
+        for seed in range(20):
+            P.bf16_step([(32, 0)] * 3, 4, seed, gather=True, edge_tiles={0, 1, 2}, skip_fill_wait=True,
+                        slow={"conv31": 0.01})
+
+
+def test_gather_model_sees_wrong_ring():
     """A producer that hands the gather form's slots to the groups of the
     eight-direction form (j & 1) feeds a group slots of the other group's
     directions: the model must report it."""
     with pytest.raises(P.ProtocolError):
-        P.pair_step([0, 0, 1], 2, 0, gather=True, gather_ring_flaw=True)
+        P.bf16_step([(32, 0)] * 3, 4, 0, gather=True, gather_ring_flaw=True)
 
 
 def test_cta_pair_model_sees_unreleased_accumulator():
