@@ -212,11 +212,12 @@ StepParams make_params(rtlb_ctx *c)
 // tc_gather: n in {16, 32}, nx % 128 == 0) gather the four taps of the
 // previous step's P while loading their operand, so a run of steps moves the
 // state once per step instead of twice (collision pass, then
-// k_stream_bilinear).  Measured at 2048^2: 1.39 against 1.69 ms per step at
+// k_stream_bilinear).  Measured at 2048^2: 1.34 against 1.69 ms per step at
 // n = 32 (bf16), 0.67 against 0.83 ms at n = 16.  The float32 step keeps the
-// two passes (its gathering load measured 8-10 % slower: the load phase of
-// its tiles does not overlap the arithmetic), and so do the n = 64 forms, whose
-// two staging slots cannot hide the windows' latency (4.16 against 3.29 ms).
+// two passes (gathering in its tile load measured slower: 1.43 against 1.30 ms
+// at 1024^2, n = 32; 4.21 against 3.80 ms at n = 64), and so do the n = 64
+// tensor-core forms, whose two staging slots cannot hide the windows' latency
+// (4.16 against 3.29 ms).
 bool gather_form(const rtlb_ctx *c)
 {
     return bilinear(c) && c->opt.precision != RTLB_PREC_FP32 && tc_gather(c);
