@@ -172,21 +172,26 @@ def _settle_each_step(s, w):
     s.set_boundary(0, w.bc[0], inflow if w.bc[0] == 2 else None)
 
 
-@pytest.mark.parametrize("prec,nzen,naz,mixed,bc", [("bf16", 4, 4, False, (2, 0, 1, 1)),
-                                                     ("bf16x2", 4, 8, True, (2, 0, 1, 1)),
-                                                     ("bf16x3", 4, 8, False, (2, 2, 0, 0)),
-                                                     ("bf16", 4, 8, True, (0, 0, 0, 0))])
-def test_gather_form_equals_two_pass(torch_cuda, prec, nzen, naz, mixed, bc):
+@pytest.mark.parametrize("prec,nzen,naz,mixed,bc,nx,nz", [("bf16", 4, 4, False, (2, 0, 1, 1), 256, 7),
+                                                           ("bf16x2", 4, 8, True, (2, 0, 1, 1), 256, 7),
+                                                           ("bf16x3", 4, 8, False, (2, 2, 0, 0), 256, 7),
+                                                           ("bf16", 4, 8, True, (0, 0, 0, 0), 256, 7),
+                                                           ("bf16x2", 4, 4, False, (1, 1, 2, 0), 256, 6),
+                                                           ("bf16", 4, 8, False, (1, 1, 1, 1), 128, 3)])
+def test_gather_form_equals_two_pass(torch_cuda, prec, nzen, naz, mixed, bc, nx, nz):
     """The gather form (each step gathers the previous step's P while
     loading: the tensor-core bf16 forms at n in {16, 32} with nx % 128 == 0)
     against the two-pass form (collision pass, then the gather kernel) on the
     same inputs: identical bits for the state, the readouts, the residual and
     a following adjoint.  Boundaries: top inflow, periodic x, vacuum bottom
     (ghost values written into the staged windows), inflow top and bottom,
-    all vacuum (the TMA's zero fill); `mixed` puts a class boundary inside
-    tiles (those tiles run on the CUDA-core kernel, also gathering)."""
+    all vacuum (the TMA's zero fill), periodic z with inflow on the left, and
+    periodic on both axes on a lattice one tile wide and three rows high
+    (every tile an edge tile, windows wrapping on both sides); `mixed` puts a
+    class boundary inside tiles (those tiles run on the CUDA-core kernel, also
+    gathering)."""
     from paper_2609_23057_b300.solver import solver_for
-    w = W.random_medium(256, 7, nzen, naz, seed=nzen * naz + 5, bc=bc, n_phase=2, steps=5)
+    w = W.random_medium(nx, nz, nzen, naz, seed=nzen * naz + 5, bc=bc, n_phase=2, steps=5)
     if mixed:
         w.phase_index = ((np.arange(w.nx)[None, :] >= 100) * np.ones((w.nz, 1))).astype(np.uint8)
     else:
