@@ -75,7 +75,7 @@ struct TcState {
     bool tmS_ready[2] = {false, false};
     const float *tmS_ptr[2] = {nullptr, nullptr};
     // gather form (bilinear streaming, single-CTA bf16 forms): window maps of
-    // both state buffers, the taps; tiles ordered down 256-site column strips
+    // both state buffers, the taps; tiles ordered down 512-site column strips
     bool gather = false;
     GatherTaps gtaps{};
     CUtensorMap tmG[2]{};
