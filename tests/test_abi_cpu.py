@@ -34,6 +34,30 @@ def test_library_exports_every_declared_symbol():
     assert set(_lib.EXPORTS) <= declared
 
 
+def _header_struct_fields(name):
+    """int32 fields of `typedef struct { ... } name;` in include/rtlb.h, in order."""
+    text = open(os.path.join(ROOT, "include", "rtlb.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct\s*\{([^}]*)\}\s*" + name + r"\s*;", text, flags=re.S).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        typ, names = decl.split(None, 1)
+        assert typ == "int32_t", decl
+        fields += [n.strip() for n in names.split(",")]
+    return fields
+
+
+def test_binding_structs_match_the_header():
+    """The ctypes mirrors of the ABI's all-int32 structs list the header's
+    fields in the header's order."""
+    for struct, cls in (("rtlb_options", _lib.Options), ("rtlb_form", _lib.Form), ("rtlb_grid", _lib.Grid)):
+        assert [f for f, _ in cls._fields_] == _header_struct_fields(struct), struct
+        assert all(t is C.c_int32 for _, t in cls._fields_), struct
+
+
 @pytest.mark.parametrize("nzen,naz", [(2, 4), (4, 8), (8, 8), (3, 6), (1, 4), (5, 7)])
 def test_offsets_match_oracle(orc, nzen, naz):
     mu, phi = orc.direction_grid(nzen, naz)
